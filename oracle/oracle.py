@@ -1,0 +1,190 @@
+"""Python front end of the CPU FP64 oracle (qs_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+CPU-baseline leg of the benchmark may import this module; the product path
+never does.  It shares no code with the CUDA library: it compiles its own C
+file with gcc (``-O2 -ffp-contract=off``) into ``oracle/_build`` and calls it
+through ctypes.  States are numpy complex128 arrays, whose memory layout is the
+interleaved (re, im) layout the C routines expect.
+"""
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def compile_source(src: str, out: str) -> str:
+    """gcc -O2 -ffp-contract=off: separately rounded IEEE double operations."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(
+        ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+         src, "-o", tmp, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile qs_oracle.c into a shared library (plain gcc, no vector extensions)."""
+    with _lock:
+        if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+            os.makedirs(_BUILD, exist_ok=True)
+            compile_source(_SRC, _LIB_PATH)
+    return _LIB_PATH
+
+
+def load_library(path):
+    """Open a compiled oracle library and declare its C signatures."""
+    lib = ctypes.CDLL(path)
+    _declare(lib)
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = load_library(build())
+    return _lib
+
+
+def _declare(lib):
+    lib.or_init_basis.argtypes = [_dp, ctypes.c_int, ctypes.c_uint64]
+    lib.or_apply_1q.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp]
+    lib.or_apply_ctrl.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+    lib.or_apply_swap.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.or_run.argtypes = [_dp, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int]
+    lib.or_run.restype = ctypes.c_int
+    lib.or_gate_matrix.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.or_norm2.argtypes = [_dp, ctypes.c_int]
+    lib.or_norm2.restype = ctypes.c_double
+    lib.or_marginals.argtypes = [_dp, ctypes.c_int, _dp]
+    lib.or_probs.argtypes = [_dp, ctypes.c_int, _dp]
+    lib.or_expect.argtypes = [_dp, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+    lib.or_expect.restype = ctypes.c_double
+    lib.or_grad.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int,
+                            ctypes.c_void_p, ctypes.c_int, _dp, _dp]
+    lib.or_grad.restype = ctypes.c_int
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _state(psi):
+    if psi.dtype != np.complex128 or not psi.flags.c_contiguous:
+        raise TypeError("oracle states are C-contiguous complex128 arrays")
+    n = int(psi.size).bit_length() - 1
+    if psi.size != (1 << n):
+        raise ValueError("state length must be a power of two")
+    return n
+
+
+def _m8(m):
+    m = np.ascontiguousarray(m, dtype=np.float64).reshape(8)
+    return m
+
+
+def basis(n: int, x: int = 0) -> np.ndarray:
+    psi = np.empty(1 << n, dtype=np.complex128)
+    _load().or_init_basis(_ptr(psi.view(np.float64)), n, x)
+    return psi
+
+
+def apply_1q(psi, k, m8):
+    n = _state(psi)
+    if not 0 <= k < n:
+        raise ValueError("qubit out of range")
+    m = _m8(m8)
+    _load().or_apply_1q(_ptr(psi.view(np.float64)), n, k, _ptr(m))
+
+
+def apply_ctrl(psi, c, t, m8):
+    n = _state(psi)
+    if not (0 <= c < n and 0 <= t < n and c != t):
+        raise ValueError("bad control/target")
+    m = _m8(m8)
+    _load().or_apply_ctrl(_ptr(psi.view(np.float64)), n, c, t, _ptr(m))
+
+
+def apply_swap(psi, a, b):
+    n = _state(psi)
+    if not (0 <= a < n and 0 <= b < n and a != b):
+        raise ValueError("bad swap qubits")
+    _load().or_apply_swap(_ptr(psi.view(np.float64)), n, a, b)
+
+
+def run(psi, gates, theta=None):
+    """Apply the gate records in order, in place."""
+    n = _state(psi)
+    gates = np.ascontiguousarray(gates)
+    th = np.ascontiguousarray(theta if theta is not None else np.zeros(0), dtype=np.float64)
+    rc = _load().or_run(_ptr(psi.view(np.float64)), n, gates.ctypes.data, len(gates),
+                        _ptr(th) if th.size else None, int(th.size))
+    if rc != 0:
+        raise ValueError("invalid gate record")
+    return psi
+
+
+def simulate(n, gates, theta=None, x=0):
+    return run(basis(n, x), gates, theta)
+
+
+def gate_matrix(gate, theta=None):
+    th = np.ascontiguousarray(theta if theta is not None else np.zeros(1), dtype=np.float64)
+    g = np.ascontiguousarray(np.atleast_1d(gate))
+    out = np.zeros(8, dtype=np.float64)
+    _load().or_gate_matrix(g.ctypes.data, _ptr(th), _ptr(out))
+    return out
+
+
+def norm2(psi):
+    n = _state(psi)
+    return _load().or_norm2(_ptr(psi.view(np.float64)), n)
+
+
+def marginals(psi):
+    n = _state(psi)
+    out = np.zeros(n, dtype=np.float64)
+    _load().or_marginals(_ptr(psi.view(np.float64)), n, _ptr(out))
+    return out
+
+
+def probs(psi):
+    n = _state(psi)
+    out = np.zeros(1 << n, dtype=np.float64)
+    _load().or_probs(_ptr(psi.view(np.float64)), n, _ptr(out))
+    return out
+
+
+def expect(psi, terms):
+    n = _state(psi)
+    terms = np.ascontiguousarray(terms)
+    v = _load().or_expect(_ptr(psi.view(np.float64)), n, terms.ctypes.data, len(terms))
+    if np.isnan(v):
+        raise ValueError("invalid Pauli term")
+    return v
+
+
+def grad(n, gates, theta, terms):
+    """(energy, gradient) of <psi(theta)|H|psi(theta)> from the definition of the derivative."""
+    gates = np.ascontiguousarray(gates)
+    terms = np.ascontiguousarray(terms)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    e = np.zeros(1, dtype=np.float64)
+    g = np.zeros(max(1, th.size), dtype=np.float64)
+    rc = _load().or_grad(n, gates.ctypes.data, len(gates), _ptr(th), int(th.size),
+                         terms.ctypes.data, len(terms), _ptr(e), _ptr(g))
+    if rc != 0:
+        raise ValueError("invalid gradient input")
+    return float(e[0]), g[: th.size].copy()
