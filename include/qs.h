@@ -1,0 +1,214 @@
+/*
+ * qs.h -- C ABI of the GB300 state-vector gate engine (libqs.so).
+ *
+ * What it computes: the data-parallel core of qHiPSTER (Smelyanskiy, Sawaya,
+ * Aspuru-Guzik, arXiv:1601.07195): a general single-qubit 2x2 unitary Q on
+ * qubit k (Eq. 2) and a controlled-Q gate with control c and target t (Eq. 3),
+ * applied in place to a dense state of 2^n complex amplitudes.  Amplitude i
+ * holds basis state |i>, qubit k is bit k of i, so the two amplitudes a gate on
+ * qubit k mixes are 2^k apart (Section 2).  Runs of gates are fused into one
+ * pass over device memory (the gate fusion / cache blocking of Section 4.4,
+ * Fig. 5, with a shared-memory tile in place of the last-level cache).
+ *
+ * Not in the paper, built beside it: complex64 states, FP64 reductions
+ * (norm, marginals, probabilities, Pauli-sum expectations), adjoint gradients
+ * of rotation angles, and batched execution of many small circuits.
+ *
+ * Conventions for every entry point:
+ *   - Pointers are plain host or device pointers; sizes are element counts.
+ *     Nothing here takes or returns a framework (PyTorch) object.
+ *   - A qs_state is bound to one CUDA device and one stream.  Apply calls are
+ *     asynchronous on that stream; calls that return host values (qs_norm,
+ *     qs_prob, qs_probs, qs_expect, qs_copy_out, qs_grad) synchronise it.
+ *   - Invalid arguments return QS_EINVAL before anything is launched; CUDA
+ *     failures return QS_ECUDA; a device-side wait that ran out of time
+ *     returns QS_ETIMEOUT.  No call aborts the process.  The message of the
+ *     last failure on the calling thread is returned by qs_last_error().
+ *   - Matrices are 8 doubles: row-major (q11, q12, q21, q22) as (re, im)
+ *     pairs; row = output amplitude, column = input amplitude (Eq. 2).
+ *     complex64 states round them to float once on the host.
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QS_API __attribute__((visibility("default")))
+#else
+#define QS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+typedef enum {
+    QS_OK = 0,
+    QS_EINVAL = 1,    /* bad argument, detected before any launch */
+    QS_ENOMEM = 2,    /* device or pinned-host allocation failed */
+    QS_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    QS_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    QS_EDTYPE = 5     /* operation not available for this state's dtype */
+} qs_status;
+
+/* Gate record kinds.  QS_G_U1: Q on t (Eq. 2).  QS_G_CU: controlled-Q,
+ * control c, target t (Eq. 3).  QS_G_SWAP: exchange qubits t and c.
+ * QS_G_RX/RY/RZ: exp(-i theta G / 2) on t, G = X/Y/Z, theta = theta[param]. */
+enum { QS_G_U1 = 0, QS_G_CU = 1, QS_G_SWAP = 2, QS_G_RX = 3, QS_G_RY = 4, QS_G_RZ = 5 };
+
+/* 80-byte gate record; m is ignored for QS_G_SWAP and the rotation kinds. */
+typedef struct {
+    int32_t kind;
+    int32_t t;      /* target qubit (first qubit of a swap) */
+    int32_t c;      /* control qubit (second qubit of a swap); -1 if none */
+    int32_t param;  /* angle index for rotations; -1 otherwise */
+    double m[8];
+} qs_gate;
+
+/* Pauli-sum term: coef * Z_q0, coef * Z_q0 Z_q1, or coef * X_q0. */
+enum { QS_P_Z = 0, QS_P_ZZ = 1, QS_P_X = 2 };
+typedef struct {
+    int32_t kind;
+    int32_t q0;
+    int32_t q1;     /* second qubit of QS_P_ZZ; -1 otherwise */
+    int32_t pad;
+    double coef;
+} qs_term;
+
+typedef struct qs_state qs_state;
+typedef struct qs_plan qs_plan;
+
+/* ---- state lifetime ------------------------------------------------------ */
+
+/* Allocate a device state of 2^n amplitudes (1 <= n <= 36, limited by free
+ * device memory) on the current device, bound to `cuda_stream` (a
+ * cudaStream_t; NULL = legacy default stream), initialised to |0..0>.
+ * The state owns its memory; qs_destroy frees it. */
+QS_API qs_status qs_create(int n, qs_dtype dt, void* cuda_stream, qs_state** out);
+
+/* Wrap caller-owned device memory of 2^n amplitudes (interleaved re, im;
+ * 16-byte aligned for complex128, 8-byte for complex64) without copying.
+ * The caller keeps the memory alive until after qs_destroy. */
+QS_API qs_status qs_wrap(void* dev_ptr, int n, qs_dtype dt, void* cuda_stream, qs_state** out);
+
+/* Release the handle (and the memory, for qs_create).  NULL is accepted. */
+QS_API qs_status qs_destroy(qs_state* s);
+
+/* Rebind the state to another stream of the same device. */
+QS_API qs_status qs_set_stream(qs_state* s, void* cuda_stream);
+
+/* Device address, qubit count and dtype of a state. */
+QS_API qs_status qs_info(const qs_state* s, void** dev_ptr, int* n, qs_dtype* dt);
+
+/* Set the state to the basis state |x> (x < 2^n). */
+QS_API qs_status qs_init_basis(qs_state* s, uint64_t x);
+
+/* Host <-> device copies of amplitudes [off, off + cnt), in the state's dtype. */
+QS_API qs_status qs_copy_out(qs_state* s, uint64_t off, uint64_t cnt, void* host);
+QS_API qs_status qs_copy_in(qs_state* s, uint64_t off, uint64_t cnt, const void* host);
+
+/* ---- single gates (Eq. 2, Eq. 3) ----------------------------------------- */
+
+/* Q on qubit k, 0 <= k < n. */
+QS_API qs_status qs_apply_1q(qs_state* s, int k, const double U[8]);
+
+/* Controlled-Q: Q on target t where control bit c is 1; c != t. */
+QS_API qs_status qs_apply_ctrl(qs_state* s, int c, int t, const double U[8]);
+
+/* SWAP of qubits a != b (an index permutation; moves amplitudes bit-exactly). */
+QS_API qs_status qs_apply_swap(qs_state* s, int a, int b);
+
+/* ---- circuits --------------------------------------------------------------- */
+
+/* Plan flags. */
+enum {
+    QS_PLAN_DEFAULT = 0,
+    QS_PLAN_NO_FUSION = 1,  /* one pass over the state per gate (no tiles) */
+    QS_PLAN_GRAPH = 2,      /* capture the launches once and replay a CUDA graph */
+    QS_PLAN_ARITH_F64 = 4,  /* complex128: native FP64 arithmetic in every kernel */
+    QS_PLAN_DRY_RUN = 8     /* plan on the host only (no device memory); cannot execute */
+};
+
+/* Build an execution plan for `gates` (copied in) on state s: gate classes,
+ * fused tile passes of gates whose mixing qubits fit one tile (Section 4.4,
+ * Fig. 5), single-gate passes for the rest.  theta (n_params angles) is read
+ * for the rotation kinds; it is copied in too.  tile_bits = log2 amplitudes
+ * per tile (0 = automatic). */
+QS_API qs_status qs_plan_create(qs_state* s, const qs_gate* gates, int n_gates, const double* theta, int n_params,
+                         int flags, int tile_bits, qs_plan** out);
+
+/* Launch the plan on the state's stream (asynchronous). */
+QS_API qs_status qs_plan_execute(qs_plan* p);
+
+/* Plan statistics: number of passes over the state, of which tile passes,
+ * and the kernel launches one execution makes. */
+QS_API qs_status qs_plan_stats(const qs_plan* p, int* n_passes, int* n_tile_passes, int* n_launches);
+
+/* Per-pass description: for pass i, its kind (0 = single gate, 1 = tile),
+ * first gate and gate count in plan order, and the tile's qubit mask. */
+QS_API qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* n_gates, uint64_t* tile_mask);
+
+/* Circuit positions of pass i's gates in execution order (n_gates ints, see
+ * qs_plan_pass).  Within and across passes the planner only moves a gate ahead
+ * of gates it commutes with (disjoint qubits, or both diagonal). */
+QS_API qs_status qs_plan_pass_gates(const qs_plan* p, int i, int* positions);
+
+/* Free the plan; waits for the plan's launches on the state's stream first. */
+QS_API qs_status qs_plan_destroy(qs_plan* p);
+
+/* Plan, execute and destroy in one call. */
+QS_API qs_status qs_run(qs_state* s, const qs_gate* gates, int n_gates, const double* theta, int n_params);
+
+/* ---- FP64 reductions (not in the paper) ---------------------------------- */
+
+/* *out = sum_i |alpha_i|^2 (squared 2-norm = total probability). */
+QS_API qs_status qs_norm(qs_state* s, double* out);
+
+/* Marginal P(qubit k = 1) = sum over i with bit k set of |alpha_i|^2.
+ * k >= 0: one value into p1[0]; k = -1: all n marginals into p1[0..n-1]. */
+QS_API qs_status qs_prob(qs_state* s, int k, double* p1);
+
+/* host_out[i] = |alpha_i|^2 for all 2^n amplitudes (host buffer of 2^n doubles). */
+QS_API qs_status qs_probs(qs_state* s, double* host_out);
+
+/* <psi|H|psi> for H = sum_j coef_j P_j with Z, ZZ and X terms. */
+QS_API qs_status qs_expect(qs_state* s, const qs_term* terms, int n_terms, double* out);
+
+/* ---- adjoint gradients (not in the paper) --------------------------------- */
+
+/* One variational instance: E(theta) = <psi|H|psi>, psi = U_P..U_1 |0..0>. */
+typedef struct {
+    int32_t n;            /* qubits */
+    int32_t n_gates;
+    const qs_gate* gates; /* rotation kinds carry the parameter index */
+    int32_t n_params;
+    const double* theta;
+    int32_t n_terms;
+    const qs_term* terms;
+} qs_instance;
+
+/* Energies and gradients dE/dtheta of a batch of instances by one adjoint
+ * reverse sweep each (Jones & Gacon, arXiv:2009.02823).  energies[i] gets
+ * instance i's energy; grads gets the instances' gradients concatenated in
+ * order (sum of n_params doubles).  Both are host buffers.  dt selects the
+ * state precision; all reductions are FP64. */
+QS_API qs_status qs_grad(const qs_instance* batch, int n_inst, qs_dtype dt, void* cuda_stream,
+                  double* energies, double* grads);
+
+/* ---- diagnostics ------------------------------------------------------------- */
+
+/* Message of the last failure on the calling thread ("" if none). */
+QS_API const char* qs_last_error(void);
+
+/* Library version string. */
+QS_API const char* qs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QS_H */

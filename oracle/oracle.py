@@ -188,3 +188,13 @@ def grad(n, gates, theta, terms):
     if rc != 0:
         raise ValueError("invalid gradient input")
     return float(e[0]), g[: th.size].copy()
+
+
+def qft_basis_amplitudes(n, x, ys):
+    """Closed form of the quantum Fourier transform of |x> at indices ys:
+    2^(-n/2) exp(2 pi i (x y mod 2^n) / 2^n), the modular product taken in exact
+    integer arithmetic before the floating-point exponential."""
+    ys = np.asarray(ys, dtype=np.uint64)
+    mod = (1 << n) - 1
+    ph = np.array([(int(x) * int(y)) & mod for y in ys], dtype=np.float64)
+    return np.exp(2j * np.pi * ph / float(1 << n)) * 2.0 ** (-n / 2)

@@ -1,0 +1,280 @@
+// plan.cu -- the circuit planner and executor.
+//
+// Section 4.4 groups consecutive gates on qubits below l_c and applies the
+// group block by block while the block stays in the last-level cache.  Here a
+// pass is a set of gates applied tile by tile in shared memory (tile.cu).  The
+// planner builds passes greedily in gate order:
+//   * qubits 0..b0-1 are always tile bits (contiguous global-memory runs);
+//   * a gate joins the pass if its mixing qubits (target; both qubits of a
+//     swap; none for a diagonal gate) fit in the b tile bits;
+//   * a later gate may be pulled into the pass ahead of gates left behind when
+//     it commutes with each of them: disjoint qubits, or both diagonal;
+//   * a pass holding a single gate runs as a strided single-gate kernel
+//     (gates.cu), which moves only the amplitudes the gate changes.
+// The order of the gates within a pass and among the gates left behind is the
+// circuit order, so the plan computes the same ordered product (up to
+// rounding) as applying the gates one at a time.
+#include <algorithm>
+#include <cstring>
+
+#include "device.cuh"
+
+namespace qs {
+namespace {
+
+constexpr int kWindow = 512;  // gates scanned ahead when filling a pass
+
+struct PlanPass {
+    int kind;        // 0 = single gate, 1 = tile pass
+    Op op;           // single gate
+    TilePass tp;     // tile pass
+    uint64_t mask;   // tile qubits (tile pass) or the gate's qubits
+    int n_gates;
+    std::vector<int> members;  // circuit positions of the pass's gates, in execution order
+};
+
+inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+void default_tile(qs_dtype dt, int& b, int& b0) {
+    if (dt == QS_C128) { b = 12; b0 = 4; }
+    else { b = 13; b0 = 5; }
+}
+
+}  // namespace
+}  // namespace qs
+
+struct qs_plan {
+    qs_state* s = nullptr;
+    int flags = 0;
+    std::vector<qs::PlanPass> passes;
+    void* d_ops = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+namespace qs {
+namespace {
+
+template <class R>
+TileOp<R> to_tile_op(const Op& o, const int* bit_of) {
+    TileOp<R> t{};
+    t.kind = o.kind;
+    t.cls = o.cls;
+    t.tq = o.t;
+    t.tb = bit_of[o.t];
+    t.cq = o.c;
+    t.cb = o.c >= 0 ? bit_of[o.c] : -1;
+    for (int j = 0; j < 8; ++j) t.m[j] = (R)o.m[j];
+    return t;
+}
+
+template <class R>
+qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse, bool upload) {
+    const int n = p->s->n;
+    b = std::min(b, n);
+    b0 = std::min(b0, b);
+    const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
+    std::vector<TileOp<R>> tops;
+    std::vector<char> taken(ops.size(), 0);
+    size_t first = 0;
+    while (first < ops.size()) {
+        std::vector<int> mem;
+        uint64_t T = (1ull << b0) - 1ull;
+        if (!fuse) {
+            mem.push_back((int)first);
+            taken[first] = 1;
+        } else {
+            const Op& f = ops[first];
+            const uint64_t fneed = f.kind == OP_SWAP ? ((1ull << f.t) | (1ull << f.c))
+                                                     : (op_is_diagonal(f) ? 0ull : (1ull << f.t));
+            if (popc(T | fneed) > b) {  // the next gate cannot share a tile: it runs alone
+                mem.push_back((int)first);
+                taken[first] = 1;
+            }
+        }
+        if (fuse && mem.empty()) {
+            uint64_t blocked_all = 0, blocked_nd = 0;
+            int scanned = 0;
+            for (size_t j = first; j < ops.size() && scanned < kWindow; ++j) {
+                if (taken[j]) continue;
+                ++scanned;
+                const Op& o = ops[j];
+                const uint64_t sup = (1ull << o.t) | (o.c >= 0 ? (1ull << o.c) : 0ull);
+                const bool diag = op_is_diagonal(o);
+                const bool movable = diag ? !(sup & blocked_nd) : !(sup & blocked_all);
+                if (movable) {
+                    const uint64_t need = o.kind == OP_SWAP ? sup : (diag ? 0ull : (1ull << o.t));
+                    if (popc(T | need) <= b) {
+                        T |= need;
+                        mem.push_back((int)j);
+                        taken[j] = 1;
+                        continue;
+                    }
+                }
+                blocked_all |= sup;
+                if (!diag) blocked_nd |= sup;
+                if ((blocked_nd & all) == all) break;
+            }
+        }
+        if (mem.empty()) return fail(QS_EINVAL, "planner made no progress");  // unreachable: the first gate always fits
+        while (first < ops.size() && taken[first]) ++first;
+
+        PlanPass pp{};
+        pp.n_gates = (int)mem.size();
+        pp.members = mem;
+        if (mem.size() == 1) {
+            pp.kind = 0;
+            pp.op = ops[mem[0]];
+            pp.mask = (1ull << pp.op.t) | (pp.op.c >= 0 ? (1ull << pp.op.c) : 0ull);
+            p->passes.push_back(pp);
+            continue;
+        }
+        // pad the tile to b bits with the lowest unused qubits (longer contiguous runs)
+        for (int q = 0; q < n && popc(T) < b; ++q) T |= (1ull << q);
+        int run = 0;
+        while (run < n && ((T >> run) & 1ull)) ++run;
+        TilePass& tp = pp.tp;
+        tp.b = b;
+        tp.b0 = run < b ? run : b;
+        tp.nontile_mask = all & ~T;
+        int bit_of[64];
+        for (int q = 0; q < 64; ++q) bit_of[q] = -1;
+        int nh = 0;
+        for (int q = 0; q < n; ++q) {
+            if (!((T >> q) & 1ull)) continue;
+            if (q < tp.b0) bit_of[q] = q;
+            else { bit_of[q] = tp.b0 + nh; tp.hi_q[nh++] = q; }
+        }
+        tp.op0 = (int)tops.size();
+        tp.nops = (int)mem.size();
+        for (int j : mem) tops.push_back(to_tile_op<R>(ops[j], bit_of));
+        pp.kind = 1;
+        pp.mask = T;
+        p->passes.push_back(pp);
+    }
+    if (upload && !tops.empty()) {
+        const size_t bytes = tops.size() * sizeof(TileOp<R>);
+        cudaError_t e = cudaMalloc(&p->d_ops, bytes);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(QS_ENOMEM, "plan: cudaMalloc of tile ops failed"); }
+        QS_CUDA_TRY(cudaMemcpy(p->d_ops, tops.data(), bytes, cudaMemcpyHostToDevice));
+    }
+    return QS_OK;
+}
+
+qs_status launch_all(qs_plan* p) {
+    const bool f64 = (p->flags & QS_PLAN_ARITH_F64) != 0;
+    for (const PlanPass& pp : p->passes) {
+        qs_status st = pp.kind == 0 ? launch_op(p->s, pp.op, f64) : launch_tile_pass(p->s, p->d_ops, pp.tp, f64);
+        if (st != QS_OK) return st;
+    }
+    return QS_OK;
+}
+
+}  // namespace
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" {
+
+qs_status qs_plan_create(qs_state* s, const qs_gate* gates, int n_gates, const double* theta, int n_params,
+                         int flags, int tile_bits, qs_plan** out) {
+    if (!out) return fail(QS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!s || !s->data) return fail(QS_EINVAL, "state handle is NULL");
+    if (n_params < 0) return fail(QS_EINVAL, "n_params < 0");
+    std::vector<Op> ops;
+    if (qs_status st = lower_gates(gates, n_gates, theta, n_params, s->n, ops)) return st;
+    int b, b0;
+    default_tile(s->dt, b, b0);
+    if (tile_bits > 0) {
+        if (tile_bits > kMaxTileBits || tile_smem_bytes(s->dt, tile_bits) + ((size_t)8 << (tile_bits - std::min(b0, tile_bits))) > smem_optin())
+            return fail(QS_EINVAL, "tile_bits too large for shared memory");
+        b = tile_bits;
+        if (b0 > b) b0 = b;
+    }
+    qs_plan* p = new (std::nothrow) qs_plan();
+    if (!p) return fail(QS_ENOMEM, "host allocation failed");
+    p->s = s;
+    p->flags = flags;
+    const bool fuse = !(flags & QS_PLAN_NO_FUSION);
+    const bool upload = !(flags & QS_PLAN_DRY_RUN);
+    qs_status st = s->dt == QS_C128 ? build<double>(p, ops, b, b0, fuse, upload) : build<float>(p, ops, b, b0, fuse, upload);
+    if (st != QS_OK) {
+        qs_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return QS_OK;
+}
+
+qs_status qs_plan_execute(qs_plan* p) {
+    if (!p || !p->s) return fail(QS_EINVAL, "plan is NULL");
+    if (p->flags & QS_PLAN_DRY_RUN) return fail(QS_EINVAL, "a dry-run plan cannot be executed");
+    const bool graph = (p->flags & QS_PLAN_GRAPH) && p->s->stream != nullptr;
+    if (!graph) return launch_all(p);
+    if (!p->gexec) {
+        QS_CUDA_TRY(cudaStreamBeginCapture(p->s->stream, cudaStreamCaptureModeThreadLocal));
+        qs_status st = launch_all(p);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(p->s->stream, &g);
+        if (st != QS_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        p->graph = g;
+        QS_CUDA_TRY(cudaGraphInstantiate(&p->gexec, g, 0));
+    }
+    QS_CUDA_TRY(cudaGraphLaunch(p->gexec, p->s->stream));
+    return QS_OK;
+}
+
+qs_status qs_plan_stats(const qs_plan* p, int* n_passes, int* n_tile_passes, int* n_launches) {
+    if (!p) return fail(QS_EINVAL, "plan is NULL");
+    int tiles = 0;
+    for (const PlanPass& pp : p->passes) tiles += pp.kind == 1;
+    if (n_passes) *n_passes = (int)p->passes.size();
+    if (n_tile_passes) *n_tile_passes = tiles;
+    if (n_launches) *n_launches = (int)p->passes.size();
+    return QS_OK;
+}
+
+qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* n_gates, uint64_t* tile_mask) {
+    if (!p) return fail(QS_EINVAL, "plan is NULL");
+    if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
+    const PlanPass& pp = p->passes[i];
+    if (kind) *kind = pp.kind;
+    if (n_gates) *n_gates = pp.n_gates;
+    if (tile_mask) *tile_mask = pp.mask;
+    return QS_OK;
+}
+
+qs_status qs_plan_pass_gates(const qs_plan* p, int i, int* positions) {
+    if (!p || !positions) return fail(QS_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
+    const PlanPass& pp = p->passes[i];
+    for (size_t j = 0; j < pp.members.size(); ++j) positions[j] = pp.members[j];
+    return QS_OK;
+}
+
+qs_status qs_plan_destroy(qs_plan* p) {
+    if (!p) return QS_OK;
+    if (p->s && p->s->stream && !(p->flags & QS_PLAN_DRY_RUN)) cudaStreamSynchronize(p->s->stream);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->d_ops) cudaFree(p->d_ops);
+    delete p;
+    return QS_OK;
+}
+
+qs_status qs_run(qs_state* s, const qs_gate* gates, int n_gates, const double* theta, int n_params) {
+    qs_plan* p = nullptr;
+    if (qs_status st = qs_plan_create(s, gates, n_gates, theta, n_params, QS_PLAN_DEFAULT, 0, &p)) return st;
+    qs_status st = qs_plan_execute(p);
+    // the plan's op table must outlive the launches that read it
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    qs_plan_destroy(p);
+    if (st != QS_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "qs_run synchronize");
+    return QS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// qs_internal.h -- structures shared by the host code (C ABI, planner) and the
+// kernels of libqs.so.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qs.h"
+
+namespace qs {
+
+// Gate classes, decided on the host from the exact matrix entries.
+enum GateClass : int {
+    GC_GENERAL = 0,   // any 2x2
+    GC_REAL = 1,      // every imaginary part is zero (H, RY)
+    GC_DIAG = 2,      // q12 = q21 = 0 (RZ)
+    GC_DIAG1 = 3,     // q12 = q21 = 0 and q11 = 1 exactly (T, phase): only |1> amplitudes change
+    GC_ANTIDIAG = 4,  // q11 = q22 = 0
+    GC_PERM = 5       // exactly [[0,1],[1,0]] (X): a move
+};
+
+// Operation kinds after lowering the gate records.
+enum OpKind : int { OP_1Q = 0, OP_CU = 1, OP_SWAP = 2 };
+
+// A lowered gate (host side, FP64 matrix).
+struct Op {
+    int kind;      // OpKind
+    int cls;       // GateClass (unused for OP_SWAP)
+    int t;         // target (first swap qubit)
+    int c;         // control (second swap qubit), -1 if none
+    double m[8];
+};
+
+inline bool op_is_diagonal(const Op& o) {
+    return o.kind != OP_SWAP && (o.cls == GC_DIAG || o.cls == GC_DIAG1);
+}
+
+// A gate inside a tile pass, in tile coordinates (device side).
+template <class R>
+struct TileOp {
+    int32_t kind;  // OpKind
+    int32_t cls;   // GateClass
+    int32_t tb;    // target tile bit, -1 if the target lies outside the tile (diagonal only)
+    int32_t tq;    // target qubit
+    int32_t cb;    // control (or second swap qubit) tile bit, -1 if outside / none
+    int32_t cq;    // control (or second swap qubit) qubit, -1 if none
+    int32_t pad0, pad1;
+    R m[8];
+};
+
+constexpr int kMaxTileBits = 14;
+
+// Kernel argument describing one tile pass (by value).
+struct TilePass {
+    uint64_t nontile_mask;     // qubits that are NOT tile bits
+    int32_t b;                 // tile bits (2^b amplitudes per tile)
+    int32_t b0;                // tile bits 0..b0-1 are qubits 0..b0-1 (contiguous runs)
+    int32_t hi_q[kMaxTileBits];// qubit of tile bit b0 + j
+    int32_t op0;               // first op in the plan's TileOp array
+    int32_t nops;
+};
+
+}  // namespace qs
+
+// Internal state handle.
+struct qs_state {
+    int n;
+    qs_dtype dt;
+    void* data;          // device amplitudes
+    bool owned;
+    cudaStream_t stream;
+    int device;
+    double* d_partials;  // reduction scratch: per-block FP64 partial sums
+    size_t partials_cap; // doubles
+    double* h_result;    // pinned host staging for reduction results
+    size_t h_result_cap;
+};
+
+namespace qs {
+
+// Error reporting (thread-local message).
+void set_error(const std::string& msg);
+qs_status fail(qs_status st, const std::string& msg);
+qs_status cuda_fail(cudaError_t e, const char* what);
+#define QS_CUDA_TRY(expr)                                        \
+    do {                                                         \
+        cudaError_t qs_e_ = (expr);                              \
+        if (qs_e_ != cudaSuccess) return ::qs::cuda_fail(qs_e_, #expr); \
+    } while (0)
+
+inline size_t amp_bytes(qs_dtype dt) { return dt == QS_C128 ? 16 : 8; }
+
+// Device properties cached per device.
+int sm_count();
+size_t smem_optin();
+
+// Host-side classification and lowering of gate records.
+int classify(const double m[8]);
+qs_status lower_gates(const qs_gate* g, int ng, const double* theta, int np, int n, std::vector<Op>& out);
+
+// Single-gate launchers (gates.cu).
+qs_status launch_op(qs_state* s, const Op& op, bool arith_f64);
+
+// Tile pass launcher (tile.cu).
+qs_status launch_tile_pass(qs_state* s, const void* d_ops, const TilePass& pass, bool arith_f64);
+size_t tile_smem_bytes(qs_dtype dt, int b);
+
+// Reductions (reduce.cu).
+qs_status ensure_scratch(qs_state* s, size_t partial_doubles, size_t result_doubles);
+
+}  // namespace qs

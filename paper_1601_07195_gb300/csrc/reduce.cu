@@ -1,0 +1,374 @@
+// reduce.cu -- FP64 reductions over a state: norm, single-qubit marginals,
+// the probability vector, and Pauli-sum expectation values.  None of these is
+// in the paper; they read the state once (2^n amplitudes).
+//
+// Determinism: every reduction writes one FP64 partial per block of a fixed
+// grid and a second single-block kernel adds the partials in a fixed order, so
+// repeated calls give bit-identical results.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "device.cuh"
+
+namespace qs {
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kChunkBits = 12;                       // marginal chunk: 2^12 amplitudes per block step
+constexpr int kPerThread = 1 << (kChunkBits - 8);    // 16 amplitudes per thread per chunk
+constexpr int kMaxHigh = 40 - kChunkBits;            // chunk-index bits tracked per thread
+
+template <class T>
+__device__ __forceinline__ double prob(const T& a) {
+    const double x = (double)a.x, y = (double)a.y;
+    return fma(x, x, y * y);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block; the result is valid in thread 0.  `red` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// ---- norm ---------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) k_norm(const T* __restrict__ psi, uint64_t N, double* partials) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    const uint64_t stride = (uint64_t)gridDim.x * kRedThreads;
+    for (uint64_t i = (uint64_t)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += stride) acc += prob(psi[i]);
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// out[k] = sum_b partials[b * stride + k] for k < count, in block order.
+__global__ void k_finalize(const double* __restrict__ partials, int n_blocks, int stride, int count, double* out) {
+    for (int k = threadIdx.x; k < count; k += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < n_blocks; ++b) s += partials[(size_t)b * stride + k];
+        out[k] = s;
+    }
+}
+
+// ---- marginals: P(bit k = 1) for all k in one pass ---------------------------
+// A block step covers a chunk of 2^12 amplitudes: thread t reads amplitudes
+// chunk_base + (r << 8) + t, r < 16.  Bits 0..7 of the index are the thread id,
+// bits 8..11 are r, bits >= 12 the chunk index.  Each thread keeps its total,
+// the partial sums over r with bit m of r set, and per chunk-index bit the sum
+// of its chunk totals with that bit set; the block then folds the thread-id
+// bits.  Output per block: n + 1 partials (marginals, then the total).
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) k_marginals(const T* __restrict__ psi, int n, uint64_t n_chunks,
+                                                           double* partials) {
+    __shared__ double red[32];
+    double tot = 0.0, rbit[4] = {0, 0, 0, 0}, hbit[kMaxHigh];
+#pragma unroll
+    for (int k = 0; k < kMaxHigh; ++k) hbit[k] = 0.0;
+    const int nh = n - kChunkBits;
+    for (uint64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const uint64_t base = ch << kChunkBits;
+        double s = 0.0;
+#pragma unroll
+        for (int r = 0; r < kPerThread; ++r) {
+            const double p = prob(psi[base + ((uint64_t)r << 8) + threadIdx.x]);
+            s += p;
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                if ((r >> m) & 1) rbit[m] += p;
+        }
+        tot += s;
+#pragma unroll
+        for (int k = 0; k < kMaxHigh; ++k)
+            if (k < nh && ((ch >> k) & 1ull)) hbit[k] += s;
+    }
+    double* out = partials + (size_t)blockIdx.x * (n + 1);
+    for (int k = 0; k < 8; ++k) {
+        const double v = block_sum(((threadIdx.x >> k) & 1u) ? tot : 0.0, red);
+        if (threadIdx.x == 0) out[k] = v;
+    }
+    for (int m = 0; m < 4; ++m) {
+        const double v = block_sum(rbit[m], red);
+        if (threadIdx.x == 0) out[8 + m] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxHigh; ++k) {
+        if (k < nh) {
+            const double v = block_sum(hbit[k], red);
+            if (threadIdx.x == 0) out[kChunkBits + k] = v;
+        }
+    }
+    const double v = block_sum(tot, red);
+    if (threadIdx.x == 0) out[n] = v;
+}
+
+// Small states (n < 12): one block, every thread keeps all n bit sums.
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) k_marginals_small(const T* __restrict__ psi, int n, double* out) {
+    __shared__ double red[32];
+    double acc[kChunkBits + 1];
+#pragma unroll
+    for (int k = 0; k <= kChunkBits; ++k) acc[k] = 0.0;
+    const uint32_t N = 1u << n;
+    for (uint32_t i = threadIdx.x; i < N; i += kRedThreads) {
+        const double p = prob(psi[i]);
+        acc[kChunkBits] += p;
+#pragma unroll
+        for (int k = 0; k < kChunkBits; ++k)
+            if (k < n && ((i >> k) & 1u)) acc[k] += p;
+    }
+    for (int k = 0; k < n; ++k) {
+        const double v = block_sum(acc[k], red);
+        if (threadIdx.x == 0) out[k] = v;
+    }
+    const double v = block_sum(acc[kChunkBits], red);
+    if (threadIdx.x == 0) out[n] = v;
+}
+
+// ---- probability vector ---------------------------------------------------------
+template <class T>
+__global__ void k_probs(const T* __restrict__ psi, uint64_t off, uint64_t cnt, double* out) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) out[i] = prob(psi[off + i]);
+}
+
+// ---- diagonal part of a Pauli sum ---------------------------------------------------
+// e(i) = lo_tab[i & lo_mask] + hi_tab[i >> lo_bits] + sum over cross terms
+// (Z_q Z_r with q below the split and r above it) of coef * z_q(i) * z_r(i);
+// z_q(i) = 1 - 2 bit_q(i).  Accumulates sum_i |alpha_i|^2 e(i).
+struct CrossTerm { int q, r; double coef; };
+constexpr int kMaxCross = 64;
+struct CrossList { int count; CrossTerm t[kMaxCross]; };
+
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) k_expect_diag(const T* __restrict__ psi, uint64_t N, int lo_bits,
+                                                             const double* __restrict__ lo_tab,
+                                                             const double* __restrict__ hi_tab, CrossList cross,
+                                                             double* partials) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    const uint64_t lo_mask = (1ull << lo_bits) - 1ull;
+    const uint64_t stride = (uint64_t)gridDim.x * kRedThreads;
+    for (uint64_t i = (uint64_t)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += stride) {
+        double e = lo_tab[i & lo_mask] + hi_tab[i >> lo_bits];
+        for (int c = 0; c < cross.count; ++c) {
+            const uint64_t par = ((i >> cross.t[c].q) ^ (i >> cross.t[c].r)) & 1ull;
+            e += par ? -cross.t[c].coef : cross.t[c].coef;
+        }
+        acc = fma(prob(psi[i]), e, acc);
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// <X_q> = sum over pairs (i0, i0 + 2^q) of 2 Re(conj(alpha_i0) alpha_i1)
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) k_expect_x(const T* __restrict__ psi, uint64_t n_pairs, int q,
+                                                          double* partials) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    const uint64_t stride = (uint64_t)gridDim.x * kRedThreads;
+    for (uint64_t p = (uint64_t)blockIdx.x * kRedThreads + threadIdx.x; p < n_pairs; p += stride) {
+        const uint64_t i0 = insert_zero(p, q);
+        const T a = psi[i0], b = psi[i0 | (1ull << q)];
+        acc += 2.0 * fma((double)a.x, (double)b.x, (double)a.y * (double)b.y);
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+int reduce_blocks(uint64_t work) {
+    const uint64_t cap = (uint64_t)sm_count() * 8;
+    uint64_t b = (work + kRedThreads - 1) / kRedThreads;
+    if (b > cap) b = cap;
+    return b ? (int)b : 1;
+}
+
+qs_status sync_result(qs_state* s, const double* d_out, int count, double* host) {
+    QS_CUDA_TRY(cudaMemcpyAsync(s->h_result, d_out, count * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    std::memcpy(host, s->h_result, count * sizeof(double));
+    return QS_OK;
+}
+
+template <class T>
+qs_status norm_impl(qs_state* s, double* out) {
+    const uint64_t N = 1ull << s->n;
+    const int blocks = reduce_blocks(N);
+    if (qs_status st = ensure_scratch(s, blocks + 1, 1)) return st;
+    k_norm<T><<<blocks, kRedThreads, 0, s->stream>>>((const T*)s->data, N, s->d_partials);
+    k_finalize<<<1, 32, 0, s->stream>>>(s->d_partials, blocks, 1, 1, s->d_partials + blocks);
+    QS_CUDA_TRY(cudaGetLastError());
+    return sync_result(s, s->d_partials + blocks, 1, out);
+}
+
+template <class T>
+qs_status marginals_impl(qs_state* s, double* out_all) {
+    const int n = s->n;
+    if (n < kChunkBits) {
+        if (qs_status st = ensure_scratch(s, n + 1, n + 1)) return st;
+        k_marginals_small<T><<<1, kRedThreads, 0, s->stream>>>((const T*)s->data, n, s->d_partials);
+        QS_CUDA_TRY(cudaGetLastError());
+        return sync_result(s, s->d_partials, n + 1, out_all);
+    }
+    const uint64_t chunks = 1ull << (n - kChunkBits);
+    uint64_t b = (uint64_t)sm_count() * 4;
+    if (b > chunks) b = chunks;
+    const int blocks = (int)b;
+    if (qs_status st = ensure_scratch(s, (size_t)blocks * (n + 1) + (n + 1), n + 1)) return st;
+    double* fin = s->d_partials + (size_t)blocks * (n + 1);
+    k_marginals<T><<<blocks, kRedThreads, 0, s->stream>>>((const T*)s->data, n, chunks, s->d_partials);
+    k_finalize<<<1, 64, 0, s->stream>>>(s->d_partials, blocks, n + 1, n + 1, fin);
+    QS_CUDA_TRY(cudaGetLastError());
+    return sync_result(s, fin, n + 1, out_all);
+}
+
+// Sign of Z-string term on basis index x: +1 / -1.
+inline double zsign(uint64_t x, int q) { return ((x >> q) & 1ull) ? -1.0 : 1.0; }
+
+template <class T>
+qs_status expect_impl(qs_state* s, const qs_term* terms, int nt, double* out) {
+    const int n = s->n;
+    const uint64_t N = 1ull << n;
+    const int lo_bits = (n + 1) / 2, hi_bits = n - lo_bits;
+    const size_t nlo = (size_t)1 << lo_bits, nhi = (size_t)1 << hi_bits;
+    std::vector<double> lo_tab(nlo, 0.0), hi_tab(nhi, 0.0);
+    CrossList cross{};
+    std::vector<const qs_term*> xs;
+    bool any_diag = false;
+    for (int j = 0; j < nt; ++j) {
+        const qs_term& t = terms[j];
+        if (t.kind == QS_P_X) { xs.push_back(&t); continue; }
+        any_diag = true;
+        if (t.kind == QS_P_Z) {
+            if (t.q0 < lo_bits) for (size_t x = 0; x < nlo; ++x) lo_tab[x] += t.coef * zsign(x, t.q0);
+            else for (size_t x = 0; x < nhi; ++x) hi_tab[x] += t.coef * zsign(x, t.q0 - lo_bits);
+        } else {
+            const int a = std::min(t.q0, t.q1), b = std::max(t.q0, t.q1);
+            if (b < lo_bits) for (size_t x = 0; x < nlo; ++x) lo_tab[x] += t.coef * zsign(x, a) * zsign(x, b);
+            else if (a >= lo_bits) for (size_t x = 0; x < nhi; ++x) hi_tab[x] += t.coef * zsign(x, a - lo_bits) * zsign(x, b - lo_bits);
+            else {
+                if (cross.count >= kMaxCross) return fail(QS_EINVAL, "too many Z_q Z_r terms straddling the qubit split");
+                cross.t[cross.count++] = CrossTerm{a, b, t.coef};
+            }
+        }
+    }
+    const int blocks = reduce_blocks(N);
+    const int n_red = (any_diag ? 1 : 0) + (int)xs.size();
+    const size_t part = (size_t)blocks * n_red;
+    const size_t need = part + n_red + (any_diag ? nlo + nhi : 0);
+    if (qs_status st = ensure_scratch(s, need, n_red > 0 ? n_red : 1)) return st;
+    double* d_fin = s->d_partials + part;
+    double* d_lo = d_fin + n_red;
+    double* d_hi = d_lo + nlo;
+    int r = 0;
+    if (any_diag) {
+        QS_CUDA_TRY(cudaMemcpyAsync(d_lo, lo_tab.data(), nlo * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        QS_CUDA_TRY(cudaMemcpyAsync(d_hi, hi_tab.data(), nhi * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        k_expect_diag<T><<<blocks, kRedThreads, 0, s->stream>>>((const T*)s->data, N, lo_bits, d_lo, d_hi, cross,
+                                                                s->d_partials);
+        ++r;
+    }
+    for (const qs_term* t : xs) {
+        k_expect_x<T><<<blocks, kRedThreads, 0, s->stream>>>((const T*)s->data, N >> 1, t->q0,
+                                                             s->d_partials + (size_t)r * blocks);
+        ++r;
+    }
+    QS_CUDA_TRY(cudaGetLastError());
+    if (n_red == 0) { *out = 0.0; return QS_OK; }
+    // per-term sums in fixed block order, then the coefficient-weighted total on the host
+    for (int k = 0; k < n_red; ++k)
+        k_finalize<<<1, 32, 0, s->stream>>>(s->d_partials + (size_t)k * blocks, blocks, 1, 1, d_fin + k);
+    QS_CUDA_TRY(cudaGetLastError());
+    std::vector<double> sums(n_red);
+    if (qs_status st = sync_result(s, d_fin, n_red, sums.data())) return st;
+    double e = any_diag ? sums[0] : 0.0;
+    for (size_t k = 0; k < xs.size(); ++k) e += xs[k]->coef * sums[(any_diag ? 1 : 0) + k];
+    *out = e;
+    return QS_OK;
+}
+
+}  // namespace
+
+qs_status ensure_scratch(qs_state* s, size_t partial_doubles, size_t result_doubles) {
+    if (partial_doubles > s->partials_cap) {
+        if (s->d_partials) { cudaStreamSynchronize(s->stream); cudaFree(s->d_partials); s->d_partials = nullptr; s->partials_cap = 0; }
+        cudaError_t e = cudaMalloc(&s->d_partials, partial_doubles * sizeof(double));
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(QS_ENOMEM, "reduction scratch allocation failed"); }
+        s->partials_cap = partial_doubles;
+    }
+    if (result_doubles > s->h_result_cap) {
+        if (s->h_result) { cudaStreamSynchronize(s->stream); cudaFreeHost(s->h_result); s->h_result = nullptr; s->h_result_cap = 0; }
+        cudaError_t e = cudaMallocHost(&s->h_result, result_doubles * sizeof(double));
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(QS_ENOMEM, "pinned result allocation failed"); }
+        s->h_result_cap = result_doubles;
+    }
+    return QS_OK;
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" {
+
+qs_status qs_norm(qs_state* s, double* out) {
+    if (!s || !s->data || !out) return fail(QS_EINVAL, "NULL argument");
+    return s->dt == QS_C128 ? norm_impl<double2>(s, out) : norm_impl<float2>(s, out);
+}
+
+qs_status qs_prob(qs_state* s, int k, double* p1) {
+    if (!s || !s->data || !p1) return fail(QS_EINVAL, "NULL argument");
+    if (k < -1 || k >= s->n) return fail(QS_EINVAL, "qubit out of range");
+    std::vector<double> all(s->n + 1);
+    qs_status st = s->dt == QS_C128 ? marginals_impl<double2>(s, all.data()) : marginals_impl<float2>(s, all.data());
+    if (st != QS_OK) return st;
+    if (k >= 0) p1[0] = all[k];
+    else std::memcpy(p1, all.data(), s->n * sizeof(double));
+    return QS_OK;
+}
+
+qs_status qs_probs(qs_state* s, double* host_out) {
+    if (!s || !s->data || !host_out) return fail(QS_EINVAL, "NULL argument");
+    const uint64_t N = 1ull << s->n;
+    const uint64_t chunk = N < (1ull << 24) ? N : (1ull << 24);
+    if (qs_status st = ensure_scratch(s, chunk, 1)) return st;
+    for (uint64_t off = 0; off < N; off += chunk) {
+        const int blocks = reduce_blocks(chunk);
+        if (s->dt == QS_C128) k_probs<double2><<<blocks, kRedThreads, 0, s->stream>>>((const double2*)s->data, off, chunk, s->d_partials);
+        else k_probs<float2><<<blocks, kRedThreads, 0, s->stream>>>((const float2*)s->data, off, chunk, s->d_partials);
+        QS_CUDA_TRY(cudaGetLastError());
+        QS_CUDA_TRY(cudaMemcpyAsync(host_out + off, s->d_partials, chunk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    }
+    return QS_OK;
+}
+
+qs_status qs_expect(qs_state* s, const qs_term* terms, int n_terms, double* out) {
+    if (!s || !s->data || !out) return fail(QS_EINVAL, "NULL argument");
+    if (n_terms < 0 || (n_terms > 0 && !terms)) return fail(QS_EINVAL, "bad term array");
+    for (int j = 0; j < n_terms; ++j) {
+        const qs_term& t = terms[j];
+        if (t.kind != QS_P_Z && t.kind != QS_P_ZZ && t.kind != QS_P_X) return fail(QS_EINVAL, "unknown Pauli term kind");
+        if (t.q0 < 0 || t.q0 >= s->n) return fail(QS_EINVAL, "term qubit out of range");
+        if (t.kind == QS_P_ZZ && (t.q1 < 0 || t.q1 >= s->n || t.q1 == t.q0)) return fail(QS_EINVAL, "bad ZZ term");
+    }
+    return s->dt == QS_C128 ? expect_impl<double2>(s, terms, n_terms, out) : expect_impl<float2>(s, terms, n_terms, out);
+}
+
+}  // extern "C"

@@ -1,0 +1,302 @@
+"""Thin ctypes binding of the C ABI in include/qs.h (argument marshalling only).
+
+Every computation runs in libqs.so on the GPU.  There is no CPU fallback: if
+the library is missing or fails to load, importing a function raises.
+PyTorch supplies device memory and streams (``State.wrap_tensor``); states
+created by ``State.create`` own their device memory.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+QS_C64, QS_C128 = 0, 1
+QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EDTYPE = range(6)
+QS_G_U1, QS_G_CU, QS_G_SWAP, QS_G_RX, QS_G_RY, QS_G_RZ = range(6)
+QS_P_Z, QS_P_ZZ, QS_P_X = range(3)
+PLAN_DEFAULT, PLAN_NO_FUSION, PLAN_GRAPH, PLAN_ARITH_F64, PLAN_DRY_RUN = 0, 1, 2, 4, 8
+
+_STATUS = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EDTYPE"}
+
+GATE_DTYPE = np.dtype([("kind", "<i4"), ("t", "<i4"), ("c", "<i4"), ("param", "<i4"), ("m", "<f8", (8,))], align=True)
+TERM_DTYPE = np.dtype([("kind", "<i4"), ("q0", "<i4"), ("q1", "<i4"), ("pad", "<i4"), ("coef", "<f8")], align=True)
+
+
+class QSError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_gates", ctypes.c_int32), ("gates", ctypes.c_void_p),
+                ("n_params", ctypes.c_int32), ("theta", ctypes.c_void_p),
+                ("n_terms", ctypes.c_int32), ("terms", ctypes.c_void_p)]
+
+
+_lib = None
+_vp, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "qs_create": [ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)],
+    "qs_wrap": [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)],
+    "qs_destroy": [_vp],
+    "qs_set_stream": [_vp, _vp],
+    "qs_info": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "qs_init_basis": [_vp, ctypes.c_uint64],
+    "qs_copy_out": [_vp, ctypes.c_uint64, ctypes.c_uint64, _vp],
+    "qs_copy_in": [_vp, ctypes.c_uint64, ctypes.c_uint64, _vp],
+    "qs_apply_1q": [_vp, ctypes.c_int, _dp],
+    "qs_apply_ctrl": [_vp, ctypes.c_int, ctypes.c_int, _dp],
+    "qs_apply_swap": [_vp, ctypes.c_int, ctypes.c_int],
+    "qs_plan_create": [_vp, _vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)],
+    "qs_plan_execute": [_vp],
+    "qs_plan_stats": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "qs_plan_pass": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                     ctypes.POINTER(ctypes.c_uint64)],
+    "qs_plan_pass_gates": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "qs_plan_destroy": [_vp],
+    "qs_run": [_vp, _vp, ctypes.c_int, _dp, ctypes.c_int],
+    "qs_norm": [_vp, _dp],
+    "qs_prob": [_vp, ctypes.c_int, _dp],
+    "qs_probs": [_vp, _dp],
+    "qs_expect": [_vp, _vp, ctypes.c_int, _dp],
+    "qs_grad": [_vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp],
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libqs.so (building it first when the toolkit is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libqs.so not found at {path}; run paper_1601_07195_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.qs_last_error.restype = ctypes.c_char_p
+    lib.qs_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != QS_OK:
+        raise QSError(status, load().qs_last_error().decode())
+
+
+def _m8(m):
+    a = np.ascontiguousarray(m, dtype=np.float64).reshape(8)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class State:
+    """A 2^n-amplitude state on the GPU, handled through the C ABI."""
+
+    def __init__(self, handle, n, dtype, keepalive=None):
+        self._h = ctypes.c_void_p(handle)
+        self.n = n
+        self.dtype = dtype
+        self._keepalive = keepalive
+
+    @classmethod
+    def create(cls, n, dtype=QS_C128, stream=None):
+        h = _vp()
+        _check(load().qs_create(n, dtype, _stream_handle(stream), ctypes.byref(h)))
+        return cls(h.value, n, dtype)
+
+    @classmethod
+    def wrap_tensor(cls, tensor, stream=None):
+        """Wrap a CUDA tensor of dtype complex128/complex64 and 2^n elements (no copy)."""
+        import torch
+        if not tensor.is_cuda or not tensor.is_contiguous():
+            raise ValueError("need a contiguous CUDA tensor")
+        dt = {torch.complex128: QS_C128, torch.complex64: QS_C64}[tensor.dtype]
+        n = tensor.numel().bit_length() - 1
+        if tensor.numel() != 1 << n:
+            raise ValueError("tensor length must be a power of two")
+        if stream is None:
+            stream = torch.cuda.current_stream(tensor.device)
+        h = _vp()
+        _check(load().qs_wrap(tensor.data_ptr(), n, dt, _stream_handle(stream), ctypes.byref(h)))
+        return cls(h.value, n, dt, keepalive=tensor)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().qs_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- data movement
+    def init_basis(self, x=0):
+        _check(load().qs_init_basis(self._h, x))
+
+    @property
+    def np_dtype(self):
+        return np.complex128 if self.dtype == QS_C128 else np.complex64
+
+    def to_numpy(self, off=0, cnt=None):
+        cnt = (1 << self.n) - off if cnt is None else cnt
+        out = np.empty(cnt, dtype=self.np_dtype)
+        _check(load().qs_copy_out(self._h, off, cnt, out.ctypes.data))
+        return out
+
+    def from_numpy(self, arr, off=0):
+        a = np.ascontiguousarray(arr, dtype=self.np_dtype)
+        _check(load().qs_copy_in(self._h, off, a.size, a.ctypes.data))
+
+    def set_stream(self, stream):
+        _check(load().qs_set_stream(self._h, _stream_handle(stream)))
+
+    # ---- gates
+    def apply_1q(self, k, m8):
+        a, p = _m8(m8)
+        _check(load().qs_apply_1q(self._h, k, p))
+
+    def apply_ctrl(self, c, t, m8):
+        a, p = _m8(m8)
+        _check(load().qs_apply_ctrl(self._h, c, t, p))
+
+    def apply_swap(self, a, b):
+        _check(load().qs_apply_swap(self._h, a, b))
+
+    def run(self, gates, theta=None):
+        g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+        th = np.ascontiguousarray(theta if theta is not None else np.zeros(0), dtype=np.float64)
+        _check(load().qs_run(self._h, g.ctypes.data, len(g), th.ctypes.data_as(_dp) if th.size else None, th.size))
+
+    def plan(self, gates, theta=None, flags=PLAN_DEFAULT, tile_bits=0):
+        return Plan(self, gates, theta, flags, tile_bits)
+
+    # ---- reductions
+    def norm(self):
+        out = ctypes.c_double()
+        _check(load().qs_norm(self._h, ctypes.byref(out)))
+        return out.value
+
+    def prob(self, k):
+        out = ctypes.c_double()
+        _check(load().qs_prob(self._h, k, ctypes.byref(out)))
+        return out.value
+
+    def marginals(self):
+        out = np.zeros(self.n, dtype=np.float64)
+        _check(load().qs_prob(self._h, -1, out.ctypes.data_as(_dp)))
+        return out
+
+    def probs(self):
+        out = np.empty(1 << self.n, dtype=np.float64)
+        _check(load().qs_probs(self._h, out.ctypes.data_as(_dp)))
+        return out
+
+    def expect(self, terms):
+        t = np.ascontiguousarray(terms, dtype=TERM_DTYPE)
+        out = ctypes.c_double()
+        _check(load().qs_expect(self._h, t.ctypes.data, len(t), ctypes.byref(out)))
+        return out.value
+
+
+class Plan:
+    """A planned circuit (fused tile passes + single-gate passes) bound to a state."""
+
+    def __init__(self, state, gates, theta=None, flags=PLAN_DEFAULT, tile_bits=0):
+        g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+        th = np.ascontiguousarray(theta if theta is not None else np.zeros(0), dtype=np.float64)
+        h = _vp()
+        _check(load().qs_plan_create(state.handle, g.ctypes.data, len(g), th.ctypes.data_as(_dp) if th.size else None,
+                                     th.size, flags, tile_bits, ctypes.byref(h)))
+        self._h = h
+        self.state = state
+        self.n_gates = len(g)
+
+    def execute(self):
+        _check(load().qs_plan_execute(self._h))
+
+    def stats(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().qs_plan_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"passes": a.value, "tile_passes": b.value, "launches": c.value}
+
+    def passes(self):
+        out = []
+        for i in range(self.stats()["passes"]):
+            k, ng, mask = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint64()
+            _check(load().qs_plan_pass(self._h, i, ctypes.byref(k), ctypes.byref(ng), ctypes.byref(mask)))
+            pos = (ctypes.c_int * max(1, ng.value))()
+            _check(load().qs_plan_pass_gates(self._h, i, pos))
+            out.append({"kind": "tile" if k.value == 1 else "single", "n_gates": ng.value, "mask": mask.value,
+                        "gates": list(pos[:ng.value])})
+        return out
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().qs_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def grad(instances, dtype=QS_C128, stream=None):
+    """Energies and adjoint gradients of a batch of instances (dicts n, gates, theta, terms)."""
+    lib = load()
+    keep = []
+    arr = (Instance * len(instances))()
+    total = 0
+    for i, inst in enumerate(instances):
+        g = np.ascontiguousarray(inst["gates"], dtype=GATE_DTYPE)
+        th = np.ascontiguousarray(inst["theta"], dtype=np.float64)
+        tm = np.ascontiguousarray(inst["terms"], dtype=TERM_DTYPE)
+        keep += [g, th, tm]
+        arr[i] = Instance(inst["n"], len(g), g.ctypes.data, th.size, th.ctypes.data, len(tm), tm.ctypes.data)
+        total += th.size
+    energies = np.zeros(len(instances), dtype=np.float64)
+    grads = np.zeros(max(1, total), dtype=np.float64)
+    _check(lib.qs_grad(ctypes.cast(arr, _vp), len(instances), dtype, _stream_handle(stream),
+                       energies.ctypes.data_as(_dp), grads.ctypes.data_as(_dp)))
+    out, off = [], 0
+    for inst in instances:
+        p = len(inst["theta"])
+        out.append(grads[off:off + p].copy())
+        off += p
+    return energies, out

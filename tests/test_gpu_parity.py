@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Tolerances (max-abs amplitude error): 1e-12 for complex128, 1e-5 for
+complex64; bit-exact for permutation circuits (X, CNOT, SWAP) and basis-state
+tracking.  Every kernel class is forced: single-gate kernels for every qubit
+and (c, t) pair, tile passes of several tile sizes (including tiles that cover
+the whole state and tiles with ragged padding), fused and unfused plans, and
+CUDA-graph replay.
+"""
+
+import numpy as np
+import pytest
+
+import qsgen as G
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = {1: 1e-12, 0: 1e-5}
+DTYPES = [1, 0]  # QS_C128, QS_C64
+RED_TOL = {1: 1e-12, 0: 2e-6}
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1601_07195_gb300 import qs as _qs
+    _qs.load()
+    return _qs
+
+
+def rand_state(n, seed):
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    return v / np.linalg.norm(v)
+
+
+def upload(qs, n, dt, psi):
+    s = qs.State.create(n, dt)
+    s.from_numpy(psi)
+    return s
+
+
+def expected_input(psi, dt):
+    """The oracle starts from the state the GPU actually holds (rounded for complex64)."""
+    return psi.astype(np.complex64).astype(np.complex128) if dt == 0 else psi.copy()
+
+
+MATS = {
+    "H": G.gate_u1(0, G.MAT_H)[0]["m"],
+    "X": G.gate_u1(0, G.MAT_X)[0]["m"],
+    "T": G.gate_u1(0, G.MAT_T)[0]["m"],
+    "HAAR": G.gate_u1(0, G.haar_2x2(G.SplitMix64(3)))[0]["m"],
+    "DIAG": G.gate_u1(0, (np.exp(0.3j), 0, 0, np.exp(-1.1j)))[0]["m"],
+    "ANTI": G.gate_u1(0, (0, np.exp(0.7j), np.exp(2.1j), 0))[0]["m"],
+}
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n", [1, 5, 13])
+def test_single_qubit_gate_every_qubit_every_class(qs, dt, n):
+    for name, m in MATS.items():
+        for k in range(n):
+            psi = rand_state(n, 100 * k + n)
+            with upload(qs, n, dt, psi) as s:
+                s.apply_1q(k, m)
+                got = s.to_numpy()
+            want = expected_input(psi, dt)
+            O.apply_1q(want, k, m)
+            if name == "X":
+                assert np.array_equal(got, want.astype(got.dtype)), f"X on {k} not bit-exact"
+            else:
+                assert np.max(np.abs(got - want)) < TOL[dt], (name, k)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n", [2, 7])
+def test_controlled_gate_every_pair(qs, dt, n):
+    for name in ("X", "T", "HAAR", "DIAG"):
+        m = MATS[name]
+        for c in range(n):
+            for t in range(n):
+                if c == t:
+                    continue
+                psi = rand_state(n, 1000 + 10 * c + t)
+                with upload(qs, n, dt, psi) as s:
+                    s.apply_ctrl(c, t, m)
+                    got = s.to_numpy()
+                want = expected_input(psi, dt)
+                O.apply_ctrl(want, c, t, m)
+                if name == "X":
+                    assert np.array_equal(got, want.astype(got.dtype))
+                else:
+                    assert np.max(np.abs(got - want)) < TOL[dt], (name, c, t)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_controlled_gate_sweep_n13(qs, dt):
+    n = 13
+    m = MATS["HAAR"]
+    psi = rand_state(n, 5)
+    want = expected_input(psi, dt)
+    with upload(qs, n, dt, psi) as s:
+        for c in range(n):
+            for t in range(n):
+                if c != t:
+                    s.apply_ctrl(c, t, m)
+                    O.apply_ctrl(want, c, t, m)
+        got = s.to_numpy()
+    assert np.max(np.abs(got - want)) < 20 * TOL[dt]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_swap_every_pair_bit_exact(qs, dt):
+    n = 6
+    for a in range(n):
+        for b in range(n):
+            if a == b:
+                continue
+            psi = rand_state(n, 7 * a + b)
+            with upload(qs, n, dt, psi) as s:
+                s.apply_swap(a, b)
+                got = s.to_numpy()
+            want = expected_input(psi, dt)
+            O.apply_swap(want, a, b)
+            assert np.array_equal(got, want.astype(got.dtype))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("mode", ["fused", "unfused", "graph"])
+def test_random_circuit_n20(qs, dt, mode):
+    """The n=20 workload: 200 random gates from |0..0>, state and all marginals."""
+    n = 20
+    gates, _ = G.random_circuit(n, 200, G.SEEDS["random20"])
+    want = O.simulate(n, gates)
+    flags = {"fused": qs.PLAN_DEFAULT, "unfused": qs.PLAN_NO_FUSION, "graph": qs.PLAN_GRAPH}[mode]
+    import torch
+    stream = torch.cuda.Stream() if mode == "graph" else None
+    with qs.State.create(n, dt, stream=stream) as s:
+        p = s.plan(gates, flags=flags)
+        p.execute()
+        if mode == "graph":  # replay twice more after resetting the input: same result
+            s.init_basis(0)
+            p.execute()
+        got = s.to_numpy()
+        marg = s.marginals()
+        probs = s.probs()
+        nrm = s.norm()
+        p.close()
+    assert np.max(np.abs(got - want)) < TOL[dt]
+    assert np.max(np.abs(marg - O.marginals(want))) < RED_TOL[dt]
+    assert np.max(np.abs(probs - O.probs(want))) < RED_TOL[dt]
+    assert abs(nrm - 1.0) < (1e-12 if dt == 1 else 1e-5)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("tile_bits", [2, 3, 5, 8, 11, 12])
+def test_tile_sizes(qs, dt, tile_bits):
+    if dt == 1 and tile_bits > 13:
+        pytest.skip("does not fit")
+    n = 14
+    gates, _ = G.random_circuit(n, 300, 77 + tile_bits)
+    gates = G.concat([gates, G.qft_circuit(n)])
+    psi = rand_state(n, 9)
+    want = O.run(expected_input(psi, dt), gates)
+    with upload(qs, n, dt, psi) as s:
+        p = s.plan(gates, tile_bits=tile_bits)
+        st = p.passes()
+        p.execute()
+        got = s.to_numpy()
+        p.close()
+    assert sum(x["n_gates"] for x in st) == len(gates)
+    assert any(x["kind"] == "tile" for x in st)
+    assert np.max(np.abs(got - want)) < 5 * TOL[dt]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 9])
+def test_small_states_whole_state_tile(qs, dt, n):
+    gates, _ = G.random_circuit(max(n, 2), 60, 500 + n) if n >= 2 else (G.concat([G.gate_u1(0, MATS["HAAR"])] * 3), None)
+    psi = rand_state(n, 3)
+    want = O.run(expected_input(psi, dt), gates)
+    with upload(qs, n, dt, psi) as s:
+        s.run(gates)
+        got = s.to_numpy()
+    assert np.max(np.abs(got - want)) < TOL[dt]
+
+
+def _perm_circuit(n, count, seed):
+    rng = G.SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        r, a = rng.randint(3), rng.randint(n)
+        b = (a + 1 + rng.randint(n - 1)) % n
+        out.append(G.gate_u1(a, G.MAT_X) if r == 0 else G.gate_cu(a, b, G.MAT_X) if r == 1 else G.gate_swap(a, b))
+    return G.concat(out)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("flags", [0, 1])
+def test_permutation_circuits_bit_exact(qs, dt, flags):
+    n = 16
+    gates = _perm_circuit(n, 300, 11)
+    rng = np.random.default_rng(1)
+    psi = (rng.uniform(0.5, 1, 1 << n) * rng.choice([-1, 1], 1 << n)
+           + 1j * rng.uniform(0.5, 1, 1 << n) * rng.choice([-1, 1], 1 << n))
+    want = O.run(expected_input(psi, dt), gates)
+    with upload(qs, n, dt, psi) as s:
+        p = s.plan(gates, flags=flags)
+        p.execute()
+        got = s.to_numpy()
+        p.close()
+        for x in (0, 12345, (1 << n) - 1):
+            s.init_basis(x)
+            s.run(gates)
+            b = s.to_numpy()
+            w = O.simulate(n, gates, x=x)
+            assert np.array_equal(b, w.astype(b.dtype))
+    assert np.array_equal(got, want.astype(got.dtype))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_qft_closed_form_n18(qs, dt):
+    n = 18
+    x = G.random_basis(n, 3)
+    with qs.State.create(n, dt) as s:
+        s.init_basis(x)
+        s.run(G.qft_circuit(n))
+        got = s.to_numpy()
+    want = O.qft_basis_amplitudes(n, x, np.arange(1 << n))
+    assert np.max(np.abs(got - want)) < TOL[dt]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n", [3, 11, 12, 13, 17])
+def test_reductions(qs, dt, n):
+    psi = rand_state(n, 40 + n)
+    ref = expected_input(psi, dt)
+    rows = [(G.P_Z, 0, -1, 0.7), (G.P_ZZ, 0, n - 1, -1.3), (G.P_X, n - 1, -1, 0.45), (G.P_X, 0, -1, -2.0)]
+    rows += [(G.P_ZZ, i, i + 1, 0.1 * (i + 1)) for i in range(n - 1)] + [(G.P_Z, i, -1, -0.2 * i) for i in range(n)]
+    terms = G.terms(rows)
+    with upload(qs, n, dt, psi) as s:
+        assert abs(s.norm() - O.norm2(ref)) < 1e-13
+        assert np.max(np.abs(s.marginals() - O.marginals(ref))) < 1e-13
+        for k in range(n):
+            assert abs(s.prob(k) - O.marginals(ref)[k]) < 1e-13
+        assert abs(s.expect(terms) - O.expect(ref, terms)) < 1e-12
+        assert np.max(np.abs(s.probs() - O.probs(ref))) < 1e-15
+
+
+def test_reductions_are_deterministic(qs):
+    n = 22
+    with qs.State.create(n, 1) as s:
+        s.run(G.random_circuit(n, 100, 5)[0])
+        a = [s.norm(), *s.marginals(), s.expect(G.z_zz_observable(n, 1))]
+        b = [s.norm(), *s.marginals(), s.expect(G.z_zz_observable(n, 1))]
+    assert a == b
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_adjoint_gradients_match_oracle(qs, dt):
+    insts = []
+    for i, n in enumerate((2, 4, 6, 9)):
+        g, p = G.ansatz(n, 2)
+        g = G.concat([g, G.gate_rot(G.G_RX, n - 1, 0), G.gate_swap(0, n - 1)])
+        theta = G.angles(p, 10 + i)
+        obs = G.z_zz_observable(n, 20 + i) if i % 2 == 0 else G.ising_observable(n, 20 + i)
+        insts.append({"n": n, "gates": g, "theta": theta, "terms": obs})
+    e, gr = qs.grad(insts, dt)
+    for i, inst in enumerate(insts):
+        e_ref, g_ref = O.grad(inst["n"], inst["gates"], inst["theta"], inst["terms"])
+        tol = 1e-11 if dt == 1 else 1e-4
+        assert abs(e[i] - e_ref) < tol
+        assert np.max(np.abs(gr[i] - g_ref)) < tol
+
+
+def test_full_size_qft30_and_inverse_c128(qs):
+    """n=30 complex128 with the planned, fused launch sequence of the benchmark:
+    QFT of a random basis state, then a 1000-gate random circuit and its inverse.
+    Sampled amplitudes are compared with the QFT closed form; the norm stays 1."""
+    n = 30
+    x = G.random_basis(n, G.SEEDS["qft30"])
+    r, _ = G.random_circuit(n, 1000, G.SEEDS["qft30"])
+    gates = G.concat([G.qft_circuit(n), r, G.inverse_circuit(r)])
+    rng = np.random.default_rng(0)
+    ys = np.unique(np.concatenate([rng.integers(0, 1 << n, 4096), [0, 1, (1 << n) - 1]]))
+    with qs.State.create(n, 1) as s:
+        s.init_basis(x)
+        p = s.plan(gates)
+        p.execute()
+        vals = np.array([s.to_numpy(int(y), 1)[0] for y in ys])
+        nrm = s.norm()
+        p.close()
+    want = O.qft_basis_amplitudes(n, x, ys)
+    assert np.max(np.abs(vals - want)) < 1e-12
+    assert abs(nrm - 1.0) < 1e-11
+
+
+def test_invalid_arguments_on_live_state(qs):
+    with qs.State.create(4, 1) as s:
+        with pytest.raises(qs.QSError):
+            s.apply_1q(4, MATS["H"])
+        with pytest.raises(qs.QSError):
+            s.apply_ctrl(2, 2, MATS["X"])
+        with pytest.raises(qs.QSError):
+            s.run(G.gate_rot(G.G_RY, 0, 0))  # no angles
+        s.apply_1q(0, MATS["H"])  # the state is still usable
+        assert abs(s.norm() - 1.0) < 1e-14

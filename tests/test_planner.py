@@ -1,0 +1,121 @@
+"""Host logic of the planner, on the CPU (dry-run plans allocate no device memory).
+
+* every gate lands in exactly one pass;
+* a tile pass holds at most 2^b amplitudes' worth of qubits and contains the
+  mixing qubits of each of its gates (target, both swap qubits; none for
+  diagonal gates);
+* the execution order only moves a gate ahead of gates it commutes with
+  (disjoint qubits, or both diagonal), and the oracle applying the gates in
+  execution order reproduces the circuit-order state.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import qsgen as G
+from oracle import oracle as O
+from paper_1601_07195_gb300 import qs
+
+
+def fake_state(n, dt):
+    h = ctypes.c_void_p()
+    assert qs.load().qs_wrap(ctypes.c_void_p(1 << 30), n, dt, None, ctypes.byref(h)) == qs.QS_OK
+    return qs.State(h.value, n, dt)
+
+
+def is_diag(g):
+    k = int(g["kind"])
+    if k == G.G_SWAP:
+        return False
+    if k == G.G_RZ:
+        return True
+    if k in (G.G_RX, G.G_RY):
+        return False
+    m = g["m"]
+    return m[2] == 0 and m[3] == 0 and m[4] == 0 and m[5] == 0
+
+
+def support(g):
+    s = {int(g["t"])}
+    if int(g["c"]) >= 0:
+        s.add(int(g["c"]))
+    return s
+
+
+def mixing(g):
+    if int(g["kind"]) == G.G_SWAP:
+        return support(g)
+    return set() if is_diag(g) else {int(g["t"])}
+
+
+def commute(a, b):
+    return not (support(a) & support(b)) or (is_diag(a) and is_diag(b))
+
+
+CASES = {
+    "random20": lambda: (20, G.random_circuit(20, 200, 1000)[0], None),
+    "qft30+random": lambda: (30, G.concat([G.qft_circuit(30), G.random_circuit(30, 1000, 1001)[0]]), None),
+    "ansatz12": lambda: (12, G.ansatz(12, 4)[0], G.angles(96, 1)),
+    "qft7": lambda: (7, G.qft_circuit(7), None),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("tile_bits", [0, 2, 5, 8, 11])
+def test_plan_is_a_valid_reordering(case, dt, tile_bits):
+    n, gates, theta = CASES[case]()
+    st = fake_state(n, dt)
+    p = qs.Plan(st, gates, theta, flags=qs.PLAN_DRY_RUN, tile_bits=tile_bits)
+    passes = p.passes()
+    order = [g for ps in passes for g in ps["gates"]]
+    assert sorted(order) == list(range(len(gates)))
+    b = tile_bits if tile_bits else (12 if dt == 1 else 13)
+    b = min(b, n)
+    for ps in passes:
+        if ps["kind"] == "tile":
+            assert bin(ps["mask"]).count("1") == b
+            for j in ps["gates"]:
+                assert all((ps["mask"] >> q) & 1 for q in mixing(gates[j]))
+        else:
+            assert ps["n_gates"] == 1
+    pos = {g: i for i, g in enumerate(order)}
+    for a in range(len(gates)):
+        for c in range(a + 1, min(len(gates), a + 600)):
+            if pos[c] < pos[a]:
+                assert commute(gates[a], gates[c]), (a, c)
+    with pytest.raises(qs.QSError):
+        p.execute()  # dry-run plans never launch
+    p.close()
+    st.close()
+
+
+def test_execution_order_reproduces_the_state():
+    n = 12
+    gates = G.concat([G.qft_circuit(n), G.random_circuit(n, 400, 3)[0]])
+    st = fake_state(n, 1)
+    p = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN, tile_bits=6)
+    order = [g for ps in p.passes() for g in ps["gates"]]
+    assert order != list(range(len(gates)))  # the planner did move gates
+    a = O.simulate(n, gates, x=5)
+    b = O.simulate(n, gates[order], x=5)
+    assert np.max(np.abs(a - b)) < 1e-13
+
+
+def test_fusion_reduces_passes_for_the_n30_workload():
+    n = 30
+    gates = G.concat([G.qft_circuit(n), G.random_circuit(n, 1000, 1001)[0]])
+    st = fake_state(n, 1)
+    fused = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN).stats()
+    unfused = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN | qs.PLAN_NO_FUSION).stats()
+    assert unfused["passes"] == len(gates)
+    assert fused["passes"] < len(gates) / 4
+
+
+def test_no_fusion_keeps_circuit_order():
+    n, gates, _ = CASES["random20"]()
+    st = fake_state(n, 1)
+    p = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN | qs.PLAN_NO_FUSION)
+    assert [g for ps in p.passes() for g in ps["gates"]] == list(range(len(gates)))
