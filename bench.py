@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the state-vector gate engine on one GB300 (replicas on N GPUs).
+
+Workload: n = 30 qubits, complex128 (16 GiB state): the quantum Fourier
+transform of a random basis state (30 H + 435 controlled phase + 15 swaps)
+followed by a 1000-gate random circuit (H / X / T / Haar 2x2 on random qubits,
+CNOT / controlled phase on random pairs), seeds as in qsgen.SEEDS["qft30"].
+
+One step = |x> initialisation, every gate of the circuit through the planned
+launch sequence (fused tile passes and single-gate passes), and the FP64
+readout of the norm and all 30 marginals.  The plan is built once before the
+timed region (host work, reported as plan_ms).
+
+value = algorithmic bytes of the step / step time, in the paper's convention
+(Section 5.3: the memory traffic each gate needs on its own, summed over the
+gates, divided by the run time).  Bytes per gate (n qubits, s bytes per
+amplitude): 2*2^n*s for a single-qubit gate, 2^n*s for T-like diagonal gates
+(only |1> amplitudes change), controlled gates and swaps, 2^(n-1)*s for a
+controlled phase; 2^n*s per reduction pass and for the initialisation.
+
+--impl reference times the CPU FP64 oracle (the only other implementation of
+this path) on a bounded sample of the same workload.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import qsgen as G  # noqa: E402
+
+METRIC = "gate-apply GB/s vs HBM peak at 30q; batched adjoint-gradient circuits/sec"
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # 152 SMs x 2 DFMA (4 flop) per clock x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--no-secondary", action="store_true", help="skip the batched-gradient measurement")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---- workload and its algorithmic cost ------------------------------------------
+
+def workload(n):
+    x = G.random_basis(n, G.SEEDS["qft30"])
+    r, _ = G.random_circuit(n, 1000, G.SEEDS["qft30"])
+    return x, G.concat([G.qft_circuit(n), r])
+
+
+def gate_class(g):
+    m = g["m"]
+    if m[0] == 0 and m[1] == 0 and m[6] == 0 and m[7] == 0 and m[2] == 1 and m[3] == 0 and m[4] == 1 and m[5] == 0:
+        return "perm"
+    if m[2] == 0 and m[3] == 0 and m[4] == 0 and m[5] == 0:
+        return "diag1" if (m[0] == 1 and m[1] == 0) else "diag"
+    if m[0] == 0 and m[1] == 0 and m[6] == 0 and m[7] == 0:
+        return "antidiag"
+    if m[1] == 0 and m[3] == 0 and m[5] == 0 and m[7] == 0:
+        return "real"
+    return "general"
+
+
+# FP64 flops per amplitude the class's update touches (FMA = 2 flops)
+_FLOPS = {"general": 14.0, "real": 6.0, "diag": 6.0, "diag1": 6.0, "antidiag": 6.0, "perm": 0.0}
+
+
+def gate_cost(g, n, s):
+    """(algorithmic bytes, FP64 flops) of one gate on a 2^n state of s-byte amplitudes."""
+    N = float(1 << n)
+    kind = int(g["kind"])
+    if kind == G.G_SWAP:
+        return N * s, 0.0
+    if kind == G.G_U1:
+        c = gate_class(g)
+        touched = 0.5 if c == "diag1" else 1.0
+        return (2.0 if c != "diag1" else 1.0) * N * s, _FLOPS[c] * N * touched
+    if kind == G.G_CU:
+        c = gate_class(g)
+        touched = 0.25 if c == "diag1" else 0.5
+        return (0.5 if c == "diag1" else 1.0) * N * s, _FLOPS[c] * N * touched
+    raise ValueError("rotation kinds are not part of this workload")
+
+
+# ---- clocks ----------------------------------------------------------------------
+
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={CLOCK_QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]) if f[3] not in ("[N/A]", "N/A") else 0.0, f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ---- measurement legs ----------------------------------------------------------------
+
+def cpu_baseline(n, gates, s_bytes, target_s=15.0):
+    """Time the CPU FP64 oracle, as it stands, on a bounded sample of the workload:
+    gates spread evenly over the circuit, applied to the n-qubit state on the host."""
+    from oracle import oracle as O
+    O.build()
+    psi = O.basis(n, G.random_basis(n, G.SEEDS["qft30"]))
+    idx = np.linspace(0, len(gates) - 1, 64).astype(int)
+    done_bytes, elapsed, used = 0.0, 0.0, []
+    for j in idx:
+        t0 = time.perf_counter()
+        O.run(psi, gates[j:j + 1])
+        elapsed += time.perf_counter() - t0
+        done_bytes += gate_cost(gates[j], n, s_bytes)[0]
+        used.append(int(j))
+        if elapsed > target_s:
+            break
+    return {"value": done_bytes / elapsed / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(used)} gates spread over the n={n} workload (circuit positions {used[0]}..{used[-1]}), "
+                      f"applied by the single-threaded FP64 oracle to a 2^{n} complex128 host state; "
+                      f"{elapsed:.1f} s of CPU work"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the same metric, a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.n
+    s = 16
+    x, gates = workload(n)
+    from oracle import oracle as O
+    O.build()
+    psi = O.basis(n, x)
+    idx = np.linspace(0, len(gates) - 1, 3 * (args.steps + args.warmup)).astype(int)
+    chunks = np.array_split(idx, args.steps + args.warmup)
+    times, bts = [], []
+    for i, ch in enumerate(chunks):
+        t0 = time.perf_counter()
+        for j in ch:
+            O.run(psi, gates[j:j + 1])
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            bts.append(sum(gate_cost(gates[j], n, s)[0] for j in ch))
+    value = sum(bts) / sum(times) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"QFT({n}) on a random basis state + 1000-gate random circuit, complex128",
+                       "n": n, "gates": len(gates)},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"3 gates per step spread over the n={n} workload, single-threaded oracle"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def secondary_gradients(qs, dtype, torch):
+    """Batched adjoint gradients of the 512-instance variational workload vs
+    per-circuit central finite differences on the same GPU (sampled)."""
+    insts = G.batch_instances(G.SEEDS["batch512"], count=512)
+    stream = torch.cuda.current_stream()
+    qs.grad(insts[:4], dtype)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e, g = qs.grad(insts, dtype)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    # finite-difference comparator: 2P+1 energy evaluations per instance, on a sample
+    sample = insts[:2]
+    t0 = time.perf_counter()
+    for inst in sample:
+        n, th = inst["n"], inst["theta"]
+        with qs.State.create(n, dtype, stream=stream) as st:
+            def energy(theta):
+                st.init_basis(0)
+                st.run(inst["gates"], theta)
+                return st.expect(inst["terms"])
+            energy(th)
+            for p in range(len(th)):
+                tp, tm = th.copy(), th.copy()
+                tp[p] += 1e-6
+                tm[p] -= 1e-6
+                energy(tp)
+                energy(tm)
+    t_fd = (time.perf_counter() - t0) / len(sample)
+    return {"metric": "batched adjoint-gradient circuits/sec", "value": len(insts) / t_adj, "unit": "circuits/s",
+            "instances": len(insts), "dtype": "c128" if dtype == 1 else "c64",
+            "fd_circuits_per_s": 1.0 / t_fd, "fd_sample": len(sample),
+            "speedup_vs_fd": (len(insts) / t_adj) * t_fd}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1601_07195_gb300 import qs
+    qs.load()
+
+    n = args.n
+    dtype = qs.QS_C128 if args.dtype == "c128" else qs.QS_C64
+    s_bytes = 16 if dtype == qs.QS_C128 else 8
+    x, gates = workload(n)
+    N = float(1 << n)
+    gate_bytes = sum(gate_cost(g, n, s_bytes)[0] for g in gates)
+    step_bytes = gate_bytes + 3 * N * s_bytes  # init write + norm read + marginals read
+
+    stream = torch.cuda.Stream()
+    state = qs.State.create(n, dtype, stream=stream)
+    t0 = time.perf_counter()
+    plan = state.plan(gates)
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    passes = plan.passes()
+    plan.set_timing(args.steps)
+
+    def step():
+        state.init_basis(x)
+        plan.execute()
+        nrm = state.norm()
+        marg = state.marginals()
+        return nrm, marg
+
+    for _ in range(args.warmup):
+        nrm, marg = step()
+    if abs(nrm - 1.0) > 1e-9:
+        raise RuntimeError(f"norm drifted: {nrm}")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        ev1.synchronize()
+    barrier()
+    total_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * step_bytes / (ms_per_step / 1e3) / 1e9
+
+    # per-pass timing of the timed steps (events on the launching stream)
+    tile_idx = [i for i, p in enumerate(passes) if p["kind"] == "tile"]
+    times = np.array([plan.pass_times(r) for r in range(args.steps)])  # steps x passes
+    pass_flops = []
+    for p in passes:
+        pass_flops.append(sum(gate_cost(gates[j], n, s_bytes)[1] for j in p["gates"]))
+    tile_ms = times[:, tile_idx].sum(axis=1).mean() if tile_idx else 0.0
+    tile_launch_ms = times[:, tile_idx].mean() if tile_idx else float("nan")
+    tile_flops = sum(pass_flops[i] for i in tile_idx)
+    gates_ms = times.sum(axis=1).mean()
+    achieved_tf = tile_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
+    roofline = {"bound": "alu", "kernel": "k_tile<double> (fused tile pass)",
+                "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (no FP64 figure in MEASURED_PEAKS.json)",
+                "launches_per_step": len(tile_idx), "avg_launch_ms": tile_launch_ms,
+                "hbm_frac_of_measured": (2 * N * s_bytes / (tile_launch_ms / 1e3)) / 6794.8e9 if tile_idx else None}
+
+    launches_per_step = 1 + len(passes) + 2 + 2  # init, passes, norm (2 kernels), marginals (2 kernels)
+
+    e2e = None
+    if not args.no_e2e:
+        # public API with host buffers: pinned host state -> device, qs_run (plans inside), marginals -> host
+        host = torch.zeros(1 << n, dtype=torch.complex128 if dtype == qs.QS_C128 else torch.complex64,
+                           pin_memory=True)
+        host[x] = 1.0
+        e2e_steps = max(1, min(args.steps, 2))
+        state.copy_in_ptr(host.data_ptr(), 1 << n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            state.copy_in_ptr(host.data_ptr(), 1 << n)
+            state.run(gates)
+            res = state.marginals()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_bytes = gate_bytes + 2 * N * s_bytes  # h2d of the state + marginals read (plus gates)
+        e2e = {"value": world * e2e_bytes / e2e_s / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": int(N * s_bytes + gates.nbytes), "d2h_bytes_per_step": int(8 * n),
+               "ms_per_step": 1e3 * e2e_s, "steps": e2e_steps}
+        del host
+
+    secondary = None
+    if not args.no_secondary and rank == 0:
+        secondary = secondary_gradients(qs, dtype, torch)
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        cpu = cpu_baseline(n, gates, s_bytes)
+
+    plan.close()
+    state.close()
+    if rank == 0:
+        kinds = {}
+        for p in passes:
+            kinds[p["kind"]] = kinds.get(p["kind"], 0) + p["n_gates"]
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"QFT({n}) on random basis |x> + 1000-gate random circuit "
+                                   f"({'complex128' if dtype == qs.QS_C128 else 'complex64'}, n={n})",
+                       "n": n, "gates": len(gates), "state_bytes": int(N * s_bytes),
+                       "l2": "state larger than L2 (129 MB): no flush needed", "parallelism": f"replicas x{world}"},
+            "hbm_frac_of_measured": value / 6794.8,
+            "breakdown": {"plan_ms": plan_ms, "gates_ms": gates_ms, "tile_ms": tile_ms, "passes": len(passes),
+                          "tile_passes": len(tile_idx), "gates_in_tile_passes": kinds.get("tile", 0),
+                          "gates_in_single_passes": kinds.get("single", 0), "gate_bytes": gate_bytes,
+                          "gates_per_s": len(gates) / (gates_ms / 1e3)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(),
+            "secondary": secondary,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -157,6 +157,15 @@ QS_API qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* n_gates, 
  * of gates it commutes with (disjoint qubits, or both diagonal). */
 QS_API qs_status qs_plan_pass_gates(const qs_plan* p, int i, int* positions);
 
+/* Per-pass timing with CUDA events recorded on the state's stream around
+ * every pass: keep `records` sets of events, used round robin by successive
+ * eager executions (0 disables; not for CUDA-graph or dry-run plans). */
+QS_API qs_status qs_plan_set_timing(qs_plan* p, int records);
+
+/* Milliseconds of each pass (n_passes floats) of timing record `record`;
+ * waits for that record's last event. */
+QS_API qs_status qs_plan_pass_times(qs_plan* p, int record, float* ms);
+
 /* Free the plan; waits for the plan's launches on the state's stream first. */
 QS_API qs_status qs_plan_destroy(qs_plan* p);
 

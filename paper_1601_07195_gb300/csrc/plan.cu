@@ -50,6 +50,10 @@ struct qs_plan {
     void* d_ops = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    // optional per-pass timing: `records` sets of (passes + 1) events, used round robin
+    std::vector<cudaEvent_t> events;
+    int records = 0;
+    int next_record = 0;
 };
 
 namespace qs {
@@ -161,12 +165,15 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
     return QS_OK;
 }
 
-qs_status launch_all(qs_plan* p) {
+qs_status launch_all(qs_plan* p, cudaEvent_t* ev) {
     const bool f64 = (p->flags & QS_PLAN_ARITH_F64) != 0;
-    for (const PlanPass& pp : p->passes) {
+    for (size_t i = 0; i < p->passes.size(); ++i) {
+        const PlanPass& pp = p->passes[i];
+        if (ev) QS_CUDA_TRY(cudaEventRecord(ev[i], p->s->stream));
         qs_status st = pp.kind == 0 ? launch_op(p->s, pp.op, f64) : launch_tile_pass(p->s, p->d_ops, pp.tp, f64);
         if (st != QS_OK) return st;
     }
+    if (ev) QS_CUDA_TRY(cudaEventRecord(ev[p->passes.size()], p->s->stream));
     return QS_OK;
 }
 
@@ -212,10 +219,17 @@ qs_status qs_plan_execute(qs_plan* p) {
     if (!p || !p->s) return fail(QS_EINVAL, "plan is NULL");
     if (p->flags & QS_PLAN_DRY_RUN) return fail(QS_EINVAL, "a dry-run plan cannot be executed");
     const bool graph = (p->flags & QS_PLAN_GRAPH) && p->s->stream != nullptr;
-    if (!graph) return launch_all(p);
+    if (!graph) {
+        cudaEvent_t* ev = nullptr;
+        if (p->records > 0) {
+            ev = &p->events[(size_t)p->next_record * (p->passes.size() + 1)];
+            p->next_record = (p->next_record + 1) % p->records;
+        }
+        return launch_all(p, ev);
+    }
     if (!p->gexec) {
         QS_CUDA_TRY(cudaStreamBeginCapture(p->s->stream, cudaStreamCaptureModeThreadLocal));
-        qs_status st = launch_all(p);
+        qs_status st = launch_all(p, nullptr);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(p->s->stream, &g);
         if (st != QS_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -255,9 +269,38 @@ qs_status qs_plan_pass_gates(const qs_plan* p, int i, int* positions) {
     return QS_OK;
 }
 
+qs_status qs_plan_set_timing(qs_plan* p, int records) {
+    if (!p) return fail(QS_EINVAL, "plan is NULL");
+    if (records < 0 || records > 4096) return fail(QS_EINVAL, "records must be in [0, 4096]");
+    if (p->flags & (QS_PLAN_DRY_RUN | QS_PLAN_GRAPH)) return fail(QS_EINVAL, "timing needs an eager, executable plan");
+    if (!p->events.empty()) cudaStreamSynchronize(p->s->stream);
+    for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+    p->events.clear();
+    p->records = 0;
+    p->next_record = 0;
+    const size_t count = (size_t)records * (p->passes.size() + 1);
+    p->events.resize(count);
+    for (size_t i = 0; i < count; ++i) {
+        cudaError_t e = cudaEventCreate(&p->events[i]);
+        if (e != cudaSuccess) { p->events.resize(i); return cuda_fail(e, "cudaEventCreate"); }
+    }
+    p->records = records;
+    return QS_OK;
+}
+
+qs_status qs_plan_pass_times(qs_plan* p, int record, float* ms) {
+    if (!p || !ms) return fail(QS_EINVAL, "NULL argument");
+    if (record < 0 || record >= p->records) return fail(QS_EINVAL, "record out of range");
+    cudaEvent_t* ev = &p->events[(size_t)record * (p->passes.size() + 1)];
+    QS_CUDA_TRY(cudaEventSynchronize(ev[p->passes.size()]));
+    for (size_t i = 0; i < p->passes.size(); ++i) QS_CUDA_TRY(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+    return QS_OK;
+}
+
 qs_status qs_plan_destroy(qs_plan* p) {
     if (!p) return QS_OK;
     if (p->s && p->s->stream && !(p->flags & QS_PLAN_DRY_RUN)) cudaStreamSynchronize(p->s->stream);
+    for (cudaEvent_t e : p->events) cudaEventDestroy(e);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->d_ops) cudaFree(p->d_ops);

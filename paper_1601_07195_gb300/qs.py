@@ -57,6 +57,8 @@ _SIGS = {
     "qs_plan_pass": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                      ctypes.POINTER(ctypes.c_uint64)],
     "qs_plan_pass_gates": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "qs_plan_set_timing": [_vp, ctypes.c_int],
+    "qs_plan_pass_times": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)],
     "qs_plan_destroy": [_vp],
     "qs_run": [_vp, _vp, ctypes.c_int, _dp, ctypes.c_int],
     "qs_norm": [_vp, _dp],
@@ -182,6 +184,10 @@ class State:
         a = np.ascontiguousarray(arr, dtype=self.np_dtype)
         _check(load().qs_copy_in(self._h, off, a.size, a.ctypes.data))
 
+    def copy_in_ptr(self, host_ptr, cnt, off=0):
+        """Copy cnt amplitudes from a host address (ideally pinned) into the state."""
+        _check(load().qs_copy_in(self._h, off, cnt, ctypes.c_void_p(host_ptr)))
+
     def set_stream(self, stream):
         _check(load().qs_set_stream(self._h, _stream_handle(stream)))
 
@@ -264,6 +270,15 @@ class Plan:
             out.append({"kind": "tile" if k.value == 1 else "single", "n_gates": ng.value, "mask": mask.value,
                         "gates": list(pos[:ng.value])})
         return out
+
+    def set_timing(self, records):
+        _check(load().qs_plan_set_timing(self._h, records))
+
+    def pass_times(self, record=0):
+        n = self.stats()["passes"]
+        out = (ctypes.c_float * max(1, n))()
+        _check(load().qs_plan_pass_times(self._h, record, out))
+        return np.array(out[:n], dtype=np.float64)
 
     def close(self):
         if self._h is not None and self._h.value:

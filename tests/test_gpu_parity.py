@@ -178,7 +178,10 @@ def test_tile_sizes(qs, dt, tile_bits):
 @pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 9])
 def test_small_states_whole_state_tile(qs, dt, n):
-    gates, _ = G.random_circuit(max(n, 2), 60, 500 + n) if n >= 2 else (G.concat([G.gate_u1(0, MATS["HAAR"])] * 3), None)
+    if n >= 2:
+        gates, _ = G.random_circuit(n, 60, 500 + n)
+    else:
+        gates = G.concat([G.gate_u1(0, G.MAT_H), G.gate_u1(0, G.haar_2x2(G.SplitMix64(2))), G.gate_u1(0, G.MAT_T)])
     psi = rand_state(n, 3)
     want = O.run(expected_input(psi, dt), gates)
     with upload(qs, n, dt, psi) as s:
