@@ -187,6 +187,29 @@ QS_API qs_status qs_probs(qs_state* s, double* host_out);
 /* <psi|H|psi> for H = sum_j coef_j P_j with Z, ZZ and X terms. */
 QS_API qs_status qs_expect(qs_state* s, const qs_term* terms, int n_terms, double* out);
 
+/* All n marginals without allocating anything (the paper has no counterpart;
+ * it exists for callers that cannot allocate device memory).  Some hosts must
+ * not call cudaMalloc: an application whose own memory pool already holds the
+ * device memory, so a fresh allocation would fail or fragment it; a
+ * latency-critical loop that cannot afford the device-wide synchronisation an
+ * allocation or free can cause; plugin code whose host forbids it.  This entry
+ * point takes a caller-owned state and output and uses, for its partial sums,
+ * a static device array of 16384 doubles (128 KiB) that every GPU loading the
+ * library keeps until the process exits.
+ *   dev_state: 2^n amplitudes of dtype dt in device memory (1 <= n <= 36;
+ *              larger n returns QS_EINVAL because the static array is sized
+ *              for at most 36 qubits).
+ *   dev_out:   device buffer of n + 1 doubles: out[k] = P(qubit k = 1) for
+ *              k < n, out[n] = sum_i |alpha_i|^2.
+ * Asynchronous on cuda_stream; read dev_out after the stream has finished.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and every value
+ * they read from it is written earlier in the same call, so nothing needs
+ * clearing, but calls whose work overlaps on the GPU (other streams, other
+ * threads) race on it and must be serialised by the caller. */
+QS_API qs_status qs_marginals_noalloc(const void* dev_state, int n, qs_dtype dt, void* cuda_stream, double* dev_out);
+
 /* ---- adjoint gradients (not in the paper) --------------------------------- */
 
 /* One variational instance: E(theta) = <psi|H|psi>, psi = U_P..U_1 |0..0>. */

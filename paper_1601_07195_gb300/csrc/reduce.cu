@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "device.cuh"
 
@@ -372,3 +373,76 @@ qs_status qs_expect(qs_state* s, const qs_term* terms, int n_terms, double* out)
 }
 
 }  // extern "C"
+
+// ---- marginals without any allocation ----------------------------------------------
+// Same kernels as qs_prob(k = -1), but the per-block partial sums live in this
+// file-scope device array instead of memory from cudaMalloc.  Every loaded
+// library instance holds it on every GPU that loads the module until exit.
+namespace qs {
+namespace {
+
+constexpr int kStaticPartials = 16384;  // doubles (128 KiB)
+constexpr int kStaticMaxQubits = 36;
+static __device__ __align__(256) double g_static_partials[kStaticPartials];
+
+std::mutex g_static_mu;
+void* g_static_addr[64] = {nullptr};
+
+// Device address of g_static_partials for the current device, looked up once
+// per device (with that device current).  In host code the symbol is only a
+// host-side stand-in, so kernels must be given this address.
+qs_status static_scratch(double** out) {
+    int dev = 0;
+    QS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(QS_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_addr[dev] = p;
+    }
+    *out = (double*)g_static_addr[dev];
+    return QS_OK;
+}
+
+template <class T>
+qs_status marginals_noalloc_impl(const void* psi, int n, cudaStream_t st, double* dev_out) {
+    if (n < kChunkBits) {
+        k_marginals_small<T><<<1, kRedThreads, 0, st>>>((const T*)psi, n, dev_out);
+        QS_CUDA_TRY(cudaGetLastError());
+        return QS_OK;
+    }
+    double* scratch = nullptr;
+    if (qs_status s = static_scratch(&scratch)) return s;
+    const uint64_t chunks = 1ull << (n - kChunkBits);
+    uint64_t b = (uint64_t)sm_count() * 4;
+    const uint64_t fit = (uint64_t)kStaticPartials / (uint64_t)(n + 1);
+    if (b > fit) b = fit;
+    if (b > chunks) b = chunks;
+    const int blocks = (int)b;
+    // every partial the finalize kernel reads is written first by k_marginals, so
+    // nothing left over from an earlier call is ever read
+    k_marginals<T><<<blocks, kRedThreads, 0, st>>>((const T*)psi, n, chunks, scratch);
+    k_finalize<<<1, 64, 0, st>>>(scratch, blocks, n + 1, n + 1, dev_out);
+    QS_CUDA_TRY(cudaGetLastError());
+    return QS_OK;
+}
+
+}  // namespace
+}  // namespace qs
+
+extern "C" qs_status qs_marginals_noalloc(const void* dev_state, int n, qs_dtype dt, void* cuda_stream,
+                                          double* dev_out) {
+    using namespace qs;
+    if (!dev_state || !dev_out) return fail(QS_EINVAL, "qs_marginals_noalloc: NULL pointer");
+    if (dt != QS_C64 && dt != QS_C128) return fail(QS_EDTYPE, "qs_marginals_noalloc: unknown dtype");
+    if (n < 1 || n > kStaticMaxQubits)
+        return fail(QS_EINVAL, "qs_marginals_noalloc: n must be in [1, 36]; larger states exceed what the "
+                               "static 16384-double scratch array is sized for");
+    if ((uintptr_t)dev_state % amp_bytes(dt) != 0 || (uintptr_t)dev_out % 8 != 0)
+        return fail(QS_EINVAL, "qs_marginals_noalloc: misaligned pointer");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    return dt == QS_C128 ? marginals_noalloc_impl<double2>(dev_state, n, st, dev_out)
+                         : marginals_noalloc_impl<float2>(dev_state, n, st, dev_out);
+}

@@ -66,6 +66,7 @@ _SIGS = {
     "qs_probs": [_vp, _dp],
     "qs_expect": [_vp, _vp, ctypes.c_int, _dp],
     "qs_grad": [_vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp],
+    "qs_marginals_noalloc": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp],
 }
 
 
