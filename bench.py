@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true", help="skip the batched-gradient measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 comparison step")
     return ap.parse_args()
 
 
@@ -79,10 +80,17 @@ def gate_class(g):
 
 # FP64 flops per amplitude the class's update touches (FMA = 2 flops)
 _FLOPS = {"general": 14.0, "real": 6.0, "diag": 6.0, "diag1": 6.0, "antidiag": 6.0, "perm": 0.0}
+# FP32 flops per touched amplitude of the double-float update (csrc/df.cuh):
+# df_mul = 1 FMUL + 3 FFMA = 7 flops; TwoSum = 6; dot2 = 2 df_mul + TwoSum + 2 adds + TwoSum = 28;
+# dot4 = 4 df_mul + 3 TwoSum + 6 adds + TwoSum = 58; a complex output = 2 dots.
+_DF_FLOPS = {"general": 116.0, "real": 56.0, "diag": 56.0, "diag1": 56.0, "antidiag": 56.0, "perm": 0.0}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
-def gate_cost(g, n, s):
-    """(algorithmic bytes, FP64 flops) of one gate on a 2^n state of s-byte amplitudes."""
+def gate_cost(g, n, s, table=None):
+    """(algorithmic bytes, flops) of one gate on a 2^n state of s-byte amplitudes;
+    flops per touched amplitude from `table` (FP64 flops of the update by default)."""
+    table = _FLOPS if table is None else table
     N = float(1 << n)
     kind = int(g["kind"])
     if kind == G.G_SWAP:
@@ -90,11 +98,11 @@ def gate_cost(g, n, s):
     if kind == G.G_U1:
         c = gate_class(g)
         touched = 0.5 if c == "diag1" else 1.0
-        return (2.0 if c != "diag1" else 1.0) * N * s, _FLOPS[c] * N * touched
+        return (2.0 if c != "diag1" else 1.0) * N * s, table[c] * N * touched
     if kind == G.G_CU:
         c = gate_class(g)
         touched = 0.25 if c == "diag1" else 0.5
-        return (0.5 if c == "diag1" else 1.0) * N * s, _FLOPS[c] * N * touched
+        return (0.5 if c == "diag1" else 1.0) * N * s, table[c] * N * touched
     raise ValueError("rotation kinds are not part of this workload")
 
 
@@ -318,15 +326,46 @@ def run_ours(args):
     tile_launch_ms = times[:, tile_idx].mean() if tile_idx else float("nan")
     tile_flops = sum(pass_flops[i] for i in tile_idx)
     gates_ms = times.sum(axis=1).mean()
-    achieved_tf = tile_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
-    roofline = {"bound": "alu", "kernel": "k_tile<double> (fused tile pass)",
-                "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (no FP64 figure in MEASURED_PEAKS.json)",
+    fp64_tf = tile_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
+    df = dtype == qs.QS_C128
+    # FP32 flops of the kernel's own algorithm: double-float update for complex128, plain FP32 for complex64
+    table = _DF_FLOPS if df else _FLOPS
+    fp32_flops = sum(sum(gate_cost(gates[j], n, s_bytes, table)[1] for j in passes[i]["gates"]) for i in tile_idx)
+    achieved_tf = fp32_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
+    roofline = {"bound": "alu", "kernel": "k_tile_df (fused tile pass, double-float)" if df else "k_tile<float>",
+                "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; MEASURED_PEAKS.json "
+                               "has no FP32 figure (an FFMA probe on this GPU measured 74.2 TFLOP/s)",
+                "flops_counted": "FP32 flops of the double-float update per touched amplitude: general 116, "
+                                 "real/diagonal/anti-diagonal 56, permutation 0" if df else "FP32 flops of the update",
+                "fp64_equivalent_tflops": fp64_tf,
+                "fp64_equivalent_frac_of_fp64_peak": fp64_tf / FP64_PEAK_TFLOPS,
                 "launches_per_step": len(tile_idx), "avg_launch_ms": tile_launch_ms,
                 "hbm_frac_of_measured": (2 * N * s_bytes / (tile_launch_ms / 1e3)) / 6794.8e9 if tile_idx else None}
 
     launches_per_step = 1 + len(passes) + 2 + 2  # init, passes, norm (2 kernels), marginals (2 kernels)
+
+    native = None
+    if dtype == qs.QS_C128 and not args.no_native:
+        # the same step with native FP64 instructions for the gate arithmetic (1 warm-up, 1 timed)
+        pn = state.plan(gates, flags=qs.PLAN_ARITH_F64)
+        state.init_basis(x)
+        pn.execute()
+        state.norm()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        state.init_basis(x)
+        pn.execute()
+        state.norm()
+        state.marginals()
+        e1.record(stream)
+        e1.synchronize()
+        nms = e0.elapsed_time(e1)
+        native = {"value": world * step_bytes / (nms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": nms,
+                  "dtype": "f64", "note": "same step, plan flag QS_PLAN_ARITH_F64 (FP64 pipe)"}
+        pn.close()
 
     e2e = None
     if not args.no_e2e:
@@ -367,11 +406,14 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32x2" if dtype == qs.QS_C128 else "f32", "data": "synthetic",
             "config": {"workload": f"QFT({n}) on random basis |x> + 1000-gate random circuit "
                                    f"({'complex128' if dtype == qs.QS_C128 else 'complex64'}, n={n})",
                        "n": n, "gates": len(gates), "state_bytes": int(N * s_bytes),
-                       "l2": "state larger than L2 (129 MB): no flush needed", "parallelism": f"replicas x{world}"},
+                       "l2": "state larger than L2 (129 MB): no flush needed", "parallelism": f"replicas x{world}",
+                       "arith": ("complex128 state in IEEE double; gate arithmetic in double-float (FP32 pairs, "
+                                 "error-free transforms); native FP64 in native_f64")
+                       if dtype == qs.QS_C128 else "complex64 state, FP32 arithmetic, FP64 reductions"},
             "hbm_frac_of_measured": value / 6794.8,
             "breakdown": {"plan_ms": plan_ms, "gates_ms": gates_ms, "tile_ms": tile_ms, "passes": len(passes),
                           "tile_passes": len(tile_idx), "gates_in_tile_passes": kinds.get("tile", 0),
@@ -383,6 +425,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(),
             "secondary": secondary,
+            "native_f64": native,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

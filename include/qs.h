@@ -129,7 +129,13 @@ enum {
     QS_PLAN_DEFAULT = 0,
     QS_PLAN_NO_FUSION = 1,  /* one pass over the state per gate (no tiles) */
     QS_PLAN_GRAPH = 2,      /* capture the launches once and replay a CUDA graph */
-    QS_PLAN_ARITH_F64 = 4,  /* complex128: native FP64 arithmetic in every kernel */
+    QS_PLAN_ARITH_F64 = 4,  /* complex128: native FP64 instructions for the gate arithmetic.
+                               Without it, fused tile passes of complex128 states compute in
+                               double-float form on the FP32 pipes (each double carried as an
+                               unevaluated float pair of about 48 bits; storage stays IEEE
+                               double): faster on GPUs whose FP64 rate is a small fraction of
+                               FP32, with a per-gate error of order 2^-44 relative to the
+                               amplitudes involved instead of 2^-53. */
     QS_PLAN_DRY_RUN = 8     /* plan on the host only (no device memory); cannot execute */
 };
 

@@ -1,0 +1,141 @@
+// df.cuh -- double-float ("DF") arithmetic for complex128 gate updates.
+//
+// On GB300 the FP64 pipe runs at 1/64 of the FP32 rate, so a complex128 gate
+// evaluated with FP64 instructions is bound by that pipe long before HBM.  DF
+// arithmetic carries each double as an unevaluated pair hi + lo of floats and
+// builds every product and sum from error-free transformations on the FP32
+// pipes:
+//   TwoProd  (p, e) = (a*b, fma(a, b, -a*b))        exact: a*b = p + e
+//   TwoSum   (s, e) = Knuth's branch-free sum         exact: a + b = s + e
+// (T. J. Dekker, "A floating-point technique for extending the available
+// precision", Numer. Math. 18, 1971; D. E. Knuth, TAOCP vol. 2, 4.2.2.)
+//
+// A pair holds about 48 significant bits.  Storage in HBM stays IEEE double:
+// the split at load is exact bit manipulation (no FP64 instruction), and the
+// recombination at store is a single FP64 addition, rounded to nearest.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qs {
+
+struct dfl { float h, l; };
+
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+// Product of a DF constant (qh, ql) and a DF value (xh, xl), left unnormalised:
+// the exact product qh*xh split by TwoProd, plus the two cross terms; the term
+// ql*xl (relative size 2^-48) is dropped.
+__device__ __forceinline__ dfl df_mul(float qh, float ql, float xh, float xl) {
+    const float ph = qh * xh;
+    float pl = fmaf(qh, xh, -ph);
+    pl = fmaf(qh, xl, pl);
+    pl = fmaf(ql, xh, pl);
+    return {ph, pl};
+}
+
+// sum of two unnormalised products, normalised
+__device__ __forceinline__ dfl df_dot2(dfl a, dfl b) {
+    const dfl s = two_sum(a.h, b.h);
+    return two_sum(s.h, s.l + (a.l + b.l));
+}
+
+// sum of four unnormalised products, normalised
+__device__ __forceinline__ dfl df_dot4(dfl a, dfl b, dfl c, dfl d) {
+    dfl s = two_sum(a.h, b.h);
+    float lo = s.l + (a.l + b.l);
+    s = two_sum(s.h, c.h);
+    lo += s.l + c.l;
+    s = two_sum(s.h, d.h);
+    lo += s.l + d.l;
+    return two_sum(s.h, lo);
+}
+
+// Exact split of a double into hi = its leading 24 significant bits and lo =
+// the next 24 bits (truncated; the dropped tail is below 2^-47 of |x|), built
+// from the IEEE bit fields with integer instructions only.  |x| < 2^-126 is
+// flushed to zero (an absolute change below 1.2e-38); |x| >= 2^128 saturates
+// to an infinity (not reachable from a normalised state).
+__device__ __forceinline__ dfl split_double(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+    const unsigned sign = hw & 0x80000000u;
+    const int e = (int)((hw >> 20) & 0x7FFu);
+    const int e32 = e - 1023 + 127;
+    if (e32 <= 0) return {__int_as_float((int)sign), __int_as_float((int)sign)};
+    if (e32 >= 255) return {__int_as_float((int)(sign | 0x7F800000u)), 0.0f};
+    const unsigned top23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    const float hi = __int_as_float((int)(sign | ((unsigned)e32 << 23) | top23));
+    const unsigned rem = lw & 0x1FFFFFFFu;  // 29 bits, weight 2^(e-1023-52)
+    if (rem == 0u) return {hi, __int_as_float((int)sign)};
+    const int p = 31 - __clz((int)rem);      // 0..28
+    const int elo = e - 1023 - 52 + p + 127;
+    if (elo <= 0) return {hi, __int_as_float((int)sign)};
+    const unsigned m = (p >= 23 ? (rem >> (p - 23)) : (rem << (23 - p))) & 0x7FFFFFu;
+    return {hi, __int_as_float((int)(sign | ((unsigned)elo << 23) | m))};
+}
+
+// float -> double by the bit fields (exact; no FP64 instruction).  Zero and
+// normal floats only (DF parts are never subnormal: see split_double).
+__device__ __forceinline__ double float_to_double_bits(float f) {
+    const unsigned u = (unsigned)__float_as_int(f);
+    const unsigned sign = u & 0x80000000u;
+    const unsigned ef = (u >> 23) & 0xFFu;
+    if (ef == 0u) return __longlong_as_double((long long)((unsigned long long)sign << 32));
+    if (ef == 0xFFu) return __longlong_as_double((long long)(((unsigned long long)(sign | 0x7FF00000u)) << 32));
+    const unsigned long long ed = (unsigned long long)(ef - 127 + 1023);
+    const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+    return __longlong_as_double((long long)(((unsigned long long)sign << 32) | (ed << 52) | m));
+}
+
+// hi + lo rounded to the nearest double (one FP64 addition).
+__device__ __forceinline__ double join_double(dfl v) {
+    return float_to_double_bits(v.h) + float_to_double_bits(v.l);
+}
+
+// ---- complex DF values: float4 (re.h, re.l, im.h, im.l) ---------------------
+
+__device__ __forceinline__ float4 df_load(double2 a) {
+    const dfl r = split_double(a.x), i = split_double(a.y);
+    return make_float4(r.h, r.l, i.h, i.l);
+}
+__device__ __forceinline__ double2 df_store(float4 v) {
+    return make_double2(join_double({v.x, v.y}), join_double({v.z, v.w}));
+}
+
+// Gate constants: 8 doubles (q11r, q11i, q12r, q12i, q21r, q21i, q22r, q22i),
+// each as (hi, lo) floats: c[2j] = hi, c[2j+1] = lo of double j.
+#define QH(j) c[2 * (j)]
+#define QL(j) c[2 * (j) + 1]
+
+// q * x for complex DF constant q = double pair (jr, ji) and complex DF value x
+__device__ __forceinline__ float4 df_cmul(const float* c, int jr, int ji, float4 x) {
+    const dfl re = df_dot2(df_mul(QH(jr), QL(jr), x.x, x.y), df_mul(-QH(ji), -QL(ji), x.z, x.w));
+    const dfl im = df_dot2(df_mul(QH(jr), QL(jr), x.z, x.w), df_mul(QH(ji), QL(ji), x.x, x.y));
+    return make_float4(re.h, re.l, im.h, im.l);
+}
+// p * a + q * b, p = pair (pr, pi), q = pair (qr, qi)
+__device__ __forceinline__ float4 df_cmul2(const float* c, int pr, int pi, float4 a, int qr, int qi, float4 b) {
+    const dfl re = df_dot4(df_mul(QH(pr), QL(pr), a.x, a.y), df_mul(-QH(pi), -QL(pi), a.z, a.w),
+                           df_mul(QH(qr), QL(qr), b.x, b.y), df_mul(-QH(qi), -QL(qi), b.z, b.w));
+    const dfl im = df_dot4(df_mul(QH(pr), QL(pr), a.z, a.w), df_mul(QH(pi), QL(pi), a.x, a.y),
+                           df_mul(QH(qr), QL(qr), b.z, b.w), df_mul(QH(qi), QL(qi), b.x, b.y));
+    return make_float4(re.h, re.l, im.h, im.l);
+}
+// real p, q: p * a + q * b
+__device__ __forceinline__ float4 df_rmul2(const float* c, int p, float4 a, int q, float4 b) {
+    const dfl re = df_dot2(df_mul(QH(p), QL(p), a.x, a.y), df_mul(QH(q), QL(q), b.x, b.y));
+    const dfl im = df_dot2(df_mul(QH(p), QL(p), a.z, a.w), df_mul(QH(q), QL(q), b.z, b.w));
+    return make_float4(re.h, re.l, im.h, im.l);
+}
+
+#undef QH
+#undef QL
+
+}  // namespace qs

@@ -16,6 +16,7 @@
 // rounding) as applying the gates one at a time.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "device.cuh"
 
@@ -30,6 +31,7 @@ struct PlanPass {
     TilePass tp;     // tile pass
     uint64_t mask;   // tile qubits (tile pass) or the gate's qubits
     int n_gates;
+    bool moves_only; // every gate is a permutation (X, CNOT, SWAP): run bit-exact on doubles
     std::vector<int> members;  // circuit positions of the pass's gates, in execution order
 };
 
@@ -48,6 +50,7 @@ struct qs_plan {
     int flags = 0;
     std::vector<qs::PlanPass> passes;
     void* d_ops = nullptr;
+    void* d_ops_f64 = nullptr;  // complex128 double-float plans: TileOp<double> copy for moves-only passes
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     // optional per-pass timing: `records` sets of (passes + 1) events, used round robin
@@ -59,26 +62,56 @@ struct qs_plan {
 namespace qs {
 namespace {
 
-template <class R>
-TileOp<R> to_tile_op(const Op& o, const int* bit_of) {
-    TileOp<R> t{};
+template <class OpT>
+void fill_common(OpT& t, const Op& o, const int* bit_of) {
     t.kind = o.kind;
     t.cls = o.cls;
     t.tq = o.t;
     t.tb = bit_of[o.t];
     t.cq = o.c;
     t.cb = o.c >= 0 ? bit_of[o.c] : -1;
-    for (int j = 0; j < 8; ++j) t.m[j] = (R)o.m[j];
+}
+
+template <class OpT> OpT to_tile_op(const Op& o, const int* bit_of);
+
+template <> TileOp<double> to_tile_op<TileOp<double>>(const Op& o, const int* bit_of) {
+    TileOp<double> t{};
+    fill_common(t, o, bit_of);
+    for (int j = 0; j < 8; ++j) t.m[j] = o.m[j];
+    return t;
+}
+template <> TileOp<float> to_tile_op<TileOp<float>>(const Op& o, const int* bit_of) {
+    TileOp<float> t{};
+    fill_common(t, o, bit_of);
+    for (int j = 0; j < 8; ++j) t.m[j] = (float)o.m[j];
+    return t;
+}
+template <> TileOpDF to_tile_op<TileOpDF>(const Op& o, const int* bit_of) {
+    TileOpDF t{};
+    fill_common(t, o, bit_of);
+    for (int j = 0; j < 8; ++j) split_to_floats(o.m[j], t.c[2 * j], t.c[2 * j + 1]);
     return t;
 }
 
-template <class R>
+template <class OpT>
+qs_status upload_ops(const std::vector<OpT>& v, void** dst) {
+    if (v.empty()) return QS_OK;
+    const size_t bytes = v.size() * sizeof(OpT);
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); *dst = nullptr; return fail(QS_ENOMEM, "plan: cudaMalloc of tile ops failed"); }
+    QS_CUDA_TRY(cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice));
+    return QS_OK;
+}
+
+template <class OpT>
 qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse, bool upload) {
     const int n = p->s->n;
     b = std::min(b, n);
     b0 = std::min(b0, b);
     const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
-    std::vector<TileOp<R>> tops;
+    std::vector<OpT> tops;
+    std::vector<TileOp<double>> t64;  // parallel records for moves-only passes of double-float plans
+    const bool df = std::is_same<OpT, TileOpDF>::value;
     std::vector<char> taken(ops.size(), 0);
     size_t first = 0;
     while (first < ops.size()) {
@@ -151,16 +184,19 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
         }
         tp.op0 = (int)tops.size();
         tp.nops = (int)mem.size();
-        for (int j : mem) tops.push_back(to_tile_op<R>(ops[j], bit_of));
+        pp.moves_only = true;
+        for (int j : mem) {
+            tops.push_back(to_tile_op<OpT>(ops[j], bit_of));
+            if (df) t64.push_back(to_tile_op<TileOp<double>>(ops[j], bit_of));
+            if (!(ops[j].kind == OP_SWAP || ops[j].cls == GC_PERM)) pp.moves_only = false;
+        }
         pp.kind = 1;
         pp.mask = T;
         p->passes.push_back(pp);
     }
-    if (upload && !tops.empty()) {
-        const size_t bytes = tops.size() * sizeof(TileOp<R>);
-        cudaError_t e = cudaMalloc(&p->d_ops, bytes);
-        if (e != cudaSuccess) { cudaGetLastError(); return fail(QS_ENOMEM, "plan: cudaMalloc of tile ops failed"); }
-        QS_CUDA_TRY(cudaMemcpy(p->d_ops, tops.data(), bytes, cudaMemcpyHostToDevice));
+    if (upload) {
+        if (qs_status st = upload_ops(tops, &p->d_ops)) return st;
+        if (qs_status st = upload_ops(t64, &p->d_ops_f64)) return st;
     }
     return QS_OK;
 }
@@ -170,7 +206,10 @@ qs_status launch_all(qs_plan* p, cudaEvent_t* ev) {
     for (size_t i = 0; i < p->passes.size(); ++i) {
         const PlanPass& pp = p->passes[i];
         if (ev) QS_CUDA_TRY(cudaEventRecord(ev[i], p->s->stream));
-        qs_status st = pp.kind == 0 ? launch_op(p->s, pp.op, f64) : launch_tile_pass(p->s, p->d_ops, pp.tp, f64);
+        qs_status st;
+        if (pp.kind == 0) st = launch_op(p->s, pp.op, f64);
+        else if (p->d_ops_f64 && pp.moves_only) st = launch_tile_pass(p->s, p->d_ops_f64, pp.tp, true);
+        else st = launch_tile_pass(p->s, p->d_ops, pp.tp, f64);
         if (st != QS_OK) return st;
     }
     if (ev) QS_CUDA_TRY(cudaEventRecord(ev[p->passes.size()], p->s->stream));
@@ -206,7 +245,10 @@ qs_status qs_plan_create(qs_state* s, const qs_gate* gates, int n_gates, const d
     p->flags = flags;
     const bool fuse = !(flags & QS_PLAN_NO_FUSION);
     const bool upload = !(flags & QS_PLAN_DRY_RUN);
-    qs_status st = s->dt == QS_C128 ? build<double>(p, ops, b, b0, fuse, upload) : build<float>(p, ops, b, b0, fuse, upload);
+    qs_status st;
+    if (s->dt == QS_C64) st = build<TileOp<float>>(p, ops, b, b0, fuse, upload);
+    else if (flags & QS_PLAN_ARITH_F64) st = build<TileOp<double>>(p, ops, b, b0, fuse, upload);
+    else st = build<TileOpDF>(p, ops, b, b0, fuse, upload);
     if (st != QS_OK) {
         qs_plan_destroy(p);
         return st;
@@ -304,6 +346,7 @@ qs_status qs_plan_destroy(qs_plan* p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->d_ops) cudaFree(p->d_ops);
+    if (p->d_ops_f64) cudaFree(p->d_ops_f64);
     delete p;
     return QS_OK;
 }

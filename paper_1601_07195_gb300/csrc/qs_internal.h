@@ -51,6 +51,13 @@ struct TileOp {
     R m[8];
 };
 
+// A tile-pass gate for complex128 states evaluated in double-float arithmetic:
+// c[2j], c[2j+1] = (hi, lo) floats of matrix double j (q11r, q11i, ..., q22i).
+struct TileOpDF {
+    int32_t kind, cls, tb, tq, cb, cq, pad0, pad1;
+    float c[16];
+};
+
 constexpr int kMaxTileBits = 14;
 
 // Kernel argument describing one tile pass (by value).
@@ -104,8 +111,11 @@ qs_status lower_gates(const qs_gate* g, int ng, const double* theta, int np, int
 // Single-gate launchers (gates.cu).
 qs_status launch_op(qs_state* s, const Op& op, bool arith_f64);
 
-// Tile pass launcher (tile.cu).
+// Tile pass launcher (tile.cu); complex128 without arith_f64 goes to the
+// double-float kernel (tile_df.cu), whose op array holds TileOpDF records.
 qs_status launch_tile_pass(qs_state* s, const void* d_ops, const TilePass& pass, bool arith_f64);
+cudaError_t launch_tile_df(qs_state* s, const void* d_ops, const TilePass& pass);
+void split_to_floats(double x, float& hi, float& lo);
 size_t tile_smem_bytes(qs_dtype dt, int b);
 
 // Reductions (reduce.cu).

@@ -169,10 +169,13 @@ cudaError_t launch_tile(qs_state* s, const void* d_ops, const TilePass& P) {
 
 size_t tile_smem_bytes(qs_dtype dt, int b) { return amp_bytes(dt) << b; }
 
-qs_status launch_tile_pass(qs_state* s, const void* d_ops, const TilePass& pass, bool /*arith_f64*/) {
+qs_status launch_tile_pass(qs_state* s, const void* d_ops, const TilePass& pass, bool arith_f64) {
     if (tile_smem_bytes(s->dt, pass.b) + ((size_t)8 << (pass.b - pass.b0)) > smem_optin())
         return fail(QS_EINVAL, "tile does not fit in shared memory");
-    cudaError_t e = (s->dt == QS_C128) ? launch_tile<double>(s, d_ops, pass) : launch_tile<float>(s, d_ops, pass);
+    cudaError_t e;
+    if (s->dt == QS_C64) e = launch_tile<float>(s, d_ops, pass);
+    else if (arith_f64) e = launch_tile<double>(s, d_ops, pass);
+    else e = launch_tile_df(s, d_ops, pass);
     if (e != cudaSuccess) return cuda_fail(e, "tile kernel launch");
     return QS_OK;
 }

@@ -310,3 +310,37 @@ def test_invalid_arguments_on_live_state(qs):
             s.run(G.gate_rot(G.G_RY, 0, 0))  # no angles
         s.apply_1q(0, MATS["H"])  # the state is still usable
         assert abs(s.norm() - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("arith", ["df", "f64"])
+@pytest.mark.parametrize("tile_bits", [0, 7])
+def test_c128_arithmetic_modes_deep_circuit(qs, arith, tile_bits):
+    """complex128 tile passes in double-float (default) and native-FP64 arithmetic
+    against the oracle on a deep circuit (4000 random gates + QFT, n = 14)."""
+    n = 14
+    gates = G.concat([G.random_circuit(n, 4000, 19)[0], G.qft_circuit(n)])
+    psi = rand_state(n, 21)
+    want = O.run(psi.copy(), gates)
+    flags = qs.PLAN_DEFAULT if arith == "df" else qs.PLAN_ARITH_F64
+    with upload(qs, n, 1, psi) as s:
+        p = s.plan(gates, flags=flags, tile_bits=tile_bits)
+        p.execute()
+        got = s.to_numpy()
+        p.close()
+    err = float(np.max(np.abs(got - want)))
+    print(f"deep circuit n={n} {len(gates)} gates arith={arith} tile_bits={tile_bits}: max-abs error {err:.3e}")
+    assert err < TOL[1]
+
+
+def test_c128_df_error_at_n22_random(qs):
+    """The n=20-style random circuit at n=22 with 600 gates: double-float error
+    stays orders of magnitude inside the 1e-12 complex128 tolerance."""
+    n = 22
+    gates, _ = G.random_circuit(n, 600, 4242)
+    want = O.simulate(n, gates)
+    with qs.State.create(n, 1) as s:
+        s.run(gates)
+        got = s.to_numpy()
+    err = float(np.max(np.abs(got - want)))
+    print(f"n={n} 600 gates double-float max-abs error {err:.3e}")
+    assert err < 1e-13
