@@ -229,7 +229,40 @@ typedef struct {
     const qs_term* terms;
 } qs_instance;
 
-/* Energies and gradients dE/dtheta of a batch of instances by one adjoint
+/* A reusable batch: the instances' circuits and observables are copied and
+ * planned once, device buffers are allocated once, and the first execution
+ * captures every launch (and the upload of the gate matrices for the current
+ * angles) into a CUDA graph that later executions replay.
+ *   - Instances small enough to hold phi and lambda in one CTA's shared
+ *     memory (n <= 12 for complex128, n <= 13 for complex64 on GB300) run in
+ *     one persistent kernel, one CTA per instance taken from a work counter.
+ *   - Larger instances with identical circuit structure (gate kinds, qubits,
+ *     parameter indices, observable terms) form a group that runs as batched
+ *     tile passes: forward passes, lambda = H psi, the energy, then reverse
+ *     tile passes holding phi and lambda together.
+ * flags: 1 = launch directly instead of capturing a graph.
+ * The caller's stream must not be capturing; NULL gives the batch its own
+ * non-blocking stream.  Angles passed at creation are used until an
+ * execution passes new ones. */
+typedef struct qs_batch qs_batch;
+QS_API qs_status qs_batch_create(const qs_instance* batch, int n_inst, qs_dtype dt, void* cuda_stream, int flags,
+                                 qs_batch** out);
+
+/* Run the batch.  theta_all: the instances' angles concatenated in instance
+ * order (sum of n_params doubles), or NULL for the last angles used.
+ * energies: n_inst host doubles; grads: concatenated host gradients.
+ * Synchronises the batch's stream. */
+QS_API qs_status qs_batch_execute(qs_batch* b, const double* theta_all, double* energies, double* grads);
+
+/* How the batch runs: instances in the persistent small-instance kernel,
+ * number of structure groups, and kernel launches per execution. */
+QS_API qs_status qs_batch_stats(const qs_batch* b, int* n_small, int* n_groups, int* n_launches);
+
+QS_API qs_status qs_batch_destroy(qs_batch* b);
+
+/* One-shot form of qs_batch_create / qs_batch_execute / qs_batch_destroy
+ * (without graph capture).
+ * Energies and gradients dE/dtheta of a batch of instances by one adjoint
  * reverse sweep each (Jones & Gacon, arXiv:2009.02823).  energies[i] gets
  * instance i's energy; grads gets the instances' gradients concatenated in
  * order (sum of n_params doubles).  Both are host buffers.  dt selects the

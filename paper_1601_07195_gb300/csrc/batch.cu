@@ -1,0 +1,1059 @@
+// batch.cu -- energies and adjoint gradients of many variational circuits at
+// once (qs_batch_*, qs_grad).  Not in the paper.
+//
+// Adjoint differentiation (T. Jones and J. Gacon, arXiv:2009.02823): for
+// psi = U_P .. U_1 |0..0> and rotations U_j = exp(-i theta_j G_j / 2),
+//   lambda = H psi,  E = Re <psi|lambda>,  phi = psi,
+//   for j = P .. 1:  if U_j is a rotation, dE/dtheta_j += Im <lambda| G_j |phi>;
+//                    phi <- U_j^dagger phi,  lambda <- U_j^dagger lambda.
+// A gate may be swept past gates it commutes with (disjoint qubits, or both
+// diagonal): such a gate U_k also commutes with G_j, so Im <lambda|G_j|phi> is
+// unchanged when U_k^dagger has (or has not yet) been applied to both states.
+//
+// Work split:
+//   * small instances (phi and lambda fit in one CTA's shared memory) run in
+//     one persistent kernel: each CTA takes instances from an atomic work
+//     counter and does the forward pass, lambda, E and the whole reverse sweep
+//     in shared memory, with block-level FP64 reductions;
+//   * larger instances are grouped by identical circuit structure; each group
+//     runs batched tile passes (grid.y = instances): forward passes on psi,
+//     then reverse tile passes that hold phi and lambda tiles together and
+//     write one FP64 partial per rotation gate and tile, summed in fixed order.
+// All launches (and the upload of the gate matrices for the current angles)
+// are captured once into a CUDA graph and replayed by qs_batch_execute.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "device.cuh"
+#include "tile_ops.cuh"
+
+namespace qs {
+namespace {
+
+constexpr int kAdjThreads = 256;
+constexpr int kSmallThreads = 512;
+constexpr int kRedThreadsB = 256;
+constexpr int kMaxCrossB = 64;
+constexpr int kMaxXB = 64;
+
+__device__ __forceinline__ double warp_sum_b(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// Sum over the block, valid in thread 0; barriers on entry and exit keep `red` reusable.
+__device__ __forceinline__ double block_sum_b(double v, double* red) {
+    v = warp_sum_b(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        r = warp_sum_b(r);
+    }
+    return r;
+}
+
+template <class T> __device__ __forceinline__ double im_cb(const T& a, const T& b) {
+    return fma((double)a.x, (double)b.y, -(double)a.y * (double)b.x);
+}
+template <class T> __device__ __forceinline__ double re_cb(const T& a, const T& b) {
+    return fma((double)a.x, (double)b.x, (double)a.y * (double)b.y);
+}
+
+// Im of <lambda| G |phi> restricted to one pair; gen 1 = X, 2 = Y, 3 = Z.
+template <class T>
+__device__ __forceinline__ double gen_term(int gen, const T& f0, const T& f1, const T& l0, const T& l1) {
+    if (gen == 1) return im_cb(l0, f1) + im_cb(l1, f0);
+    if (gen == 2) return re_cb(l1, f0) - re_cb(l0, f1);
+    return im_cb(l0, f0) - im_cb(l1, f1);
+}
+
+// ---- one reversed op on (phi, lambda) tiles ------------------------------------
+// op.pad0 = generator (0 = not a rotation), op.pad1 = output slot.
+template <class R, int CLS, int THREADS>
+__device__ __forceinline__ double adj_pairs(typename Amp<R>::T* f, typename Amp<R>::T* l, uint32_t N, int cb, int tb,
+                                            const R* m, int gen) {
+    using T = typename Amp<R>::T;
+    double acc = 0.0;
+    if (cb < 0) {
+        for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
+            const uint32_t i0 = insert_zero32(p, tb), i1 = i0 | (1u << tb);
+            T f0 = f[i0], f1 = f[i1], l0 = l[i0], l1 = l[i1];
+            if (gen) acc += gen_term(gen, f0, f1, l0, l1);
+            pair_update<CLS>(m, f0, f1);
+            pair_update<CLS>(m, l0, l1);
+            f[i0] = f0; f[i1] = f1; l[i0] = l0; l[i1] = l1;
+        }
+    } else {
+        const int lo = min(cb, tb), hi = max(cb, tb);
+        for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
+            const uint32_t i0 = insert_two_zeros32(p, lo, hi) | (1u << cb), i1 = i0 | (1u << tb);
+            T f0 = f[i0], f1 = f[i1], l0 = l[i0], l1 = l[i1];
+            if (gen) acc += gen_term(gen, f0, f1, l0, l1);
+            pair_update<CLS>(m, f0, f1);
+            pair_update<CLS>(m, l0, l1);
+            f[i0] = f0; f[i1] = f1; l[i0] = l0; l[i1] = l1;
+        }
+    }
+    return acc;
+}
+
+template <class R, int THREADS>
+__device__ __forceinline__ void adj_apply(typename Amp<R>::T* f, typename Amp<R>::T* l, uint32_t N, const TileOp<R>& op,
+                                          uint64_t base, double* red, double* out) {
+    using T = typename Amp<R>::T;
+    const int gen = op.pad0;
+    double acc = 0.0;
+    bool active = true;
+    int cb = -1;
+    if (op.kind == OP_SWAP) {
+        const int lo = min(op.tb, op.cb), hi = max(op.tb, op.cb);
+        for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
+            const uint32_t i = insert_two_zeros32(p, lo, hi), a = i | (1u << op.tb), b = i | (1u << op.cb);
+            const T x = f[a]; f[a] = f[b]; f[b] = x;
+            const T y = l[a]; l[a] = l[b]; l[b] = y;
+        }
+        active = false;
+    } else if (op.kind == OP_CU) {
+        if (op.cb < 0) active = ((base >> op.cq) & 1ull) != 0;
+        else cb = op.cb;
+    }
+    if (active && op.kind != OP_SWAP) {
+        if (op.tb < 0) {  // diagonal with its target outside the tile: one factor per (half-)tile
+            const bool bit = (base >> op.tq) & 1ull;
+            const R fr = bit ? op.m[6] : op.m[0], fi = bit ? op.m[7] : op.m[1];
+            const bool skip = op.cls == GC_DIAG1 && !bit;
+            if (cb < 0) {
+                for (uint32_t e = threadIdx.x; e < N; e += THREADS) {
+                    if (gen) acc += im_cb(l[e], f[e]);
+                    if (!skip) { f[e] = cmul(fr, fi, f[e]); l[e] = cmul(fr, fi, l[e]); }
+                }
+            } else {
+                for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
+                    const uint32_t e = insert_zero32(p, cb) | (1u << cb);
+                    if (gen) acc += im_cb(l[e], f[e]);
+                    if (!skip) { f[e] = cmul(fr, fi, f[e]); l[e] = cmul(fr, fi, l[e]); }
+                }
+            }
+            if (bit) acc = -acc;  // Z eigenvalue of the target bit (only Z rotations are diagonal)
+        } else {
+            switch (op.cls) {
+            case GC_GENERAL: acc = adj_pairs<R, GC_GENERAL, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
+            case GC_REAL: acc = adj_pairs<R, GC_REAL, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
+            case GC_DIAG: acc = adj_pairs<R, GC_DIAG, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
+            case GC_DIAG1: acc = adj_pairs<R, GC_DIAG1, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
+            case GC_ANTIDIAG: acc = adj_pairs<R, GC_ANTIDIAG, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
+            default: acc = adj_pairs<R, GC_PERM, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
+            }
+        }
+    }
+    if (gen) {  // uniform over the CTA: every thread takes part in the reduction
+        const double s = block_sum_b(active ? acc : 0.0, red);
+        if (threadIdx.x == 0) out[op.pad1] = s;
+    }
+}
+
+// ---- reverse tile pass over a group of instances --------------------------------
+template <class R>
+__global__ void __launch_bounds__(kAdjThreads) k_tile_adj(typename Amp<R>::T* __restrict__ phi,
+                                                          typename Amp<R>::T* __restrict__ lam,
+                                                          const TileOp<R>* __restrict__ ops, TilePass P,
+                                                          double* __restrict__ partials, int n_slots) {
+    using T = typename Amp<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    const int b = P.b, b0 = P.b0, nh = b - b0;
+    const uint32_t N = 1u << b;
+    T* f = reinterpret_cast<T*>(smem_raw);
+    T* l = f + N;
+    uint64_t* hioff = reinterpret_cast<uint64_t*>(l + N);
+    phi += (uint64_t)blockIdx.y * P.inst_stride;
+    lam += (uint64_t)blockIdx.y * P.inst_stride;
+    ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride;
+    double* out = partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * n_slots;
+    const uint64_t base = deposit_bits((uint64_t)blockIdx.x, P.nontile_mask);
+    for (uint32_t h = threadIdx.x; h < (1u << nh); h += kAdjThreads) {
+        uint64_t off = 0;
+        for (int j = 0; j < nh; ++j)
+            if ((h >> j) & 1u) off |= 1ull << P.hi_q[j];
+        hioff[h] = off;
+    }
+    __syncthreads();
+    const uint32_t lomask = (1u << b0) - 1u;
+    for (uint32_t e = threadIdx.x; e < N; e += kAdjThreads) {
+        const uint64_t g = base + hioff[e >> b0] + (e & lomask);
+        f[e] = phi[g];
+        l[e] = lam[g];
+    }
+    __syncthreads();
+    for (int g = 0; g < P.nops; ++g) {
+        const TileOp<R> op = ops[P.op0 + g];
+        adj_apply<R, kAdjThreads>(f, l, N, op, base, red, out);
+        __syncthreads();
+    }
+    for (uint32_t e = threadIdx.x; e < N; e += kAdjThreads) {
+        const uint64_t g = base + hioff[e >> b0] + (e & lomask);
+        phi[g] = f[e];
+        lam[g] = l[e];
+    }
+}
+
+// rot_vals[inst * n_rot + slot_rot[s]] = sum over tiles of partials[inst][tile][s]
+__global__ void k_adj_finalize(const double* __restrict__ partials, int n_tiles, int n_slots, int count,
+                               const int* __restrict__ slot_rot, double* __restrict__ rot_vals, int n_rot) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count * n_slots) return;
+    const int inst = k / n_slots, s = k % n_slots;
+    const int r = slot_rot[s];
+    if (r < 0) return;
+    double acc = 0.0;
+    for (int t = 0; t < n_tiles; ++t) acc += partials[((size_t)inst * n_tiles + t) * n_slots + s];
+    rot_vals[(size_t)inst * n_rot + r] = acc;
+}
+
+// ---- lambda = H psi and E = Re <psi|lambda> for a group --------------------------
+struct HGroup {
+    int lo_bits;
+    int tab_stride;            // doubles per instance: lo table then hi table
+    int n_cross, n_x;          // per instance (same structure within the group)
+};
+
+template <class T>
+__global__ void k_apply_h_b(const T* __restrict__ psi, T* __restrict__ lam, uint64_t N, HGroup H,
+                            const double* __restrict__ tabs, const int* __restrict__ cross_q,
+                            const double* __restrict__ cross_c, const int* __restrict__ x_q,
+                            const double* __restrict__ x_c) {
+    const uint64_t inst = blockIdx.y;
+    psi += inst * N;
+    lam += inst * N;
+    const double* lo_tab = tabs + inst * (uint64_t)H.tab_stride;
+    const double* hi_tab = lo_tab + (1ull << H.lo_bits);
+    cross_c += inst * H.n_cross;
+    x_c += inst * H.n_x;
+    const uint64_t lo_mask = (1ull << H.lo_bits) - 1ull;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        double e = lo_tab[i & lo_mask] + hi_tab[i >> H.lo_bits];
+        for (int k = 0; k < H.n_cross; ++k) {
+            const uint64_t par = ((i >> cross_q[2 * k]) ^ (i >> cross_q[2 * k + 1])) & 1ull;
+            e += par ? -cross_c[k] : cross_c[k];
+        }
+        const T v = psi[i];
+        double ox = e * (double)v.x, oy = e * (double)v.y;
+        for (int k = 0; k < H.n_x; ++k) {
+            const T w = psi[i ^ (1ull << x_q[k])];
+            ox = fma(x_c[k], (double)w.x, ox);
+            oy = fma(x_c[k], (double)w.y, oy);
+        }
+        T o;
+        o.x = (decltype(o.x))ox;
+        o.y = (decltype(o.y))oy;
+        lam[i] = o;
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kRedThreadsB) k_dot_b(const T* __restrict__ a, const T* __restrict__ b, uint64_t N,
+                                                        double* __restrict__ partials) {
+    __shared__ double red[32];
+    const uint64_t inst = blockIdx.y;
+    a += inst * N;
+    b += inst * N;
+    double acc = 0.0;
+    const uint64_t stride = (uint64_t)gridDim.x * kRedThreadsB;
+    for (uint64_t i = (uint64_t)blockIdx.x * kRedThreadsB + threadIdx.x; i < N; i += stride) acc += re_cb(a[i], b[i]);
+    const double s = block_sum_b(acc, red);
+    if (threadIdx.x == 0) partials[inst * gridDim.x + blockIdx.x] = s;
+}
+
+// out[r] = sum_c partials[r * cols + c], fixed order
+__global__ void k_sum_rows(const double* __restrict__ partials, int rows, int cols, double* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    double s = 0.0;
+    for (int c = 0; c < cols; ++c) s += partials[(size_t)r * cols + c];
+    out[r] = s;
+}
+
+// |0..0> for `count` instances of N amplitudes (memset to zero beforehand)
+template <class T>
+__global__ void k_set_zero_basis(T* psi, uint64_t N, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        T one;
+        one.x = 1;
+        one.y = 0;
+        psi[(uint64_t)i * N] = one;
+    }
+}
+
+// ---- small instances: one CTA does everything in shared memory ------------------
+struct SmallDesc {
+    int32_t n, n_ops, op_off, n_terms, term_off, rot_off, e_out, pad;
+};
+
+template <class R>
+__global__ void __launch_bounds__(kSmallThreads) k_batch_small(const SmallDesc* __restrict__ descs, int n_desc,
+                                                               const TileOp<R>* __restrict__ fwd,
+                                                               const TileOp<R>* __restrict__ rev,
+                                                               const qs_term* __restrict__ terms,
+                                                               double* __restrict__ rot_vals,
+                                                               double* __restrict__ energies, int* counter) {
+    using T = typename Amp<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    __shared__ int item_s;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = item_s;
+        __syncthreads();
+        if (item >= n_desc) break;
+        const SmallDesc d = descs[item];
+        const uint32_t N = 1u << d.n;
+        T* psi = reinterpret_cast<T*>(smem_raw);
+        T* lam = psi + N;
+        for (uint32_t e = threadIdx.x; e < N; e += kSmallThreads) {
+            T z;
+            z.x = e == 0 ? 1 : 0;
+            z.y = 0;
+            psi[e] = z;
+        }
+        __syncthreads();
+        for (int g = 0; g < d.n_ops; ++g) {
+            const TileOp<R> op = fwd[d.op_off + g];
+            if (tile_apply<R, kSmallThreads>(psi, N, op, 0ull)) __syncthreads();
+        }
+        // lambda = H psi, diagonal terms evaluated from the index bits
+        for (uint32_t e = threadIdx.x; e < N; e += kSmallThreads) {
+            double ev = 0.0, ox = 0.0, oy = 0.0;
+            for (int k = 0; k < d.n_terms; ++k) {
+                const qs_term t = terms[d.term_off + k];
+                if (t.kind == QS_P_X) {
+                    const T w = psi[e ^ (1u << t.q0)];
+                    ox = fma(t.coef, (double)w.x, ox);
+                    oy = fma(t.coef, (double)w.y, oy);
+                } else {
+                    const uint32_t par = t.kind == QS_P_Z ? ((e >> t.q0) & 1u) : (((e >> t.q0) ^ (e >> t.q1)) & 1u);
+                    ev += par ? -t.coef : t.coef;
+                }
+            }
+            const T v = psi[e];
+            T o;
+            o.x = (R)fma(ev, (double)v.x, ox);
+            o.y = (R)fma(ev, (double)v.y, oy);
+            lam[e] = o;
+        }
+        __syncthreads();
+        double acc = 0.0;
+        for (uint32_t e = threadIdx.x; e < N; e += kSmallThreads) acc += re_cb(psi[e], lam[e]);
+        const double en = block_sum_b(acc, red);
+        if (threadIdx.x == 0) energies[d.e_out] = en;
+        for (int g = 0; g < d.n_ops; ++g) {  // rev[] is already in reverse circuit order
+            const TileOp<R> op = rev[d.op_off + g];
+            adj_apply<R, kSmallThreads>(psi, lam, N, op, 0ull, red, rot_vals + d.rot_off);
+            __syncthreads();
+        }
+    }
+}
+
+// ---- host side -------------------------------------------------------------------
+
+int rot_gen(int kind) { return kind == QS_G_RX ? 1 : kind == QS_G_RY ? 2 : kind == QS_G_RZ ? 3 : 0; }
+
+void dagger(const double m[8], double d[8]) {
+    d[0] = m[0]; d[1] = -m[1];
+    d[2] = m[4]; d[3] = -m[5];
+    d[4] = m[2]; d[5] = -m[3];
+    d[6] = m[6]; d[7] = -m[7];
+}
+
+// Lower an instance's gates; rotation classes are fixed by kind so that every
+// angle gives the same plan (RX general, RY real, RZ diagonal).
+qs_status lower_instance(const qs_instance& in, std::vector<Op>& ops) {
+    if (qs_status st = lower_gates(in.gates, in.n_gates, in.theta, in.n_params, in.n, ops)) return st;
+    for (int j = 0; j < in.n_gates; ++j) {
+        const int k = in.gates[j].kind;
+        if (k == QS_G_RX) ops[j].cls = GC_GENERAL;
+        else if (k == QS_G_RY) ops[j].cls = GC_REAL;
+        else if (k == QS_G_RZ) ops[j].cls = GC_DIAG;
+    }
+    return QS_OK;
+}
+
+// reversed, daggered op list
+void reverse_ops(const std::vector<Op>& f, std::vector<Op>& r) {
+    r.assign(f.rbegin(), f.rend());
+    for (Op& o : r) {
+        if (o.kind == OP_SWAP) continue;
+        double d[8];
+        dagger(o.m, d);
+        std::memcpy(o.m, d, sizeof(d));
+        if (o.cls == GC_DIAG1) o.cls = classify(o.m) == GC_DIAG1 ? GC_DIAG1 : GC_DIAG;
+    }
+}
+
+template <class R>
+TileOp<R> make_op(const Op& o, const int* bit_of, int gen, int slot) {
+    TileOp<R> t{};
+    t.kind = o.kind;
+    t.cls = o.cls;
+    t.tq = o.t;
+    t.tb = bit_of ? bit_of[o.t] : o.t;
+    t.cq = o.c;
+    t.cb = o.c >= 0 ? (bit_of ? bit_of[o.c] : o.c) : -1;
+    t.pad0 = gen;
+    t.pad1 = slot;
+    for (int j = 0; j < 8; ++j) t.m[j] = (R)o.m[j];
+    return t;
+}
+
+TileOpDF make_op_df(const Op& o, const int* bit_of) {
+    TileOpDF t{};
+    t.kind = o.kind;
+    t.cls = o.cls;
+    t.tq = o.t;
+    t.tb = bit_of[o.t];
+    t.cq = o.c;
+    t.cb = o.c >= 0 ? bit_of[o.c] : -1;
+    for (int j = 0; j < 8; ++j) split_to_floats(o.m[j], t.c[2 * j], t.c[2 * j + 1]);
+    return t;
+}
+
+std::vector<long long> signature(const qs_instance& in) {
+    std::vector<long long> s;
+    s.push_back(in.n);
+    s.push_back(in.n_params);
+    for (int j = 0; j < in.n_gates; ++j) {
+        const qs_gate& g = in.gates[j];
+        s.push_back(g.kind);
+        s.push_back(g.t);
+        s.push_back(g.c);
+        s.push_back(g.param);
+        if (g.kind == QS_G_U1 || g.kind == QS_G_CU) s.push_back(classify(g.m));
+    }
+    for (int j = 0; j < in.n_terms; ++j) {
+        s.push_back(100 + in.terms[j].kind);
+        s.push_back(in.terms[j].q0);
+        s.push_back(in.terms[j].q1);
+    }
+    return s;
+}
+
+struct Region { size_t off = 0, bytes = 0; };
+
+struct Group {
+    int n = 0;
+    std::vector<int> members;
+    std::vector<PassDesc> fwd, rev;
+    std::vector<int> rev_nslot_used;
+    int n_slots = 0, n_rot = 0;
+    size_t fwd_per = 0, rev_per = 0;  // op records per instance
+    Region st_fwd, st_rev;            // in the staging / device op buffer
+    std::vector<int> slot_rot;        // rev.size() * n_slots
+    int* d_slot_rot = nullptr;
+    void* phi = nullptr;
+    void* lam = nullptr;
+    double* d_part = nullptr;         // reverse partials: count * tiles * n_slots
+    double* d_epart = nullptr;        // energy partials: count * eblocks
+    int eblocks = 0;
+    HGroup H{};
+    double* d_tabs = nullptr;
+    int* d_cross_q = nullptr;
+    double* d_cross_c = nullptr;
+    int* d_x_q = nullptr;
+    double* d_x_c = nullptr;
+    int b_fwd = 0, b_adj = 0;
+    size_t rot_out = 0, e_out = 0;    // offsets into the result buffer (doubles)
+};
+
+}  // namespace
+}  // namespace qs
+
+struct qs_batch {
+    qs_dtype dt;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t own_stream = nullptr;  // used when the caller passes the legacy default stream
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    int flags = 0;
+    std::vector<qs_instance> inst;      // shallow copies (structure only)
+    std::vector<std::vector<qs_gate>> gates;
+    std::vector<std::vector<qs_term>> terms;
+    std::vector<int> n_params;
+    std::vector<size_t> param_off;
+    size_t total_params = 0;
+    // small instances
+    std::vector<int> small;
+    std::vector<qs::Region> small_fwd;  // per small instance, offsets (records) in the small op arrays
+    size_t small_ops = 0;
+    qs::Region st_small_fwd, st_small_rev;
+    qs::SmallDesc* d_small = nullptr;
+    qs_term* d_terms = nullptr;
+    int* d_counter = nullptr;
+    int small_nmax = 0;
+    std::vector<qs::Group> groups;
+    // op staging (pinned) and its device mirror
+    unsigned char* h_stage = nullptr;
+    unsigned char* d_stage = nullptr;
+    size_t stage_bytes = 0;
+    // results: rotation values and energies (device and pinned host)
+    double* d_res = nullptr;
+    double* h_res = nullptr;
+    size_t res_doubles = 0;
+    std::vector<size_t> rot_of_inst;     // offset of instance i's rotation values in the result
+    std::vector<std::vector<int>> rot_param;  // instance i: parameter index of its r-th rotation (in gate order)
+    std::vector<size_t> e_of_inst;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+namespace qs {
+namespace {
+
+cudaStream_t main_stream(qs_batch* b) { return b->own_stream ? b->own_stream : b->user_stream; }
+
+// Fill the staging buffer with op records for the given angles (host work).
+template <class R>
+qs_status stage_ops(qs_batch* bt, const double* theta_all) {
+    for (size_t si = 0; si < bt->small.size(); ++si) {
+        const int idx = bt->small[si];
+        qs_instance in = bt->inst[idx];
+        if (theta_all) in.theta = theta_all + bt->param_off[idx];
+        std::vector<Op> ops, rops;
+        if (qs_status st = lower_instance(in, ops)) return st;
+        reverse_ops(ops, rops);
+        const Region& reg = bt->small_fwd[si];
+        TileOp<R>* f = reinterpret_cast<TileOp<R>*>(bt->h_stage + bt->st_small_fwd.off) + reg.off;
+        TileOp<R>* r = reinterpret_cast<TileOp<R>*>(bt->h_stage + bt->st_small_rev.off) + reg.off;
+        int rot = 0;
+        std::vector<int> rank(ops.size(), -1);
+        for (size_t j = 0; j < ops.size(); ++j)
+            if (rot_gen(in.gates[j].kind)) rank[j] = rot++;
+        for (size_t j = 0; j < ops.size(); ++j) {
+            f[j] = make_op<R>(ops[j], nullptr, 0, -1);
+            const size_t orig = ops.size() - 1 - j;
+            const int gen = rot_gen(in.gates[orig].kind);
+            r[j] = make_op<R>(rops[j], nullptr, gen, gen ? rank[orig] : -1);
+        }
+    }
+    for (Group& g : bt->groups) {
+        for (size_t k = 0; k < g.members.size(); ++k) {
+            const int idx = g.members[k];
+            qs_instance in = bt->inst[idx];
+            if (theta_all) in.theta = theta_all + bt->param_off[idx];
+            std::vector<Op> ops, rops;
+            if (qs_status st = lower_instance(in, ops)) return st;
+            reverse_ops(ops, rops);
+            // forward: double-float records for complex128, FP32 records for complex64
+            size_t w = 0;
+            for (const PassDesc& d : g.fwd) {
+                for (int j : d.members) {
+                    if (bt->dt == QS_C128) {
+                        TileOpDF* f = reinterpret_cast<TileOpDF*>(bt->h_stage + g.st_fwd.off) + k * g.fwd_per;
+                        f[w++] = make_op_df(ops[j], d.bit_of);
+                    } else {
+                        TileOp<float>* f = reinterpret_cast<TileOp<float>*>(bt->h_stage + g.st_fwd.off) + k * g.fwd_per;
+                        f[w++] = make_op<float>(ops[j], d.bit_of, 0, -1);
+                    }
+                }
+            }
+            // reverse: rotation r (gate order) -> slot within its pass
+            std::vector<int> rank(ops.size(), -1);
+            int rot = 0;
+            for (size_t j = 0; j < ops.size(); ++j)
+                if (rot_gen(in.gates[j].kind)) rank[j] = rot++;
+            TileOp<R>* r = reinterpret_cast<TileOp<R>*>(bt->h_stage + g.st_rev.off) + k * g.rev_per;
+            w = 0;
+            for (const PassDesc& d : g.rev) {
+                int slot = 0;
+                for (int j : d.members) {
+                    const size_t orig = ops.size() - 1 - (size_t)j;
+                    const int gen = rot_gen(in.gates[orig].kind);
+                    r[w++] = make_op<R>(rops[j], d.bit_of, gen, gen ? slot++ : -1);
+                }
+            }
+        }
+    }
+    return QS_OK;
+}
+
+template <class R>
+qs_status record(qs_batch* bt) {
+    using T = typename Amp<R>::T;
+    cudaStream_t ms = main_stream(bt);
+    QS_CUDA_TRY(cudaMemcpyAsync(bt->d_stage, bt->h_stage, bt->stage_bytes, cudaMemcpyHostToDevice, ms));
+    QS_CUDA_TRY(cudaEventRecord(bt->events[0], ms));
+    const int ns = (int)bt->streams.size();
+    std::vector<char> forked(ns, 0);  // only streams that joined the fork are joined back
+    // small instances: one persistent kernel on stream 0
+    if (!bt->small.empty()) {
+        cudaStream_t st = bt->streams[0];
+        QS_CUDA_TRY(cudaStreamWaitEvent(st, bt->events[0], 0));
+        forked[0] = 1;
+        QS_CUDA_TRY(cudaMemsetAsync(bt->d_counter, 0, sizeof(int), st));
+        const size_t smem = (size_t)2 * sizeof(T) << bt->small_nmax;
+        int grid = std::min<int>((int)bt->small.size(), sm_count());
+        k_batch_small<R><<<grid, kSmallThreads, smem, st>>>(
+            bt->d_small, (int)bt->small.size(), reinterpret_cast<const TileOp<R>*>(bt->d_stage + bt->st_small_fwd.off),
+            reinterpret_cast<const TileOp<R>*>(bt->d_stage + bt->st_small_rev.off), bt->d_terms, bt->d_res, bt->d_res,
+            bt->d_counter);
+        QS_CUDA_TRY(cudaGetLastError());
+    }
+    // groups round robin over the remaining streams
+    for (size_t gi = 0; gi < bt->groups.size(); ++gi) {
+        Group& g = bt->groups[gi];
+        cudaStream_t st = bt->streams[(gi + 1) % ns];
+        if (!forked[(gi + 1) % ns]) QS_CUDA_TRY(cudaStreamWaitEvent(st, bt->events[0], 0));
+        forked[(gi + 1) % ns] = 1;
+        const uint64_t N = 1ull << g.n;
+        const unsigned count = (unsigned)g.members.size();
+        QS_CUDA_TRY(cudaMemsetAsync(g.phi, 0, sizeof(T) * N * count, st));
+        k_set_zero_basis<T><<<(count + 127) / 128, 128, 0, st>>>((T*)g.phi, N, (int)count);
+        QS_CUDA_TRY(cudaGetLastError());
+        qs_state sv{};
+        sv.n = g.n;
+        sv.dt = bt->dt;
+        sv.data = g.phi;
+        sv.stream = st;
+        size_t op0 = 0;
+        for (const PassDesc& d : g.fwd) {
+            TilePass tp = d.tp;
+            tp.op0 = (int)op0;
+            tp.nops = (int)d.members.size();
+            tp.inst_stride = N;
+            tp.ops_stride = (int)g.fwd_per;
+            if (qs_status s = launch_tile_pass(&sv, bt->d_stage + g.st_fwd.off, tp, false, count)) return s;
+            op0 += d.members.size();
+        }
+        // lambda = H psi, energy
+        dim3 hg((unsigned)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count() * 4), count);
+        k_apply_h_b<T><<<hg, 256, 0, st>>>((const T*)g.phi, (T*)g.lam, N, g.H, g.d_tabs, g.d_cross_q, g.d_cross_c,
+                                          g.d_x_q, g.d_x_c);
+        dim3 eg((unsigned)g.eblocks, count);
+        k_dot_b<T><<<eg, kRedThreadsB, 0, st>>>((const T*)g.phi, (const T*)g.lam, N, g.d_epart);
+        k_sum_rows<<<(count + 127) / 128, 128, 0, st>>>(g.d_epart, (int)count, g.eblocks, bt->d_res + g.e_out);
+        QS_CUDA_TRY(cudaGetLastError());
+        // reverse sweep
+        op0 = 0;
+        const size_t smem = ((size_t)2 * sizeof(T) << g.b_adj) + ((size_t)8 << g.b_adj);
+        for (size_t pi = 0; pi < g.rev.size(); ++pi) {
+            const PassDesc& d = g.rev[pi];
+            TilePass tp = d.tp;
+            tp.op0 = (int)op0;
+            tp.nops = (int)d.members.size();
+            tp.inst_stride = N;
+            tp.ops_stride = (int)g.rev_per;
+            const unsigned tiles = (unsigned)(1ull << (g.n - tp.b));
+            k_tile_adj<R><<<dim3(tiles, count), kAdjThreads, smem, st>>>(
+                (T*)g.phi, (T*)g.lam, reinterpret_cast<const TileOp<R>*>(bt->d_stage + g.st_rev.off), tp, g.d_part,
+                g.n_slots);
+            QS_CUDA_TRY(cudaGetLastError());
+            if (g.rev_nslot_used[pi] > 0) {
+                const int work = (int)count * g.n_slots;
+                k_adj_finalize<<<(work + 127) / 128, 128, 0, st>>>(g.d_part, (int)tiles, g.n_slots, (int)count,
+                                                                   g.d_slot_rot + pi * g.n_slots, bt->d_res + g.rot_out,
+                                                                   g.n_rot);
+                QS_CUDA_TRY(cudaGetLastError());
+            }
+            op0 += d.members.size();
+        }
+    }
+    // join and read the results back
+    for (int s = 0; s < ns; ++s) {
+        if (!forked[s]) continue;
+        QS_CUDA_TRY(cudaEventRecord(bt->events[1 + s], bt->streams[s]));
+        QS_CUDA_TRY(cudaStreamWaitEvent(ms, bt->events[1 + s], 0));
+    }
+    QS_CUDA_TRY(cudaMemcpyAsync(bt->h_res, bt->d_res, bt->res_doubles * sizeof(double), cudaMemcpyDeviceToHost, ms));
+    return QS_OK;
+}
+
+// Let a kernel use all the opt-in shared memory left beside its static shared memory.
+template <class K>
+qs_status allow_dynamic_smem(K* kernel) {
+    cudaFuncAttributes a;
+    QS_CUDA_TRY(cudaFuncGetAttributes(&a, kernel));
+    QS_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(smem_optin() - a.sharedSizeBytes)));
+    return QS_OK;
+}
+
+qs_status build_batch(qs_batch* bt) {
+    const bool c128 = bt->dt == QS_C128;
+    const size_t amp = c128 ? 16 : 8;
+    const size_t rec_native = c128 ? sizeof(TileOp<double>) : sizeof(TileOp<float>);
+    const size_t rec_fwd = c128 ? sizeof(TileOpDF) : sizeof(TileOp<float>);
+    // instances whose phi and lambda fit in one CTA's shared memory run whole in the persistent kernel
+    int small_max = 0;
+    while (small_max < 16 && ((size_t)2 * amp << (small_max + 1)) + 1024 <= smem_optin()) ++small_max;
+    std::map<std::vector<long long>, int> by_sig;
+    size_t res = 0;
+    bt->rot_of_inst.assign(bt->inst.size(), 0);
+    bt->e_of_inst.assign(bt->inst.size(), 0);
+    bt->rot_param.assign(bt->inst.size(), {});
+    for (size_t i = 0; i < bt->inst.size(); ++i) {
+        const qs_instance& in = bt->inst[i];
+        for (int j = 0; j < in.n_gates; ++j)
+            if (rot_gen(in.gates[j].kind)) bt->rot_param[i].push_back(in.gates[j].param);
+    }
+    // result layout: energies first, then rotation values
+    res = bt->inst.size();
+    for (size_t i = 0; i < bt->inst.size(); ++i) bt->e_of_inst[i] = i;
+    size_t small_rec = 0;
+    std::vector<SmallDesc> sd;
+    std::vector<qs_term> all_terms;
+    for (size_t i = 0; i < bt->inst.size(); ++i) {
+        const qs_instance& in = bt->inst[i];
+        if (in.n <= small_max) {
+            SmallDesc d{};
+            d.n = in.n;
+            d.n_ops = in.n_gates;
+            d.op_off = (int)small_rec;
+            d.n_terms = in.n_terms;
+            d.term_off = (int)all_terms.size();
+            d.rot_off = (int)res;
+            d.e_out = (int)i;
+            for (int j = 0; j < in.n_terms; ++j) all_terms.push_back(in.terms[j]);
+            bt->rot_of_inst[i] = res;
+            res += bt->rot_param[i].size();
+            Region r;
+            r.off = small_rec;
+            small_rec += in.n_gates;
+            bt->small.push_back((int)i);
+            bt->small_fwd.push_back(r);
+            bt->small_nmax = std::max(bt->small_nmax, in.n);
+            sd.push_back(d);
+            continue;
+        }
+        auto sig = signature(in);
+        auto it = by_sig.find(sig);
+        if (it == by_sig.end()) {
+            by_sig[sig] = (int)bt->groups.size();
+            bt->groups.emplace_back();
+            bt->groups.back().n = in.n;
+            it = by_sig.find(sig);
+        }
+        bt->groups[it->second].members.push_back((int)i);
+    }
+    // plans for every group (structure of its first member)
+    size_t stage = 0;
+    auto take = [&](size_t bytes) { size_t o = (stage + 255) & ~(size_t)255; stage = o + bytes; return o; };
+    bt->small_ops = small_rec;
+    bt->st_small_fwd.off = take(small_rec * rec_native);
+    bt->st_small_rev.off = take(small_rec * rec_native);
+    for (Group& g : bt->groups) {
+        const qs_instance& in = bt->inst[g.members[0]];
+        std::vector<Op> ops, rops;
+        if (qs_status st = lower_instance(in, ops)) return st;
+        reverse_ops(ops, rops);
+        g.b_fwd = std::min(g.n, c128 ? 12 : 13);
+        g.b_adj = std::min(g.n, c128 ? 11 : 12);
+        const int b0 = std::min(4, std::max(0, g.b_adj - 3));
+        if (qs_status st = plan_passes(g.n, ops, g.b_fwd, b0, true, 1, g.fwd)) return st;
+        if (qs_status st = plan_passes(g.n, rops, g.b_adj, b0, true, 1, g.rev)) return st;
+        for (const PassDesc& d : g.fwd)
+            if (!d.tile) return fail(QS_EINVAL, "batch: a gate does not fit a tile");
+        g.fwd_per = ops.size();
+        g.rev_per = rops.size();
+        // rotation slots per reverse pass
+        std::vector<int> rank(ops.size(), -1);
+        int rot = 0;
+        for (size_t j = 0; j < ops.size(); ++j)
+            if (rot_gen(in.gates[j].kind)) rank[j] = rot++;
+        g.n_rot = rot;
+        g.n_slots = 1;
+        for (const PassDesc& d : g.rev) {
+            if (!d.tile) return fail(QS_EINVAL, "batch: a gate does not fit a tile");
+            int c = 0;
+            for (int j : d.members)
+                if (rot_gen(in.gates[ops.size() - 1 - j].kind)) ++c;
+            g.n_slots = std::max(g.n_slots, c);
+        }
+        g.slot_rot.assign(g.rev.size() * g.n_slots, -1);
+        g.rev_nslot_used.assign(g.rev.size(), 0);
+        for (size_t pi = 0; pi < g.rev.size(); ++pi) {
+            int slot = 0;
+            for (int j : g.rev[pi].members) {
+                const size_t orig = ops.size() - 1 - j;
+                if (rot_gen(in.gates[orig].kind)) g.slot_rot[pi * g.n_slots + slot++] = rank[orig];
+            }
+            g.rev_nslot_used[pi] = slot;
+        }
+        g.st_fwd.off = take(g.members.size() * g.fwd_per * rec_fwd);
+        g.st_rev.off = take(g.members.size() * g.rev_per * rec_native);
+        g.e_out = res;
+        for (size_t k = 0; k < g.members.size(); ++k) bt->e_of_inst[g.members[k]] = res + k;
+        res += g.members.size();
+        g.rot_out = res;
+        for (size_t k = 0; k < g.members.size(); ++k) bt->rot_of_inst[g.members[k]] = res + k * g.n_rot;
+        res += g.members.size() * g.n_rot;
+    }
+    bt->stage_bytes = std::max<size_t>(stage, 256);
+    bt->res_doubles = std::max<size_t>(res, 1);
+    // allocations
+    if (cudaMallocHost(&bt->h_stage, bt->stage_bytes) != cudaSuccess) { cudaGetLastError(); return fail(QS_ENOMEM, "batch: pinned staging"); }
+    if (cudaMalloc(&bt->d_stage, bt->stage_bytes) != cudaSuccess) { cudaGetLastError(); return fail(QS_ENOMEM, "batch: device ops"); }
+    if (cudaMallocHost(&bt->h_res, bt->res_doubles * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return fail(QS_ENOMEM, "batch: pinned results"); }
+    if (cudaMalloc(&bt->d_res, bt->res_doubles * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return fail(QS_ENOMEM, "batch: device results"); }
+    QS_CUDA_TRY(cudaMemset(bt->d_res, 0, bt->res_doubles * sizeof(double)));
+    if (!bt->small.empty()) {
+        if (cudaMalloc(&bt->d_small, sd.size() * sizeof(SmallDesc)) != cudaSuccess ||
+            cudaMalloc(&bt->d_terms, std::max<size_t>(1, all_terms.size()) * sizeof(qs_term)) != cudaSuccess ||
+            cudaMalloc(&bt->d_counter, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(QS_ENOMEM, "batch: small-instance tables");
+        }
+        QS_CUDA_TRY(cudaMemcpy(bt->d_small, sd.data(), sd.size() * sizeof(SmallDesc), cudaMemcpyHostToDevice));
+        if (!all_terms.empty())
+            QS_CUDA_TRY(cudaMemcpy(bt->d_terms, all_terms.data(), all_terms.size() * sizeof(qs_term), cudaMemcpyHostToDevice));
+    }
+    for (Group& g : bt->groups) {
+        const uint64_t N = 1ull << g.n;
+        const size_t count = g.members.size();
+        const size_t tiles = (size_t)1 << (g.n - g.b_adj);
+        g.eblocks = (int)std::min<uint64_t>((N + kRedThreadsB - 1) / kRedThreadsB, 64);
+        // H tables per member
+        const qs_instance& first = bt->inst[g.members[0]];
+        g.H.lo_bits = (g.n + 1) / 2;
+        const size_t nlo = (size_t)1 << g.H.lo_bits, nhi = (size_t)1 << (g.n - g.H.lo_bits);
+        g.H.tab_stride = (int)(nlo + nhi);
+        std::vector<int> cq, xq;
+        for (int j = 0; j < first.n_terms; ++j) {
+            const qs_term& t = first.terms[j];
+            if (t.kind == QS_P_X) xq.push_back(t.q0);
+            else if (t.kind == QS_P_ZZ) {
+                const int a = std::min(t.q0, t.q1), b = std::max(t.q0, t.q1);
+                if (a < g.H.lo_bits && b >= g.H.lo_bits) { cq.push_back(a); cq.push_back(b); }
+            }
+        }
+        g.H.n_cross = (int)cq.size() / 2;
+        g.H.n_x = (int)xq.size();
+        if (g.H.n_cross > kMaxCrossB || g.H.n_x > kMaxXB) return fail(QS_EINVAL, "batch: observable has too many terms");
+        std::vector<double> tabs(count * (nlo + nhi), 0.0), cc(std::max<size_t>(1, count * g.H.n_cross)),
+            xc(std::max<size_t>(1, count * g.H.n_x));
+        auto zs = [](uint64_t x, int q) { return ((x >> q) & 1ull) ? -1.0 : 1.0; };
+        for (size_t k = 0; k < count; ++k) {
+            const qs_instance& in = bt->inst[g.members[k]];
+            double* lo = tabs.data() + k * (nlo + nhi);
+            double* hi = lo + nlo;
+            int ci = 0, xi = 0;
+            for (int j = 0; j < in.n_terms; ++j) {
+                const qs_term& t = in.terms[j];
+                const int L = g.H.lo_bits;
+                if (t.kind == QS_P_X) { xc[k * g.H.n_x + xi++] = t.coef; continue; }
+                if (t.kind == QS_P_Z) {
+                    if (t.q0 < L) for (size_t x = 0; x < nlo; ++x) lo[x] += t.coef * zs(x, t.q0);
+                    else for (size_t x = 0; x < nhi; ++x) hi[x] += t.coef * zs(x, t.q0 - L);
+                    continue;
+                }
+                const int a = std::min(t.q0, t.q1), b = std::max(t.q0, t.q1);
+                if (b < L) for (size_t x = 0; x < nlo; ++x) lo[x] += t.coef * zs(x, a) * zs(x, b);
+                else if (a >= L) for (size_t x = 0; x < nhi; ++x) hi[x] += t.coef * zs(x, a - L) * zs(x, b - L);
+                else cc[k * g.H.n_cross + ci++] = t.coef;
+            }
+        }
+        if (cudaMalloc(&g.phi, amp * N * count) != cudaSuccess || cudaMalloc(&g.lam, amp * N * count) != cudaSuccess ||
+            cudaMalloc(&g.d_part, std::max<size_t>(1, count * tiles * g.n_slots) * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&g.d_epart, count * g.eblocks * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&g.d_slot_rot, g.slot_rot.size() * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&g.d_tabs, tabs.size() * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&g.d_cross_q, std::max<size_t>(1, cq.size()) * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&g.d_cross_c, cc.size() * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&g.d_x_q, std::max<size_t>(1, xq.size()) * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&g.d_x_c, xc.size() * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(QS_ENOMEM, "batch: group buffers");
+        }
+        QS_CUDA_TRY(cudaMemcpy(g.d_slot_rot, g.slot_rot.data(), g.slot_rot.size() * sizeof(int), cudaMemcpyHostToDevice));
+        QS_CUDA_TRY(cudaMemcpy(g.d_tabs, tabs.data(), tabs.size() * sizeof(double), cudaMemcpyHostToDevice));
+        if (!cq.empty()) QS_CUDA_TRY(cudaMemcpy(g.d_cross_q, cq.data(), cq.size() * sizeof(int), cudaMemcpyHostToDevice));
+        QS_CUDA_TRY(cudaMemcpy(g.d_cross_c, cc.data(), cc.size() * sizeof(double), cudaMemcpyHostToDevice));
+        if (!xq.empty()) QS_CUDA_TRY(cudaMemcpy(g.d_x_q, xq.data(), xq.size() * sizeof(int), cudaMemcpyHostToDevice));
+        QS_CUDA_TRY(cudaMemcpy(g.d_x_c, xc.data(), xc.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    // kernels that take more than 48 KiB of dynamic shared memory (set outside any graph capture)
+    if (c128) {
+        if (qs_status st = allow_dynamic_smem(k_batch_small<double>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_tile_adj<double>)) return st;
+    } else {
+        if (qs_status st = allow_dynamic_smem(k_batch_small<float>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_tile_adj<float>)) return st;
+    }
+    return QS_OK;
+}
+
+void free_batch(qs_batch* bt) {
+    cudaStream_t ms = main_stream(bt);
+    if (ms || bt->user_stream == nullptr) cudaStreamSynchronize(ms);
+    if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    for (Group& g : bt->groups) {
+        cudaFree(g.phi); cudaFree(g.lam); cudaFree(g.d_part); cudaFree(g.d_epart); cudaFree(g.d_slot_rot);
+        cudaFree(g.d_tabs); cudaFree(g.d_cross_q); cudaFree(g.d_cross_c); cudaFree(g.d_x_q); cudaFree(g.d_x_c);
+    }
+    cudaFree(bt->d_small); cudaFree(bt->d_terms); cudaFree(bt->d_counter);
+    cudaFree(bt->d_stage); cudaFree(bt->d_res);
+    if (bt->h_stage) cudaFreeHost(bt->h_stage);
+    if (bt->h_res) cudaFreeHost(bt->h_res);
+    for (cudaStream_t s : bt->streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : bt->events) cudaEventDestroy(e);
+    if (bt->own_stream) cudaStreamDestroy(bt->own_stream);
+}
+
+qs_status check_instance(const qs_instance& in) {
+    if (in.n < 1 || in.n > 30) return fail(QS_EINVAL, "batch instance: n must be in [1, 30]");
+    if (in.n_gates < 0 || in.n_params < 0 || in.n_terms < 0) return fail(QS_EINVAL, "batch instance: negative count");
+    if ((in.n_gates && !in.gates) || (in.n_params && !in.theta) || (in.n_terms && !in.terms))
+        return fail(QS_EINVAL, "batch instance: NULL array");
+    for (int j = 0; j < in.n_terms; ++j) {
+        const qs_term& t = in.terms[j];
+        if (t.kind != QS_P_Z && t.kind != QS_P_ZZ && t.kind != QS_P_X) return fail(QS_EINVAL, "unknown Pauli term kind");
+        if (t.q0 < 0 || t.q0 >= in.n) return fail(QS_EINVAL, "term qubit out of range");
+        if (t.kind == QS_P_ZZ && (t.q1 < 0 || t.q1 >= in.n || t.q1 == t.q0)) return fail(QS_EINVAL, "bad ZZ term");
+    }
+    std::vector<Op> ops;
+    return lower_gates(in.gates, in.n_gates, in.theta, in.n_params, in.n, ops);
+}
+
+}  // namespace
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" {
+
+qs_status qs_batch_create(const qs_instance* batch, int n_inst, qs_dtype dt, void* cuda_stream, int flags,
+                          qs_batch** out) {
+    if (!out) return fail(QS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_inst < 1 || !batch) return fail(QS_EINVAL, "empty batch");
+    if (dt != QS_C64 && dt != QS_C128) return fail(QS_EDTYPE, "unknown dtype");
+    for (int i = 0; i < n_inst; ++i)
+        if (qs_status st = check_instance(batch[i])) return st;
+    qs_batch* bt = new (std::nothrow) qs_batch();
+    if (!bt) return fail(QS_ENOMEM, "host allocation failed");
+    bt->dt = dt;
+    bt->flags = flags;
+    bt->user_stream = (cudaStream_t)cuda_stream;
+    // copy the instances' structure and angles (the caller's arrays may go away)
+    bt->gates.resize(n_inst);
+    bt->terms.resize(n_inst);
+    bt->param_off.resize(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+        const qs_instance& in = batch[i];
+        bt->gates[i].assign(in.gates, in.gates + in.n_gates);
+        bt->terms[i].assign(in.terms, in.terms + in.n_terms);
+        bt->param_off[i] = bt->total_params;
+        bt->total_params += in.n_params;
+    }
+    bt->inst.resize(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+        bt->inst[i] = batch[i];
+        bt->inst[i].gates = bt->gates[i].data();
+        bt->inst[i].terms = bt->terms[i].data();
+        bt->n_params.push_back(batch[i].n_params);
+    }
+    qs_status st = QS_OK;
+    auto cuda_ok = [&](cudaError_t e, const char* what) {
+        if (e != cudaSuccess && st == QS_OK) st = cuda_fail(e, what);
+        return e == cudaSuccess;
+    };
+    if (bt->user_stream == nullptr) cuda_ok(cudaStreamCreateWithFlags(&bt->own_stream, cudaStreamNonBlocking), "stream");
+    const int ns = 4;
+    for (int s = 0; s < ns && st == QS_OK; ++s) {
+        cudaStream_t x;
+        if (cuda_ok(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking), "stream")) bt->streams.push_back(x);
+    }
+    for (int e = 0; e < ns + 1 && st == QS_OK; ++e) {
+        cudaEvent_t x;
+        if (cuda_ok(cudaEventCreateWithFlags(&x, cudaEventDisableTiming), "event")) bt->events.push_back(x);
+    }
+    if (st == QS_OK) st = build_batch(bt);
+    // first staging with the angles given here (they are read now, not kept)
+    if (st == QS_OK) st = dt == QS_C128 ? stage_ops<double>(bt, nullptr) : stage_ops<float>(bt, nullptr);
+    for (int i = 0; i < n_inst; ++i) bt->inst[i].theta = nullptr;
+    if (st != QS_OK) {
+        free_batch(bt);
+        delete bt;
+        return st;
+    }
+    *out = bt;
+    return QS_OK;
+}
+
+qs_status qs_batch_execute(qs_batch* bt, const double* theta_all, double* energies, double* grads) {
+    if (!bt) return fail(QS_EINVAL, "batch is NULL");
+    if (!energies || (bt->total_params && !grads)) return fail(QS_EINVAL, "NULL output");
+    cudaStream_t ms = main_stream(bt);
+    if (theta_all) {
+        for (size_t i = 0; i < bt->inst.size(); ++i) bt->inst[i].theta = theta_all + bt->param_off[i];
+        qs_status st = bt->dt == QS_C128 ? stage_ops<double>(bt, theta_all) : stage_ops<float>(bt, theta_all);
+        for (size_t i = 0; i < bt->inst.size(); ++i) bt->inst[i].theta = nullptr;
+        if (st != QS_OK) return st;
+    }
+    const bool use_graph = !(bt->flags & 1);
+    if (use_graph) {
+        if (!bt->gexec) {
+            QS_CUDA_TRY(cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal));
+            qs_status st = bt->dt == QS_C128 ? record<double>(bt) : record<float>(bt);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(ms, &g);
+            if (st != QS_OK) { if (g) cudaGraphDestroy(g); return st; }
+            if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
+            bt->graph = g;
+            QS_CUDA_TRY(cudaGraphInstantiate(&bt->gexec, g, 0));
+        }
+        QS_CUDA_TRY(cudaGraphLaunch(bt->gexec, ms));
+    } else {
+        qs_status st = bt->dt == QS_C128 ? record<double>(bt) : record<float>(bt);
+        if (st != QS_OK) return st;
+    }
+    QS_CUDA_TRY(cudaStreamSynchronize(ms));
+    for (size_t i = 0; i < bt->inst.size(); ++i) {
+        energies[i] = bt->h_res[bt->e_of_inst[i]];
+        double* gi = grads + bt->param_off[i];
+        for (int p = 0; p < bt->n_params[i]; ++p) gi[p] = 0.0;
+        const std::vector<int>& rp = bt->rot_param[i];
+        for (size_t r = 0; r < rp.size(); ++r) gi[rp[r]] += bt->h_res[bt->rot_of_inst[i] + r];
+    }
+    return QS_OK;
+}
+
+qs_status qs_batch_stats(const qs_batch* bt, int* n_small, int* n_groups, int* n_launches) {
+    if (!bt) return fail(QS_EINVAL, "batch is NULL");
+    int launches = bt->small.empty() ? 0 : 1;
+    for (const Group& g : bt->groups) {
+        launches += 1 + (int)g.fwd.size() + 3 + (int)g.rev.size();
+        for (int u : g.rev_nslot_used) launches += u > 0;
+    }
+    if (n_small) *n_small = (int)bt->small.size();
+    if (n_groups) *n_groups = (int)bt->groups.size();
+    if (n_launches) *n_launches = launches;
+    return QS_OK;
+}
+
+qs_status qs_batch_destroy(qs_batch* bt) {
+    if (!bt) return QS_OK;
+    free_batch(bt);
+    delete bt;
+    return QS_OK;
+}
+
+qs_status qs_grad(const qs_instance* batch, int n_inst, qs_dtype dt, void* cuda_stream, double* energies,
+                  double* grads) {
+    if (n_inst == 0) return QS_OK;
+    qs_batch* bt = nullptr;
+    if (qs_status st = qs_batch_create(batch, n_inst, dt, cuda_stream, 1, &bt)) return st;
+    qs_status st = qs_batch_execute(bt, nullptr, energies, grads);
+    qs_batch_destroy(bt);
+    return st;
+}
+
+}  // extern "C"

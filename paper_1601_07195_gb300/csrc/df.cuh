@@ -40,10 +40,18 @@ __device__ __forceinline__ dfl df_mul(float qh, float ql, float xh, float xl) {
     return {ph, pl};
 }
 
+// Fast2Sum (Dekker): exact when |a| >= |b|.  When cancellation leaves |a| <
+// |b| the pair still sums to a + b up to one rounding of b's size, i.e. within
+// 2^-46 of the magnitudes that entered the dot product: inside the DF bound.
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
 // sum of two unnormalised products, normalised
 __device__ __forceinline__ dfl df_dot2(dfl a, dfl b) {
     const dfl s = two_sum(a.h, b.h);
-    return two_sum(s.h, s.l + (a.l + b.l));
+    return fast_two_sum(s.h, s.l + (a.l + b.l));
 }
 
 // sum of four unnormalised products, normalised
@@ -54,7 +62,7 @@ __device__ __forceinline__ dfl df_dot4(dfl a, dfl b, dfl c, dfl d) {
     lo += s.l + c.l;
     s = two_sum(s.h, d.h);
     lo += s.l + d.l;
-    return two_sum(s.h, lo);
+    return fast_two_sum(s.h, lo);
 }
 
 // Exact split of a double into hi = its leading 24 significant bits and lo =

@@ -105,15 +105,66 @@ qs_status upload_ops(const std::vector<OpT>& v, void** dst) {
 
 template <class OpT>
 qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse, bool upload) {
-    const int n = p->s->n;
-    b = std::min(b, n);
-    b0 = std::min(b0, b);
-    const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
+    std::vector<PassDesc> descs;
+    if (qs_status st = plan_passes(p->s->n, ops, b, b0, fuse, 2, descs)) return st;
     std::vector<OpT> tops;
     std::vector<TileOp<double>> t64;  // parallel records for moves-only passes of double-float plans
     const bool df = std::is_same<OpT, TileOpDF>::value;
+    for (const PassDesc& d : descs) {
+        PlanPass pp{};
+        pp.n_gates = (int)d.members.size();
+        pp.members = d.members;
+        pp.mask = d.mask;
+        if (!d.tile) {
+            pp.kind = 0;
+            pp.op = ops[d.members[0]];
+            p->passes.push_back(pp);
+            continue;
+        }
+        pp.kind = 1;
+        pp.tp = d.tp;
+        pp.tp.op0 = (int)tops.size();
+        pp.tp.nops = (int)d.members.size();
+        pp.moves_only = true;
+        for (int j : d.members) {
+            tops.push_back(to_tile_op<OpT>(ops[j], d.bit_of));
+            if (df) t64.push_back(to_tile_op<TileOp<double>>(ops[j], d.bit_of));
+            if (!(ops[j].kind == OP_SWAP || ops[j].cls == GC_PERM)) pp.moves_only = false;
+        }
+        p->passes.push_back(pp);
+    }
+    if (upload) {
+        if (qs_status st = upload_ops(tops, &p->d_ops)) return st;
+        if (qs_status st = upload_ops(t64, &p->d_ops_f64)) return st;
+    }
+    return QS_OK;
+}
+
+qs_status launch_all(qs_plan* p, cudaEvent_t* ev) {
+    const bool f64 = (p->flags & QS_PLAN_ARITH_F64) != 0;
+    for (size_t i = 0; i < p->passes.size(); ++i) {
+        const PlanPass& pp = p->passes[i];
+        if (ev) QS_CUDA_TRY(cudaEventRecord(ev[i], p->s->stream));
+        qs_status st;
+        if (pp.kind == 0) st = launch_op(p->s, pp.op, f64);
+        else if (p->d_ops_f64 && pp.moves_only) st = launch_tile_pass(p->s, p->d_ops_f64, pp.tp, true);
+        else st = launch_tile_pass(p->s, p->d_ops, pp.tp, f64);
+        if (st != QS_OK) return st;
+    }
+    if (ev) QS_CUDA_TRY(cudaEventRecord(ev[p->passes.size()], p->s->stream));
+    return QS_OK;
+}
+
+}  // namespace
+
+qs_status plan_passes(int n, const std::vector<Op>& ops, int b, int b0, bool fuse, int min_tile_members,
+                      std::vector<PassDesc>& out) {
+    b = std::min(b, n);
+    b0 = std::min(b0, b);
+    const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1ull);
     std::vector<char> taken(ops.size(), 0);
     size_t first = 0;
+    out.clear();
     while (first < ops.size()) {
         std::vector<int> mem;
         uint64_t T = (1ull << b0) - 1ull;
@@ -127,6 +178,7 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
             if (popc(T | fneed) > b) {  // the next gate cannot share a tile: it runs alone
                 mem.push_back((int)first);
                 taken[first] = 1;
+                T |= fneed;
             }
         }
         if (fuse && mem.empty()) {
@@ -156,67 +208,39 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
         if (mem.empty()) return fail(QS_EINVAL, "planner made no progress");  // unreachable: the first gate always fits
         while (first < ops.size() && taken[first]) ++first;
 
-        PlanPass pp{};
-        pp.n_gates = (int)mem.size();
-        pp.members = mem;
-        if (mem.size() == 1) {
-            pp.kind = 0;
-            pp.op = ops[mem[0]];
-            pp.mask = (1ull << pp.op.t) | (pp.op.c >= 0 ? (1ull << pp.op.c) : 0ull);
-            p->passes.push_back(pp);
+        PassDesc d;
+        d.members = mem;
+        for (int q = 0; q < 64; ++q) d.bit_of[q] = -1;
+        std::memset(&d.tp, 0, sizeof(d.tp));
+        const bool tile = (int)mem.size() >= min_tile_members && popc(T) <= b;
+        if (!tile) {
+            d.tile = false;
+            const Op& o = ops[mem[0]];
+            d.mask = (1ull << o.t) | (o.c >= 0 ? (1ull << o.c) : 0ull);
+            out.push_back(d);
             continue;
         }
         // pad the tile to b bits with the lowest unused qubits (longer contiguous runs)
         for (int q = 0; q < n && popc(T) < b; ++q) T |= (1ull << q);
         int run = 0;
         while (run < n && ((T >> run) & 1ull)) ++run;
-        TilePass& tp = pp.tp;
+        d.tile = true;
+        d.mask = T;
+        TilePass& tp = d.tp;
         tp.b = b;
         tp.b0 = run < b ? run : b;
         tp.nontile_mask = all & ~T;
-        int bit_of[64];
-        for (int q = 0; q < 64; ++q) bit_of[q] = -1;
         int nh = 0;
         for (int q = 0; q < n; ++q) {
             if (!((T >> q) & 1ull)) continue;
-            if (q < tp.b0) bit_of[q] = q;
-            else { bit_of[q] = tp.b0 + nh; tp.hi_q[nh++] = q; }
+            if (q < tp.b0) d.bit_of[q] = q;
+            else { d.bit_of[q] = tp.b0 + nh; tp.hi_q[nh++] = q; }
         }
-        tp.op0 = (int)tops.size();
-        tp.nops = (int)mem.size();
-        pp.moves_only = true;
-        for (int j : mem) {
-            tops.push_back(to_tile_op<OpT>(ops[j], bit_of));
-            if (df) t64.push_back(to_tile_op<TileOp<double>>(ops[j], bit_of));
-            if (!(ops[j].kind == OP_SWAP || ops[j].cls == GC_PERM)) pp.moves_only = false;
-        }
-        pp.kind = 1;
-        pp.mask = T;
-        p->passes.push_back(pp);
-    }
-    if (upload) {
-        if (qs_status st = upload_ops(tops, &p->d_ops)) return st;
-        if (qs_status st = upload_ops(t64, &p->d_ops_f64)) return st;
+        out.push_back(d);
     }
     return QS_OK;
 }
 
-qs_status launch_all(qs_plan* p, cudaEvent_t* ev) {
-    const bool f64 = (p->flags & QS_PLAN_ARITH_F64) != 0;
-    for (size_t i = 0; i < p->passes.size(); ++i) {
-        const PlanPass& pp = p->passes[i];
-        if (ev) QS_CUDA_TRY(cudaEventRecord(ev[i], p->s->stream));
-        qs_status st;
-        if (pp.kind == 0) st = launch_op(p->s, pp.op, f64);
-        else if (p->d_ops_f64 && pp.moves_only) st = launch_tile_pass(p->s, p->d_ops_f64, pp.tp, true);
-        else st = launch_tile_pass(p->s, p->d_ops, pp.tp, f64);
-        if (st != QS_OK) return st;
-    }
-    if (ev) QS_CUDA_TRY(cudaEventRecord(ev[p->passes.size()], p->s->stream));
-    return QS_OK;
-}
-
-}  // namespace
 }  // namespace qs
 
 using namespace qs;

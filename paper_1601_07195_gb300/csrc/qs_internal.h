@@ -68,7 +68,25 @@ struct TilePass {
     int32_t hi_q[kMaxTileBits];// qubit of tile bit b0 + j
     int32_t op0;               // first op in the plan's TileOp array
     int32_t nops;
+    uint64_t inst_stride;      // batched launches: amplitudes between instances (blockIdx.y)
+    int32_t ops_stride;        // batched launches: op records between instances
+    int32_t pad;
 };
+
+// One pass of a plan, before its ops are converted to device records.
+struct PassDesc {
+    std::vector<int> members;  // op indices in execution order
+    bool tile = false;         // false: a single op, run by the strided kernels
+    uint64_t mask = 0;         // tile qubits (tile pass) or the op's qubits
+    TilePass tp;               // tile passes: everything but op0 / nops / strides
+    int bit_of[64];            // qubit -> tile bit, -1 if not a tile bit
+};
+
+// Greedy pass building (plan.cu): gates join a pass while their mixing qubits
+// fit b tile bits, pulled ahead only over gates they commute with.  Passes of
+// fewer than min_tile_members gates become single-op passes.
+qs_status plan_passes(int n, const std::vector<Op>& ops, int b, int b0, bool fuse, int min_tile_members,
+                      std::vector<PassDesc>& out);
 
 }  // namespace qs
 
@@ -113,8 +131,9 @@ qs_status launch_op(qs_state* s, const Op& op, bool arith_f64);
 
 // Tile pass launcher (tile.cu); complex128 without arith_f64 goes to the
 // double-float kernel (tile_df.cu), whose op array holds TileOpDF records.
-qs_status launch_tile_pass(qs_state* s, const void* d_ops, const TilePass& pass, bool arith_f64);
-cudaError_t launch_tile_df(qs_state* s, const void* d_ops, const TilePass& pass);
+// count > 1 runs `count` instances side by side (grid.y), strides in `pass`.
+qs_status launch_tile_pass(qs_state* s, const void* d_ops, const TilePass& pass, bool arith_f64, unsigned count = 1);
+cudaError_t launch_tile_df(qs_state* s, const void* d_ops, const TilePass& pass, unsigned count);
 void split_to_floats(double x, float& hi, float& lo);
 size_t tile_smem_bytes(qs_dtype dt, int b);
 

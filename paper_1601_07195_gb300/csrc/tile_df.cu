@@ -12,7 +12,10 @@
 namespace qs {
 namespace {
 
-constexpr int kThreads = 512;
+#ifndef QS_TILE_DF_THREADS
+#define QS_TILE_DF_THREADS 512
+#endif
+constexpr int kThreads = QS_TILE_DF_THREADS;
 
 template <int CLS>
 __device__ __forceinline__ void df_pair_update(const float* c, float4& a, float4& b) {
@@ -143,6 +146,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_df(double2* __restrict__ psi,
                                                       TilePass P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* sm = reinterpret_cast<float4*>(smem_raw);
+    psi += (uint64_t)blockIdx.y * P.inst_stride;
+    ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride;
     const int b = P.b, b0 = P.b0, nh = b - b0;
     const uint32_t N = 1u << b;
     uint64_t* hioff = reinterpret_cast<uint64_t*>(sm + N);
@@ -171,7 +176,7 @@ void split_to_floats(double x, float& hi, float& lo) {
     lo = (float)(x - (double)hi);
 }
 
-cudaError_t launch_tile_df(qs_state* s, const void* d_ops, const TilePass& P) {
+cudaError_t launch_tile_df(qs_state* s, const void* d_ops, const TilePass& P, unsigned count) {
     const size_t smem = tile_smem_bytes(s->dt, P.b) + ((size_t)8 << (P.b - P.b0));
     static bool configured = false;
     if (!configured) {
@@ -179,7 +184,7 @@ cudaError_t launch_tile_df(qs_state* s, const void* d_ops, const TilePass& P) {
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const unsigned grid = (unsigned)(1ull << (s->n - P.b));
+    const dim3 grid((unsigned)(1ull << (s->n - P.b)), count);
     k_tile_df<<<grid, kThreads, smem, s->stream>>>(reinterpret_cast<double2*>(s->data),
                                                    reinterpret_cast<const TileOpDF*>(d_ops), P);
     return cudaGetLastError();

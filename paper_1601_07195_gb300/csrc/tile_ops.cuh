@@ -1,0 +1,117 @@
+// tile_ops.cuh -- in-shared-memory gate updates on a tile of 2^b amplitudes
+// (tile bits, not qubits): Eq. 2 pairs for single-qubit gates, Eq. 3 pairs
+// with a control tile bit, per-tile factors for diagonal gates whose target is
+// not a tile bit, and swaps.  Every branch depends only on the op and on the
+// tile's fixed non-tile bits (`base`), so it is uniform over the CTA.
+// THREADS is the CTA size that strides the loops.
+#pragma once
+
+#include "device.cuh"
+
+namespace qs {
+
+template <class R, int CLS, int THREADS>
+__device__ __forceinline__ void tile_1q(typename Amp<R>::T* sm, uint32_t N, int tb, const R* m) {
+    using T = typename Amp<R>::T;
+    for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
+        const uint32_t i0 = insert_zero32(p, tb), i1 = i0 | (1u << tb);
+        T a, b;
+        if (CLS != GC_DIAG1) a = sm[i0];
+        b = sm[i1];
+        pair_update<CLS>(m, a, b);
+        if (CLS != GC_DIAG1) sm[i0] = a;
+        sm[i1] = b;
+    }
+}
+
+template <class R, int CLS, int THREADS>
+__device__ __forceinline__ void tile_cu(typename Amp<R>::T* sm, uint32_t N, int cb, int tb, const R* m) {
+    using T = typename Amp<R>::T;
+    const int lo = min(cb, tb), hi = max(cb, tb);
+    for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
+        const uint32_t i0 = insert_two_zeros32(p, lo, hi) | (1u << cb), i1 = i0 | (1u << tb);
+        T a, b;
+        if (CLS != GC_DIAG1) a = sm[i0];
+        b = sm[i1];
+        pair_update<CLS>(m, a, b);
+        if (CLS != GC_DIAG1) sm[i0] = a;
+        sm[i1] = b;
+    }
+}
+
+// Multiply the tile (or, with cb >= 0, the half whose tile bit cb is 1) by f.
+template <class R, int THREADS>
+__device__ __forceinline__ void tile_scale(typename Amp<R>::T* sm, uint32_t N, R fr, R fi, int cb) {
+    if (cb < 0) {
+        for (uint32_t e = threadIdx.x; e < N; e += THREADS) sm[e] = cmul(fr, fi, sm[e]);
+    } else {
+        for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
+            const uint32_t e = insert_zero32(p, cb) | (1u << cb);
+            sm[e] = cmul(fr, fi, sm[e]);
+        }
+    }
+}
+
+template <class R, int THREADS>
+__device__ __forceinline__ void tile_swap(typename Amp<R>::T* sm, uint32_t N, int ab, int bb) {
+    using T = typename Amp<R>::T;
+    const int lo = min(ab, bb), hi = max(ab, bb);
+    for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
+        const uint32_t i = insert_two_zeros32(p, lo, hi);
+        const T x = sm[i | (1u << ab)];
+        sm[i | (1u << ab)] = sm[i | (1u << bb)];
+        sm[i | (1u << bb)] = x;
+    }
+}
+
+template <class R, int THREADS>
+__device__ __forceinline__ void tile_pairs(typename Amp<R>::T* sm, uint32_t N, int cls, int cb, int tb, const R* m) {
+    if (cb < 0) {
+        switch (cls) {
+        case GC_GENERAL: tile_1q<R, GC_GENERAL, THREADS>(sm, N, tb, m); break;
+        case GC_REAL: tile_1q<R, GC_REAL, THREADS>(sm, N, tb, m); break;
+        case GC_DIAG: tile_1q<R, GC_DIAG, THREADS>(sm, N, tb, m); break;
+        case GC_DIAG1: tile_1q<R, GC_DIAG1, THREADS>(sm, N, tb, m); break;
+        case GC_ANTIDIAG: tile_1q<R, GC_ANTIDIAG, THREADS>(sm, N, tb, m); break;
+        default: tile_1q<R, GC_PERM, THREADS>(sm, N, tb, m); break;
+        }
+    } else {
+        switch (cls) {
+        case GC_GENERAL: tile_cu<R, GC_GENERAL, THREADS>(sm, N, cb, tb, m); break;
+        case GC_REAL: tile_cu<R, GC_REAL, THREADS>(sm, N, cb, tb, m); break;
+        case GC_DIAG: tile_cu<R, GC_DIAG, THREADS>(sm, N, cb, tb, m); break;
+        case GC_DIAG1: tile_cu<R, GC_DIAG1, THREADS>(sm, N, cb, tb, m); break;
+        case GC_ANTIDIAG: tile_cu<R, GC_ANTIDIAG, THREADS>(sm, N, cb, tb, m); break;
+        default: tile_cu<R, GC_PERM, THREADS>(sm, N, cb, tb, m); break;
+        }
+    }
+}
+
+// Apply one op to the tile whose non-tile qubits are fixed by `base`.  Every
+// branch depends only on the op and on base, so it is uniform over the CTA.
+// Returns false when the op leaves this tile unchanged (no barrier needed).
+template <class R, int THREADS>
+__device__ __forceinline__ bool tile_apply(typename Amp<R>::T* sm, uint32_t N, const TileOp<R>& op, uint64_t base) {
+    if (op.kind == OP_SWAP) {
+        tile_swap<R, THREADS>(sm, N, op.tb, op.cb);
+        return true;
+    }
+    int cb = -1;
+    if (op.kind == OP_CU) {
+        if (op.cb < 0) {
+            if (((base >> op.cq) & 1ull) == 0) return false;  // control outside the tile is 0 here
+        } else {
+            cb = op.cb;
+        }
+    }
+    if (op.tb < 0) {  // diagonal gate whose target is not a tile bit: one factor for the (half-)tile
+        const bool bit = (base >> op.tq) & 1ull;
+        if (op.cls == GC_DIAG1 && !bit) return false;
+        tile_scale<R, THREADS>(sm, N, bit ? op.m[6] : op.m[0], bit ? op.m[7] : op.m[1], cb);
+        return true;
+    }
+    tile_pairs<R, THREADS>(sm, N, op.cls, cb, op.tb, op.m);
+    return true;
+}
+
+}  // namespace qs

@@ -67,6 +67,10 @@ _SIGS = {
     "qs_expect": [_vp, _vp, ctypes.c_int, _dp],
     "qs_grad": [_vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp],
     "qs_marginals_noalloc": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp],
+    "qs_batch_create": [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int, ctypes.POINTER(_vp)],
+    "qs_batch_execute": [_vp, _dp, _dp, _dp],
+    "qs_batch_stats": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "qs_batch_destroy": [_vp],
 }
 
 
@@ -284,6 +288,64 @@ class Plan:
     def close(self):
         if self._h is not None and self._h.value:
             load().qs_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _instance_array(instances):
+    keep = []
+    arr = (Instance * len(instances))()
+    for i, inst in enumerate(instances):
+        g = np.ascontiguousarray(inst["gates"], dtype=GATE_DTYPE)
+        th = np.ascontiguousarray(inst["theta"], dtype=np.float64)
+        tm = np.ascontiguousarray(inst["terms"], dtype=TERM_DTYPE)
+        keep += [g, th, tm]
+        arr[i] = Instance(inst["n"], len(g), g.ctypes.data, th.size, th.ctypes.data, len(tm), tm.ctypes.data)
+    return arr, keep
+
+
+class Batch:
+    """A planned batch of variational instances (qs_batch_*): energies and
+    adjoint gradients, replayed as one CUDA graph with new angles."""
+
+    def __init__(self, instances, dtype=QS_C128, stream=None, graph=True):
+        arr, keep = _instance_array(instances)
+        h = _vp()
+        _check(load().qs_batch_create(ctypes.cast(arr, _vp), len(instances), dtype, _stream_handle(stream),
+                                      0 if graph else 1, ctypes.byref(h)))
+        self._h = h
+        self.sizes = [len(inst["theta"]) for inst in instances]
+
+    def execute(self, thetas=None):
+        lib = load()
+        th = None
+        if thetas is not None:
+            th = np.ascontiguousarray(np.concatenate([np.asarray(t, dtype=np.float64) for t in thetas]))
+            if th.size != sum(self.sizes):
+                raise ValueError("angle count does not match the batch")
+        energies = np.zeros(len(self.sizes), dtype=np.float64)
+        grads = np.zeros(max(1, sum(self.sizes)), dtype=np.float64)
+        _check(lib.qs_batch_execute(self._h, th.ctypes.data_as(_dp) if th is not None else None,
+                                    energies.ctypes.data_as(_dp), grads.ctypes.data_as(_dp)))
+        out, off = [], 0
+        for p in self.sizes:
+            out.append(grads[off:off + p].copy())
+            off += p
+        return energies, out
+
+    def stats(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().qs_batch_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"small": a.value, "groups": b.value, "launches": c.value}
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            load().qs_batch_destroy(self._h)
         self._h = None
 
     def __del__(self):
