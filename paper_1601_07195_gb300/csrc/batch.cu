@@ -28,6 +28,8 @@
 #include <vector>
 
 #include "device.cuh"
+#include "df.cuh"
+#include "tile_df_ops.cuh"
 #include "tile_ops.cuh"
 
 namespace qs {
@@ -59,65 +61,129 @@ __device__ __forceinline__ double block_sum_b(double v, double* red) {
     return r;
 }
 
-template <class T> __device__ __forceinline__ double im_cb(const T& a, const T& b) {
-    return fma((double)a.x, (double)b.y, -(double)a.y * (double)b.x);
-}
 template <class T> __device__ __forceinline__ double re_cb(const T& a, const T& b) {
     return fma((double)a.x, (double)b.x, (double)a.y * (double)b.y);
 }
 
-// Im of <lambda| G |phi> restricted to one pair; gen 1 = X, 2 = Y, 3 = Z.
-template <class T>
-__device__ __forceinline__ double gen_term(int gen, const T& f0, const T& f1, const T& l0, const T& l1) {
-    if (gen == 1) return im_cb(l0, f1) + im_cb(l1, f0);
-    if (gen == 2) return re_cb(l1, f0) - re_cb(l0, f1);
-    return im_cb(l0, f0) - im_cb(l1, f1);
+// Per-thread gradient and energy sums: a float pair (hi, lo) fed with products
+// split exactly (TwoProd) or as double-float products; converted to double once
+// per reduction and summed across the block in FP64.  No FP64 instruction per
+// amplitude pair.
+struct GAcc { float h = 0.0f, l = 0.0f; };
+__device__ __forceinline__ void gacc_add(GAcc& a, float ph, float pl) {
+    const dfl s = two_sum(a.h, ph);
+    a.h = s.h;
+    a.l += s.l + pl;
+}
+__device__ __forceinline__ void gacc_prod(GAcc& a, float x, float y) {
+    const float p = x * y;
+    gacc_add(a, p, fmaf(x, y, -p));
+}
+__device__ __forceinline__ void gacc_dfprod(GAcc& a, float xh, float xl, float yh, float yl) {
+    const dfl p = df_mul(xh, xl, yh, yl);
+    gacc_add(a, p.h, p.l);
+}
+__device__ __forceinline__ double gacc_value(const GAcc& a) { return (double)a.h + (double)a.l; }
+
+// ---- arithmetic traits: complex64 (FP32) and complex128 (double-float) ----------
+struct TrF {
+    using E = float2;               // tile element
+    using G = float2;               // element in device memory
+    using Op = TileOp<float>;
+    static __device__ __forceinline__ E load(G g) { return g; }
+    static __device__ __forceinline__ G store(E e) { return e; }
+    template <int CLS> static __device__ __forceinline__ void pair(const Op& op, E& a, E& b) { pair_update<CLS>(op.m, a, b); }
+    static __device__ __forceinline__ E scale(const Op& op, bool use22, E x) {
+        return use22 ? cmul(op.m[6], op.m[7], x) : cmul(op.m[0], op.m[1], x);
+    }
+    // +Re(conj(a) b) or +Im(conj(a) b), with sign s = +1 / -1
+    static __device__ __forceinline__ void re(GAcc& c, E a, E b, float s) { gacc_prod(c, s * a.x, b.x); gacc_prod(c, s * a.y, b.y); }
+    static __device__ __forceinline__ void im(GAcc& c, E a, E b, float s) { gacc_prod(c, s * a.x, b.y); gacc_prod(c, -s * a.y, b.x); }
+    static __device__ __forceinline__ double2 to_d(E e) { return make_double2(e.x, e.y); }
+    static __device__ __forceinline__ E from_d(double2 d) { return make_float2((float)d.x, (float)d.y); }
+    template <int THREADS>
+    static __device__ __forceinline__ bool fwd(E* sm, uint32_t N, const Op& op, uint64_t base) {
+        return tile_apply<float, THREADS>(sm, N, op, base);
+    }
+};
+
+struct TrDF {
+    using E = float4;
+    using G = double2;
+    using Op = TileOpDF;
+    static __device__ __forceinline__ E load(G g) { return df_load(g); }
+    static __device__ __forceinline__ G store(E e) { return df_store(e); }
+    template <int CLS> static __device__ __forceinline__ void pair(const Op& op, E& a, E& b) { df_pair_update<CLS>(op.c, a, b); }
+    static __device__ __forceinline__ E scale(const Op& op, bool use22, E x) {
+        return use22 ? df_cmul(op.c, 6, 7, x) : df_cmul(op.c, 0, 1, x);
+    }
+    static __device__ __forceinline__ void re(GAcc& c, E a, E b, float s) {
+        gacc_dfprod(c, s * a.x, s * a.y, b.x, b.y);
+        gacc_dfprod(c, s * a.z, s * a.w, b.z, b.w);
+    }
+    static __device__ __forceinline__ void im(GAcc& c, E a, E b, float s) {
+        gacc_dfprod(c, s * a.x, s * a.y, b.z, b.w);
+        gacc_dfprod(c, -s * a.z, -s * a.w, b.x, b.y);
+    }
+    static __device__ __forceinline__ double2 to_d(E e) { return df_store(e); }
+    static __device__ __forceinline__ E from_d(double2 d) { return df_load(d); }
+    template <int THREADS>
+    static __device__ __forceinline__ bool fwd(E* sm, uint32_t N, const Op& op, uint64_t base) {
+        return df_tile_apply<THREADS>(sm, N, op, base);
+    }
+};
+
+// Im <lambda| G |phi> restricted to one pair; gen 1 = X, 2 = Y, 3 = Z.
+template <class Tr>
+__device__ __forceinline__ void gen_acc(GAcc& c, int gen, const typename Tr::E& f0, const typename Tr::E& f1,
+                                        const typename Tr::E& l0, const typename Tr::E& l1) {
+    if (gen == 1) { Tr::im(c, l0, f1, 1.0f); Tr::im(c, l1, f0, 1.0f); }
+    else if (gen == 2) { Tr::re(c, l1, f0, 1.0f); Tr::re(c, l0, f1, -1.0f); }
+    else { Tr::im(c, l0, f0, 1.0f); Tr::im(c, l1, f1, -1.0f); }
 }
 
 // ---- one reversed op on (phi, lambda) tiles ------------------------------------
 // op.pad0 = generator (0 = not a rotation), op.pad1 = output slot.
-template <class R, int CLS, int THREADS>
-__device__ __forceinline__ double adj_pairs(typename Amp<R>::T* f, typename Amp<R>::T* l, uint32_t N, int cb, int tb,
-                                            const R* m, int gen) {
-    using T = typename Amp<R>::T;
-    double acc = 0.0;
+template <class Tr, int CLS, int THREADS>
+__device__ __forceinline__ void adj_pairs(typename Tr::E* f, typename Tr::E* l, uint32_t N, int cb, int tb,
+                                          const typename Tr::Op& op, int gen, GAcc& acc) {
+    using E = typename Tr::E;
     if (cb < 0) {
         for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
             const uint32_t i0 = insert_zero32(p, tb), i1 = i0 | (1u << tb);
-            T f0 = f[i0], f1 = f[i1], l0 = l[i0], l1 = l[i1];
-            if (gen) acc += gen_term(gen, f0, f1, l0, l1);
-            pair_update<CLS>(m, f0, f1);
-            pair_update<CLS>(m, l0, l1);
+            E f0 = f[i0], f1 = f[i1], l0 = l[i0], l1 = l[i1];
+            if (gen) gen_acc<Tr>(acc, gen, f0, f1, l0, l1);
+            Tr::template pair<CLS>(op, f0, f1);
+            Tr::template pair<CLS>(op, l0, l1);
             f[i0] = f0; f[i1] = f1; l[i0] = l0; l[i1] = l1;
         }
     } else {
         const int lo = min(cb, tb), hi = max(cb, tb);
         for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
             const uint32_t i0 = insert_two_zeros32(p, lo, hi) | (1u << cb), i1 = i0 | (1u << tb);
-            T f0 = f[i0], f1 = f[i1], l0 = l[i0], l1 = l[i1];
-            if (gen) acc += gen_term(gen, f0, f1, l0, l1);
-            pair_update<CLS>(m, f0, f1);
-            pair_update<CLS>(m, l0, l1);
+            E f0 = f[i0], f1 = f[i1], l0 = l[i0], l1 = l[i1];
+            if (gen) gen_acc<Tr>(acc, gen, f0, f1, l0, l1);
+            Tr::template pair<CLS>(op, f0, f1);
+            Tr::template pair<CLS>(op, l0, l1);
             f[i0] = f0; f[i1] = f1; l[i0] = l0; l[i1] = l1;
         }
     }
-    return acc;
 }
 
-template <class R, int THREADS>
-__device__ __forceinline__ void adj_apply(typename Amp<R>::T* f, typename Amp<R>::T* l, uint32_t N, const TileOp<R>& op,
+template <class Tr, int THREADS>
+__device__ __forceinline__ void adj_apply(typename Tr::E* f, typename Tr::E* l, uint32_t N, const typename Tr::Op& op,
                                           uint64_t base, double* red, double* out) {
-    using T = typename Amp<R>::T;
+    using E = typename Tr::E;
     const int gen = op.pad0;
-    double acc = 0.0;
+    GAcc acc;
     bool active = true;
     int cb = -1;
     if (op.kind == OP_SWAP) {
         const int lo = min(op.tb, op.cb), hi = max(op.tb, op.cb);
         for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
             const uint32_t i = insert_two_zeros32(p, lo, hi), a = i | (1u << op.tb), b = i | (1u << op.cb);
-            const T x = f[a]; f[a] = f[b]; f[b] = x;
-            const T y = l[a]; l[a] = l[b]; l[b] = y;
+            const E x = f[a]; f[a] = f[b]; f[b] = x;
+            const E y = l[a]; l[a] = l[b]; l[b] = y;
         }
         active = false;
     } else if (op.kind == OP_CU) {
@@ -127,51 +193,50 @@ __device__ __forceinline__ void adj_apply(typename Amp<R>::T* f, typename Amp<R>
     if (active && op.kind != OP_SWAP) {
         if (op.tb < 0) {  // diagonal with its target outside the tile: one factor per (half-)tile
             const bool bit = (base >> op.tq) & 1ull;
-            const R fr = bit ? op.m[6] : op.m[0], fi = bit ? op.m[7] : op.m[1];
             const bool skip = op.cls == GC_DIAG1 && !bit;
+            const float zs = bit ? -1.0f : 1.0f;  // Z eigenvalue of the target bit (only Z rotations are diagonal)
             if (cb < 0) {
                 for (uint32_t e = threadIdx.x; e < N; e += THREADS) {
-                    if (gen) acc += im_cb(l[e], f[e]);
-                    if (!skip) { f[e] = cmul(fr, fi, f[e]); l[e] = cmul(fr, fi, l[e]); }
+                    if (gen) Tr::im(acc, l[e], f[e], zs);
+                    if (!skip) { f[e] = Tr::scale(op, bit, f[e]); l[e] = Tr::scale(op, bit, l[e]); }
                 }
             } else {
                 for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
                     const uint32_t e = insert_zero32(p, cb) | (1u << cb);
-                    if (gen) acc += im_cb(l[e], f[e]);
-                    if (!skip) { f[e] = cmul(fr, fi, f[e]); l[e] = cmul(fr, fi, l[e]); }
+                    if (gen) Tr::im(acc, l[e], f[e], zs);
+                    if (!skip) { f[e] = Tr::scale(op, bit, f[e]); l[e] = Tr::scale(op, bit, l[e]); }
                 }
             }
-            if (bit) acc = -acc;  // Z eigenvalue of the target bit (only Z rotations are diagonal)
         } else {
             switch (op.cls) {
-            case GC_GENERAL: acc = adj_pairs<R, GC_GENERAL, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
-            case GC_REAL: acc = adj_pairs<R, GC_REAL, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
-            case GC_DIAG: acc = adj_pairs<R, GC_DIAG, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
-            case GC_DIAG1: acc = adj_pairs<R, GC_DIAG1, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
-            case GC_ANTIDIAG: acc = adj_pairs<R, GC_ANTIDIAG, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
-            default: acc = adj_pairs<R, GC_PERM, THREADS>(f, l, N, cb, op.tb, op.m, gen); break;
+            case GC_GENERAL: adj_pairs<Tr, GC_GENERAL, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
+            case GC_REAL: adj_pairs<Tr, GC_REAL, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
+            case GC_DIAG: adj_pairs<Tr, GC_DIAG, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
+            case GC_DIAG1: adj_pairs<Tr, GC_DIAG1, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
+            case GC_ANTIDIAG: adj_pairs<Tr, GC_ANTIDIAG, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
+            default: adj_pairs<Tr, GC_PERM, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
             }
         }
     }
     if (gen) {  // uniform over the CTA: every thread takes part in the reduction
-        const double s = block_sum_b(active ? acc : 0.0, red);
+        const double s = block_sum_b(active ? gacc_value(acc) : 0.0, red);
         if (threadIdx.x == 0) out[op.pad1] = s;
     }
 }
 
 // ---- reverse tile pass over a group of instances --------------------------------
-template <class R>
-__global__ void __launch_bounds__(kAdjThreads) k_tile_adj(typename Amp<R>::T* __restrict__ phi,
-                                                          typename Amp<R>::T* __restrict__ lam,
-                                                          const TileOp<R>* __restrict__ ops, TilePass P,
+template <class Tr>
+__global__ void __launch_bounds__(kAdjThreads) k_tile_adj(typename Tr::G* __restrict__ phi,
+                                                          typename Tr::G* __restrict__ lam,
+                                                          const typename Tr::Op* __restrict__ ops, TilePass P,
                                                           double* __restrict__ partials, int n_slots) {
-    using T = typename Amp<R>::T;
+    using E = typename Tr::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     const int b = P.b, b0 = P.b0, nh = b - b0;
     const uint32_t N = 1u << b;
-    T* f = reinterpret_cast<T*>(smem_raw);
-    T* l = f + N;
+    E* f = reinterpret_cast<E*>(smem_raw);
+    E* l = f + N;
     uint64_t* hioff = reinterpret_cast<uint64_t*>(l + N);
     phi += (uint64_t)blockIdx.y * P.inst_stride;
     lam += (uint64_t)blockIdx.y * P.inst_stride;
@@ -188,19 +253,19 @@ __global__ void __launch_bounds__(kAdjThreads) k_tile_adj(typename Amp<R>::T* __
     const uint32_t lomask = (1u << b0) - 1u;
     for (uint32_t e = threadIdx.x; e < N; e += kAdjThreads) {
         const uint64_t g = base + hioff[e >> b0] + (e & lomask);
-        f[e] = phi[g];
-        l[e] = lam[g];
+        f[e] = Tr::load(phi[g]);
+        l[e] = Tr::load(lam[g]);
     }
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
-        const TileOp<R> op = ops[P.op0 + g];
-        adj_apply<R, kAdjThreads>(f, l, N, op, base, red, out);
+        const typename Tr::Op op = ops[P.op0 + g];
+        adj_apply<Tr, kAdjThreads>(f, l, N, op, base, red, out);
         __syncthreads();
     }
     for (uint32_t e = threadIdx.x; e < N; e += kAdjThreads) {
         const uint64_t g = base + hioff[e >> b0] + (e & lomask);
-        phi[g] = f[e];
-        lam[g] = l[e];
+        phi[g] = Tr::store(f[e]);
+        lam[g] = Tr::store(l[e]);
     }
 }
 
@@ -298,14 +363,14 @@ struct SmallDesc {
     int32_t n, n_ops, op_off, n_terms, term_off, rot_off, e_out, pad;
 };
 
-template <class R>
+template <class Tr>
 __global__ void __launch_bounds__(kSmallThreads) k_batch_small(const SmallDesc* __restrict__ descs, int n_desc,
-                                                               const TileOp<R>* __restrict__ fwd,
-                                                               const TileOp<R>* __restrict__ rev,
+                                                               const typename Tr::Op* __restrict__ fwd,
+                                                               const typename Tr::Op* __restrict__ rev,
                                                                const qs_term* __restrict__ terms,
                                                                double* __restrict__ rot_vals,
                                                                double* __restrict__ energies, int* counter) {
-    using T = typename Amp<R>::T;
+    using E = typename Tr::E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     __shared__ int item_s;
@@ -317,47 +382,39 @@ __global__ void __launch_bounds__(kSmallThreads) k_batch_small(const SmallDesc* 
         if (item >= n_desc) break;
         const SmallDesc d = descs[item];
         const uint32_t N = 1u << d.n;
-        T* psi = reinterpret_cast<T*>(smem_raw);
-        T* lam = psi + N;
-        for (uint32_t e = threadIdx.x; e < N; e += kSmallThreads) {
-            T z;
-            z.x = e == 0 ? 1 : 0;
-            z.y = 0;
-            psi[e] = z;
-        }
+        E* psi = reinterpret_cast<E*>(smem_raw);
+        E* lam = psi + N;
+        for (uint32_t e = threadIdx.x; e < N; e += kSmallThreads) psi[e] = Tr::from_d(make_double2(e == 0 ? 1.0 : 0.0, 0.0));
         __syncthreads();
         for (int g = 0; g < d.n_ops; ++g) {
-            const TileOp<R> op = fwd[d.op_off + g];
-            if (tile_apply<R, kSmallThreads>(psi, N, op, 0ull)) __syncthreads();
+            const typename Tr::Op op = fwd[d.op_off + g];
+            if (Tr::template fwd<kSmallThreads>(psi, N, op, 0ull)) __syncthreads();
         }
-        // lambda = H psi, diagonal terms evaluated from the index bits
+        // lambda = H psi; the diagonal part is evaluated from the index bits, per element in FP64
         for (uint32_t e = threadIdx.x; e < N; e += kSmallThreads) {
             double ev = 0.0, ox = 0.0, oy = 0.0;
             for (int k = 0; k < d.n_terms; ++k) {
                 const qs_term t = terms[d.term_off + k];
                 if (t.kind == QS_P_X) {
-                    const T w = psi[e ^ (1u << t.q0)];
-                    ox = fma(t.coef, (double)w.x, ox);
-                    oy = fma(t.coef, (double)w.y, oy);
+                    const double2 w = Tr::to_d(psi[e ^ (1u << t.q0)]);
+                    ox = fma(t.coef, w.x, ox);
+                    oy = fma(t.coef, w.y, oy);
                 } else {
                     const uint32_t par = t.kind == QS_P_Z ? ((e >> t.q0) & 1u) : (((e >> t.q0) ^ (e >> t.q1)) & 1u);
                     ev += par ? -t.coef : t.coef;
                 }
             }
-            const T v = psi[e];
-            T o;
-            o.x = (R)fma(ev, (double)v.x, ox);
-            o.y = (R)fma(ev, (double)v.y, oy);
-            lam[e] = o;
+            const double2 v = Tr::to_d(psi[e]);
+            lam[e] = Tr::from_d(make_double2(fma(ev, v.x, ox), fma(ev, v.y, oy)));
         }
         __syncthreads();
-        double acc = 0.0;
-        for (uint32_t e = threadIdx.x; e < N; e += kSmallThreads) acc += re_cb(psi[e], lam[e]);
-        const double en = block_sum_b(acc, red);
+        GAcc acc;
+        for (uint32_t e = threadIdx.x; e < N; e += kSmallThreads) Tr::re(acc, psi[e], lam[e], 1.0f);
+        const double en = block_sum_b(gacc_value(acc), red);
         if (threadIdx.x == 0) energies[d.e_out] = en;
         for (int g = 0; g < d.n_ops; ++g) {  // rev[] is already in reverse circuit order
-            const TileOp<R> op = rev[d.op_off + g];
-            adj_apply<R, kSmallThreads>(psi, lam, N, op, 0ull, red, rot_vals + d.rot_off);
+            const typename Tr::Op op = rev[d.op_off + g];
+            adj_apply<Tr, kSmallThreads>(psi, lam, N, op, 0ull, red, rot_vals + d.rot_off);
             __syncthreads();
         }
     }
@@ -399,9 +456,8 @@ void reverse_ops(const std::vector<Op>& f, std::vector<Op>& r) {
     }
 }
 
-template <class R>
-TileOp<R> make_op(const Op& o, const int* bit_of, int gen, int slot) {
-    TileOp<R> t{};
+template <class OpT>
+void rec_common(OpT& t, const Op& o, const int* bit_of, int gen, int slot) {
     t.kind = o.kind;
     t.cls = o.cls;
     t.tq = o.t;
@@ -410,18 +466,19 @@ TileOp<R> make_op(const Op& o, const int* bit_of, int gen, int slot) {
     t.cb = o.c >= 0 ? (bit_of ? bit_of[o.c] : o.c) : -1;
     t.pad0 = gen;
     t.pad1 = slot;
-    for (int j = 0; j < 8; ++j) t.m[j] = (R)o.m[j];
-    return t;
 }
 
-TileOpDF make_op_df(const Op& o, const int* bit_of) {
+// Device record of a lowered op: FP32 matrix (complex64) or double-float pairs (complex128).
+template <class OpT> OpT make_rec(const Op& o, const int* bit_of, int gen, int slot);
+template <> TileOp<float> make_rec<TileOp<float>>(const Op& o, const int* bit_of, int gen, int slot) {
+    TileOp<float> t{};
+    rec_common(t, o, bit_of, gen, slot);
+    for (int j = 0; j < 8; ++j) t.m[j] = (float)o.m[j];
+    return t;
+}
+template <> TileOpDF make_rec<TileOpDF>(const Op& o, const int* bit_of, int gen, int slot) {
     TileOpDF t{};
-    t.kind = o.kind;
-    t.cls = o.cls;
-    t.tq = o.t;
-    t.tb = bit_of[o.t];
-    t.cq = o.c;
-    t.cb = o.c >= 0 ? bit_of[o.c] : -1;
+    rec_common(t, o, bit_of, gen, slot);
     for (int j = 0; j < 8; ++j) split_to_floats(o.m[j], t.c[2 * j], t.c[2 * j + 1]);
     return t;
 }
@@ -520,8 +577,9 @@ namespace {
 cudaStream_t main_stream(qs_batch* b) { return b->own_stream ? b->own_stream : b->user_stream; }
 
 // Fill the staging buffer with op records for the given angles (host work).
-template <class R>
+template <class Tr>
 qs_status stage_ops(qs_batch* bt, const double* theta_all) {
+    using OpT = typename Tr::Op;
     for (size_t si = 0; si < bt->small.size(); ++si) {
         const int idx = bt->small[si];
         qs_instance in = bt->inst[idx];
@@ -530,17 +588,17 @@ qs_status stage_ops(qs_batch* bt, const double* theta_all) {
         if (qs_status st = lower_instance(in, ops)) return st;
         reverse_ops(ops, rops);
         const Region& reg = bt->small_fwd[si];
-        TileOp<R>* f = reinterpret_cast<TileOp<R>*>(bt->h_stage + bt->st_small_fwd.off) + reg.off;
-        TileOp<R>* r = reinterpret_cast<TileOp<R>*>(bt->h_stage + bt->st_small_rev.off) + reg.off;
+        OpT* f = reinterpret_cast<OpT*>(bt->h_stage + bt->st_small_fwd.off) + reg.off;
+        OpT* r = reinterpret_cast<OpT*>(bt->h_stage + bt->st_small_rev.off) + reg.off;
         int rot = 0;
         std::vector<int> rank(ops.size(), -1);
         for (size_t j = 0; j < ops.size(); ++j)
             if (rot_gen(in.gates[j].kind)) rank[j] = rot++;
         for (size_t j = 0; j < ops.size(); ++j) {
-            f[j] = make_op<R>(ops[j], nullptr, 0, -1);
+            f[j] = make_rec<OpT>(ops[j], nullptr, 0, -1);
             const size_t orig = ops.size() - 1 - j;
             const int gen = rot_gen(in.gates[orig].kind);
-            r[j] = make_op<R>(rops[j], nullptr, gen, gen ? rank[orig] : -1);
+            r[j] = make_rec<OpT>(rops[j], nullptr, gen, gen ? rank[orig] : -1);
         }
     }
     for (Group& g : bt->groups) {
@@ -551,32 +609,19 @@ qs_status stage_ops(qs_batch* bt, const double* theta_all) {
             std::vector<Op> ops, rops;
             if (qs_status st = lower_instance(in, ops)) return st;
             reverse_ops(ops, rops);
-            // forward: double-float records for complex128, FP32 records for complex64
+            OpT* f = reinterpret_cast<OpT*>(bt->h_stage + g.st_fwd.off) + k * g.fwd_per;
             size_t w = 0;
-            for (const PassDesc& d : g.fwd) {
-                for (int j : d.members) {
-                    if (bt->dt == QS_C128) {
-                        TileOpDF* f = reinterpret_cast<TileOpDF*>(bt->h_stage + g.st_fwd.off) + k * g.fwd_per;
-                        f[w++] = make_op_df(ops[j], d.bit_of);
-                    } else {
-                        TileOp<float>* f = reinterpret_cast<TileOp<float>*>(bt->h_stage + g.st_fwd.off) + k * g.fwd_per;
-                        f[w++] = make_op<float>(ops[j], d.bit_of, 0, -1);
-                    }
-                }
-            }
-            // reverse: rotation r (gate order) -> slot within its pass
-            std::vector<int> rank(ops.size(), -1);
-            int rot = 0;
-            for (size_t j = 0; j < ops.size(); ++j)
-                if (rot_gen(in.gates[j].kind)) rank[j] = rot++;
-            TileOp<R>* r = reinterpret_cast<TileOp<R>*>(bt->h_stage + g.st_rev.off) + k * g.rev_per;
+            for (const PassDesc& d : g.fwd)
+                for (int j : d.members) f[w++] = make_rec<OpT>(ops[j], d.bit_of, 0, -1);
+            // reverse: a rotation's gradient goes to its slot within the pass
+            OpT* r = reinterpret_cast<OpT*>(bt->h_stage + g.st_rev.off) + k * g.rev_per;
             w = 0;
             for (const PassDesc& d : g.rev) {
                 int slot = 0;
                 for (int j : d.members) {
                     const size_t orig = ops.size() - 1 - (size_t)j;
                     const int gen = rot_gen(in.gates[orig].kind);
-                    r[w++] = make_op<R>(rops[j], d.bit_of, gen, gen ? slot++ : -1);
+                    r[w++] = make_rec<OpT>(rops[j], d.bit_of, gen, gen ? slot++ : -1);
                 }
             }
         }
@@ -584,9 +629,10 @@ qs_status stage_ops(qs_batch* bt, const double* theta_all) {
     return QS_OK;
 }
 
-template <class R>
+template <class Tr>
 qs_status record(qs_batch* bt) {
-    using T = typename Amp<R>::T;
+    using T = typename Tr::G;
+    using OpT = typename Tr::Op;
     cudaStream_t ms = main_stream(bt);
     QS_CUDA_TRY(cudaMemcpyAsync(bt->d_stage, bt->h_stage, bt->stage_bytes, cudaMemcpyHostToDevice, ms));
     QS_CUDA_TRY(cudaEventRecord(bt->events[0], ms));
@@ -600,9 +646,9 @@ qs_status record(qs_batch* bt) {
         QS_CUDA_TRY(cudaMemsetAsync(bt->d_counter, 0, sizeof(int), st));
         const size_t smem = (size_t)2 * sizeof(T) << bt->small_nmax;
         int grid = std::min<int>((int)bt->small.size(), sm_count());
-        k_batch_small<R><<<grid, kSmallThreads, smem, st>>>(
-            bt->d_small, (int)bt->small.size(), reinterpret_cast<const TileOp<R>*>(bt->d_stage + bt->st_small_fwd.off),
-            reinterpret_cast<const TileOp<R>*>(bt->d_stage + bt->st_small_rev.off), bt->d_terms, bt->d_res, bt->d_res,
+        k_batch_small<Tr><<<grid, kSmallThreads, smem, st>>>(
+            bt->d_small, (int)bt->small.size(), reinterpret_cast<const OpT*>(bt->d_stage + bt->st_small_fwd.off),
+            reinterpret_cast<const OpT*>(bt->d_stage + bt->st_small_rev.off), bt->d_terms, bt->d_res, bt->d_res,
             bt->d_counter);
         QS_CUDA_TRY(cudaGetLastError());
     }
@@ -651,8 +697,8 @@ qs_status record(qs_batch* bt) {
             tp.inst_stride = N;
             tp.ops_stride = (int)g.rev_per;
             const unsigned tiles = (unsigned)(1ull << (g.n - tp.b));
-            k_tile_adj<R><<<dim3(tiles, count), kAdjThreads, smem, st>>>(
-                (T*)g.phi, (T*)g.lam, reinterpret_cast<const TileOp<R>*>(bt->d_stage + g.st_rev.off), tp, g.d_part,
+            k_tile_adj<Tr><<<dim3(tiles, count), kAdjThreads, smem, st>>>(
+                (T*)g.phi, (T*)g.lam, reinterpret_cast<const OpT*>(bt->d_stage + g.st_rev.off), tp, g.d_part,
                 g.n_slots);
             QS_CUDA_TRY(cudaGetLastError());
             if (g.rev_nslot_used[pi] > 0) {
@@ -688,8 +734,8 @@ qs_status allow_dynamic_smem(K* kernel) {
 qs_status build_batch(qs_batch* bt) {
     const bool c128 = bt->dt == QS_C128;
     const size_t amp = c128 ? 16 : 8;
-    const size_t rec_native = c128 ? sizeof(TileOp<double>) : sizeof(TileOp<float>);
-    const size_t rec_fwd = c128 ? sizeof(TileOpDF) : sizeof(TileOp<float>);
+    const size_t rec_native = c128 ? sizeof(TileOpDF) : sizeof(TileOp<float>);
+    const size_t rec_fwd = rec_native;
     // instances whose phi and lambda fit in one CTA's shared memory run whole in the persistent kernel
     int small_max = 0;
     while (small_max < 16 && ((size_t)2 * amp << (small_max + 1)) + 1024 <= smem_optin()) ++small_max;
@@ -880,11 +926,11 @@ qs_status build_batch(qs_batch* bt) {
     }
     // kernels that take more than 48 KiB of dynamic shared memory (set outside any graph capture)
     if (c128) {
-        if (qs_status st = allow_dynamic_smem(k_batch_small<double>)) return st;
-        if (qs_status st = allow_dynamic_smem(k_tile_adj<double>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_batch_small<TrDF>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_tile_adj<TrDF>)) return st;
     } else {
-        if (qs_status st = allow_dynamic_smem(k_batch_small<float>)) return st;
-        if (qs_status st = allow_dynamic_smem(k_tile_adj<float>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_batch_small<TrF>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_tile_adj<TrF>)) return st;
     }
     return QS_OK;
 }
@@ -977,7 +1023,7 @@ qs_status qs_batch_create(const qs_instance* batch, int n_inst, qs_dtype dt, voi
     }
     if (st == QS_OK) st = build_batch(bt);
     // first staging with the angles given here (they are read now, not kept)
-    if (st == QS_OK) st = dt == QS_C128 ? stage_ops<double>(bt, nullptr) : stage_ops<float>(bt, nullptr);
+    if (st == QS_OK) st = dt == QS_C128 ? stage_ops<TrDF>(bt, nullptr) : stage_ops<TrF>(bt, nullptr);
     for (int i = 0; i < n_inst; ++i) bt->inst[i].theta = nullptr;
     if (st != QS_OK) {
         free_batch(bt);
@@ -994,7 +1040,7 @@ qs_status qs_batch_execute(qs_batch* bt, const double* theta_all, double* energi
     cudaStream_t ms = main_stream(bt);
     if (theta_all) {
         for (size_t i = 0; i < bt->inst.size(); ++i) bt->inst[i].theta = theta_all + bt->param_off[i];
-        qs_status st = bt->dt == QS_C128 ? stage_ops<double>(bt, theta_all) : stage_ops<float>(bt, theta_all);
+        qs_status st = bt->dt == QS_C128 ? stage_ops<TrDF>(bt, theta_all) : stage_ops<TrF>(bt, theta_all);
         for (size_t i = 0; i < bt->inst.size(); ++i) bt->inst[i].theta = nullptr;
         if (st != QS_OK) return st;
     }
@@ -1002,7 +1048,7 @@ qs_status qs_batch_execute(qs_batch* bt, const double* theta_all, double* energi
     if (use_graph) {
         if (!bt->gexec) {
             QS_CUDA_TRY(cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal));
-            qs_status st = bt->dt == QS_C128 ? record<double>(bt) : record<float>(bt);
+            qs_status st = bt->dt == QS_C128 ? record<TrDF>(bt) : record<TrF>(bt);
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamEndCapture(ms, &g);
             if (st != QS_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -1012,7 +1058,7 @@ qs_status qs_batch_execute(qs_batch* bt, const double* theta_all, double* energi
         }
         QS_CUDA_TRY(cudaGraphLaunch(bt->gexec, ms));
     } else {
-        qs_status st = bt->dt == QS_C128 ? record<double>(bt) : record<float>(bt);
+        qs_status st = bt->dt == QS_C128 ? record<TrDF>(bt) : record<TrF>(bt);
         if (st != QS_OK) return st;
     }
     QS_CUDA_TRY(cudaStreamSynchronize(ms));

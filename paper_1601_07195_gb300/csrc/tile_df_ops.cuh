@@ -1,0 +1,140 @@
+// tile_df_ops.cuh -- shared-memory gate updates on a tile held as double-float
+// pairs (float4 = re.hi, re.lo, im.hi, im.lo; see df.cuh).  Same contract as
+// tile_ops.cuh: tile bits, per-tile factors for diagonal gates whose target
+// is not a tile bit, per-tile predicates for controls outside the tile.
+#pragma once
+
+#include "device.cuh"
+#include "df.cuh"
+
+namespace qs {
+
+template <int CLS>
+__device__ __forceinline__ void df_pair_update(const float* c, float4& a, float4& b) {
+    if constexpr (CLS == GC_GENERAL) {
+        const float4 a2 = df_cmul2(c, 0, 1, a, 2, 3, b);
+        const float4 b2 = df_cmul2(c, 4, 5, a, 6, 7, b);
+        a = a2; b = b2;
+    } else if constexpr (CLS == GC_REAL) {
+        const float4 a2 = df_rmul2(c, 0, a, 2, b);
+        const float4 b2 = df_rmul2(c, 4, a, 6, b);
+        a = a2; b = b2;
+    } else if constexpr (CLS == GC_DIAG) {
+        a = df_cmul(c, 0, 1, a);
+        b = df_cmul(c, 6, 7, b);
+    } else if constexpr (CLS == GC_DIAG1) {
+        b = df_cmul(c, 6, 7, b);
+    } else if constexpr (CLS == GC_ANTIDIAG) {
+        const float4 a2 = df_cmul(c, 2, 3, b);
+        const float4 b2 = df_cmul(c, 4, 5, a);
+        a = a2; b = b2;
+    } else {
+        const float4 t = a; a = b; b = t;
+    }
+}
+
+template <int CLS, int THREADS>
+__device__ __forceinline__ void df_tile_1q(float4* sm, uint32_t N, int tb, const float* c) {
+#pragma unroll 2
+    for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
+        const uint32_t i0 = insert_zero32(p, tb), i1 = i0 | (1u << tb);
+        float4 a, b;
+        if (CLS != GC_DIAG1) a = sm[i0];
+        b = sm[i1];
+        df_pair_update<CLS>(c, a, b);
+        if (CLS != GC_DIAG1) sm[i0] = a;
+        sm[i1] = b;
+    }
+}
+
+template <int CLS, int THREADS>
+__device__ __forceinline__ void df_tile_cu(float4* sm, uint32_t N, int cb, int tb, const float* c) {
+    const int lo = min(cb, tb), hi = max(cb, tb);
+#pragma unroll 2
+    for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
+        const uint32_t i0 = insert_two_zeros32(p, lo, hi) | (1u << cb), i1 = i0 | (1u << tb);
+        float4 a, b;
+        if (CLS != GC_DIAG1) a = sm[i0];
+        b = sm[i1];
+        df_pair_update<CLS>(c, a, b);
+        if (CLS != GC_DIAG1) sm[i0] = a;
+        sm[i1] = b;
+    }
+}
+
+// Multiply the tile (or the half with tile bit cb = 1) by matrix entry q11
+// (use22 = false) or q22 (use22 = true).
+template <bool USE22, int THREADS>
+__device__ __forceinline__ void df_tile_scale(float4* sm, uint32_t N, const float* c, int cb) {
+    if (cb < 0) {
+#pragma unroll 2
+        for (uint32_t e = threadIdx.x; e < N; e += THREADS) sm[e] = USE22 ? df_cmul(c, 6, 7, sm[e]) : df_cmul(c, 0, 1, sm[e]);
+    } else {
+#pragma unroll 2
+        for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
+            const uint32_t e = insert_zero32(p, cb) | (1u << cb);
+            sm[e] = USE22 ? df_cmul(c, 6, 7, sm[e]) : df_cmul(c, 0, 1, sm[e]);
+        }
+    }
+}
+
+template <int THREADS>
+__device__ __forceinline__ void df_tile_swap(float4* sm, uint32_t N, int ab, int bb) {
+    const int lo = min(ab, bb), hi = max(ab, bb);
+    for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
+        const uint32_t i = insert_two_zeros32(p, lo, hi);
+        const float4 x = sm[i | (1u << ab)];
+        sm[i | (1u << ab)] = sm[i | (1u << bb)];
+        sm[i | (1u << bb)] = x;
+    }
+}
+
+template <int THREADS>
+__device__ __forceinline__ void df_tile_pairs(float4* sm, uint32_t N, int cls, int cb, int tb, const float* c) {
+    if (cb < 0) {
+        switch (cls) {
+        case GC_GENERAL: df_tile_1q<GC_GENERAL, THREADS>(sm, N, tb, c); break;
+        case GC_REAL: df_tile_1q<GC_REAL, THREADS>(sm, N, tb, c); break;
+        case GC_DIAG: df_tile_1q<GC_DIAG, THREADS>(sm, N, tb, c); break;
+        case GC_DIAG1: df_tile_1q<GC_DIAG1, THREADS>(sm, N, tb, c); break;
+        case GC_ANTIDIAG: df_tile_1q<GC_ANTIDIAG, THREADS>(sm, N, tb, c); break;
+        default: df_tile_1q<GC_PERM, THREADS>(sm, N, tb, c); break;
+        }
+    } else {
+        switch (cls) {
+        case GC_GENERAL: df_tile_cu<GC_GENERAL, THREADS>(sm, N, cb, tb, c); break;
+        case GC_REAL: df_tile_cu<GC_REAL, THREADS>(sm, N, cb, tb, c); break;
+        case GC_DIAG: df_tile_cu<GC_DIAG, THREADS>(sm, N, cb, tb, c); break;
+        case GC_DIAG1: df_tile_cu<GC_DIAG1, THREADS>(sm, N, cb, tb, c); break;
+        case GC_ANTIDIAG: df_tile_cu<GC_ANTIDIAG, THREADS>(sm, N, cb, tb, c); break;
+        default: df_tile_cu<GC_PERM, THREADS>(sm, N, cb, tb, c); break;
+        }
+    }
+}
+
+template <int THREADS>
+__device__ __forceinline__ bool df_tile_apply(float4* sm, uint32_t N, const TileOpDF& op, uint64_t base) {
+    if (op.kind == OP_SWAP) {
+        df_tile_swap<THREADS>(sm, N, op.tb, op.cb);
+        return true;
+    }
+    int cb = -1;
+    if (op.kind == OP_CU) {
+        if (op.cb < 0) {
+            if (((base >> op.cq) & 1ull) == 0) return false;
+        } else {
+            cb = op.cb;
+        }
+    }
+    if (op.tb < 0) {
+        const bool bit = (base >> op.tq) & 1ull;
+        if (op.cls == GC_DIAG1 && !bit) return false;
+        if (bit) df_tile_scale<true, THREADS>(sm, N, op.c, cb);
+        else df_tile_scale<false, THREADS>(sm, N, op.c, cb);
+        return true;
+    }
+    df_tile_pairs<THREADS>(sm, N, op.cls, cb, op.tb, op.c);
+    return true;
+}
+
+}  // namespace qs
