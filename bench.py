@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 comparison step")
+    ap.add_argument("--workload", default="qft30", choices=["qft30", "random33", "adjoint28"],
+                    help="qft30: the headline n=30 step; random33: n=33 complex128 / n=34 complex64 500-gate "
+                         "circuits and the n=26 error table; adjoint28: n=28 complex64 adjoint vs parameter shift")
     return ap.parse_args()
 
 
@@ -450,10 +453,130 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _timed(fn, stream, torch):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def run_random33(args):
+    """500-gate random circuits at n=33 complex128 and n=34 complex64 (128 GiB each),
+    and the error of both precisions against the FP64 oracle at n=26."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1601_07195_gb300 import qs
+    from oracle import oracle as O
+    seed = G.SEEDS["random33"]
+    out = {"workload": "random33", "runs": []}
+    for n, dt, s_bytes in ((33, qs.QS_C128, 16), (34, qs.QS_C64, 8)):
+        gates, _ = G.random_circuit(n, 500, seed)
+        stream = torch.cuda.Stream()
+        st = qs.State.create(n, dt, stream=stream)
+        plan = st.plan(gates)
+        bytes_ = sum(gate_cost(g, n, s_bytes)[0] for g in gates)
+        times = []
+        for rep in range(1 + max(1, args.steps)):
+            st.init_basis(0)
+            ms, _ = _timed(plan.execute, stream, torch)
+            if rep >= 1:
+                times.append(ms)
+        nrm = st.norm()
+        ms = statistics.mean(times)
+        out["runs"].append({"n": n, "dtype": "c128" if dt == qs.QS_C128 else "c64", "gates": len(gates),
+                            "passes": plan.stats()["passes"], "ms_per_circuit": ms,
+                            "gates_per_s": len(gates) / (ms / 1e3), "GBps": bytes_ / (ms / 1e3) / 1e9,
+                            "hbm_frac_of_measured": bytes_ / (ms / 1e3) / 6794.8e9, "norm_minus_1": nrm - 1.0})
+        plan.close()
+        st.close()
+        torch.cuda.empty_cache()
+    # error table at n = 26 (same circuit family and seed)
+    n = 26
+    gates, _ = G.random_circuit(n, 500, seed)
+    t0 = time.perf_counter()
+    ref = O.simulate(n, gates)
+    t_oracle = time.perf_counter() - t0
+    z0 = G.terms([(G.P_Z, 0, -1, 1.0)])
+    ref_z0 = O.expect(ref, z0)
+    for dt, name in ((qs.QS_C128, "c128"), (qs.QS_C64, "c64")):
+        with qs.State.create(n, dt) as st:
+            st.run(gates)
+            amp = st.to_numpy()
+            out.setdefault("error_n26", {})[name] = {
+                "max_abs_amplitude": float(np.max(np.abs(amp - ref))),
+                "norm_minus_1": st.norm() - 1.0, "z0_error": st.expect(z0) - ref_z0}
+    out["error_n26"]["oracle_seconds_single_core"] = t_oracle
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint28(args):
+    """Adjoint gradient of the n=28 complex64 Ising workload (L=20, 1120 angles)
+    against parameter shift (2 forward simulations per angle) on the same GPU."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1601_07195_gb300 import qs
+    n, layers = 28, 20
+    seed = G.SEEDS["adjoint28"]
+    gates, p = G.ansatz(n, layers)
+    theta = G.angles(p, seed)
+    obs = G.ising_observable(n, seed + 1)
+    inst = [{"n": n, "gates": gates, "theta": theta, "terms": obs}]
+    res = {"workload": "adjoint28", "n": n, "params": p, "gates": len(gates)}
+    for dt, name in ((qs.QS_C64, "c64"), (qs.QS_C128, "c128")):
+        b = qs.Batch(inst, dt)
+        b.execute()  # plans and captures
+        t0 = time.perf_counter()
+        reps = max(1, args.steps)
+        for _ in range(reps):
+            e, g = b.execute()
+        res[f"adjoint_s_{name}"] = (time.perf_counter() - t0) / reps
+        res[f"energy_{name}"] = float(e[0])
+        res[f"grad_{name}"] = g[0]
+        b.close()
+        torch.cuda.empty_cache()
+    res["grad_max_abs_c64_vs_c128"] = float(np.max(np.abs(res["grad_c64"] - res["grad_c128"])))
+    res["energy_c64_minus_c128"] = res["energy_c64"] - res["energy_c128"]
+    # parameter shift on the same GPU: 2 planned forward simulations + expectation per angle (sampled)
+    stream = torch.cuda.Stream()
+    with qs.State.create(n, qs.QS_C64, stream=stream) as st:
+        def energy(th):
+            st.init_basis(0)
+            pl = st.plan(gates, th)
+            pl.execute()
+            e = st.expect(obs)
+            pl.close()
+            return e
+        energy(theta)
+        sample = 6
+        t0 = time.perf_counter()
+        shift = []
+        for k in range(sample):
+            tp, tm = theta.copy(), theta.copy()
+            tp[k] += np.pi / 2
+            tm[k] -= np.pi / 2
+            shift.append(0.5 * (energy(tp) - energy(tm)))
+        t_ps = (time.perf_counter() - t0) / sample
+    res["param_shift_s_per_angle"] = t_ps
+    res["param_shift_s_all_angles_extrapolated"] = t_ps * p
+    res["param_shift_sample"] = sample
+    res["param_shift_vs_adjoint_c64_max_abs"] = float(np.max(np.abs(np.array(shift) - res["grad_c64"][:sample])))
+    res["speedup_adjoint_c64_vs_param_shift"] = t_ps * p / res["adjoint_s_c64"]
+    res["grad_c64"] = None
+    res["grad_c128"] = None
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "random33":
+        run_random33(args)
+    elif args.workload == "adjoint28":
+        run_adjoint28(args)
     else:
         run_ours(args)
 

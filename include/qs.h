@@ -142,8 +142,11 @@ enum {
 /* Build an execution plan for `gates` (copied in) on state s: gate classes,
  * fused tile passes of gates whose mixing qubits fit one tile (Section 4.4,
  * Fig. 5), single-gate passes for the rest.  theta (n_params angles) is read
- * for the rotation kinds; it is copied in too.  tile_bits = log2 amplitudes
- * per tile (0 = automatic). */
+ * for the rotation kinds; it is copied in too.
+ * tile_bits: bits 0-7 = log2 amplitudes per tile, bits 8-15 = how many of the
+ * lowest qubits every tile contains (contiguous runs of 2^run amplitudes in
+ * device memory); 0 in either field = the tuned value for (dtype, n), see
+ * qs_tune_set / qs_autotune, else the built-in default. */
 QS_API qs_status qs_plan_create(qs_state* s, const qs_gate* gates, int n_gates, const double* theta, int n_params,
                          int flags, int tile_bits, qs_plan** out);
 
@@ -174,6 +177,24 @@ QS_API qs_status qs_plan_pass_times(qs_plan* p, int record, float* ms);
 
 /* Free the plan; waits for the plan's launches on the state's stream first. */
 QS_API qs_status qs_plan_destroy(qs_plan* p);
+
+/* ---- tile-shape tuning (the planner's fusion block size) ------------------- */
+
+/* Record the tile shape plans of (dt, n) use when qs_plan_create gets 0:
+ * 2^tile_bits amplitudes per tile, the lowest run_bits qubits in every tile.
+ * Process-wide, thread-safe. */
+QS_API qs_status qs_tune_set(qs_dtype dt, int n, int tile_bits, int run_bits);
+
+/* The tile shape in effect for (dt, n) (tuned or built-in default). */
+QS_API qs_status qs_tune_get(qs_dtype dt, int n, int* tile_bits, int* run_bits);
+
+/* Autotuner: time the circuit `gates` on state s (its contents are
+ * overwritten) for every tile shape that fits shared memory (tile bits from 9
+ * or 10 up to the largest that fits, run bits 3..6), with CUDA events over
+ * `reps` executions after one warm-up; record the fastest with qs_tune_set
+ * and return it.  Synchronises the state's stream. */
+QS_API qs_status qs_autotune(qs_state* s, const qs_gate* gates, int n_gates, const double* theta, int n_params,
+                             int reps, int* best_tile_bits, int* best_run_bits, float* best_ms);
 
 /* Plan, execute and destroy in one call. */
 QS_API qs_status qs_run(qs_state* s, const qs_gate* gates, int n_gates, const double* theta, int n_params);

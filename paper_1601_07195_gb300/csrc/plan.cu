@@ -16,6 +16,8 @@
 // rounding) as applying the gates one at a time.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "device.cuh"
@@ -37,9 +39,17 @@ struct PlanPass {
 
 inline int popc(uint64_t x) { return __builtin_popcountll(x); }
 
-void default_tile(qs_dtype dt, int& b, int& b0) {
+// Tile shape per (dtype, n): built-in defaults, overridden by qs_tune_set
+// (the autotuner's choices).
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, std::pair<int, int>> g_tune;
+
+void default_tile(qs_dtype dt, int n, int& b, int& b0) {
     if (dt == QS_C128) { b = 12; b0 = 4; }
     else { b = 13; b0 = 5; }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find({(int)dt, n});
+    if (it != g_tune.end()) { b = it->second.first; b0 = it->second.second; }
 }
 
 }  // namespace
@@ -256,13 +266,15 @@ qs_status qs_plan_create(qs_state* s, const qs_gate* gates, int n_gates, const d
     std::vector<Op> ops;
     if (qs_status st = lower_gates(gates, n_gates, theta, n_params, s->n, ops)) return st;
     int b, b0;
-    default_tile(s->dt, b, b0);
-    if (tile_bits > 0) {
-        if (tile_bits > kMaxTileBits || tile_smem_bytes(s->dt, tile_bits) + ((size_t)8 << (tile_bits - std::min(b0, tile_bits))) > smem_optin())
-            return fail(QS_EINVAL, "tile_bits too large for shared memory");
-        b = tile_bits;
-        if (b0 > b) b0 = b;
-    }
+    default_tile(s->dt, s->n, b, b0);
+    const int req_b = tile_bits & 0xFF, req_b0 = (tile_bits >> 8) & 0xFF;
+    if (tile_bits < 0 || req_b > kMaxTileBits || req_b0 > kMaxTileBits) return fail(QS_EINVAL, "bad tile_bits");
+    if (req_b > 0) b = req_b;
+    if (req_b0 > 0) b0 = req_b0;
+    if (b0 > b) b0 = b;
+    if (!(flags & QS_PLAN_DRY_RUN) &&  // a host-only plan is not bound by this device's shared memory
+        tile_smem_bytes(s->dt, std::min(b, s->n)) + ((size_t)8 << (std::min(b, s->n) - std::min(b0, s->n))) > smem_optin())
+        return fail(QS_EINVAL, "tile shape too large for shared memory");
     qs_plan* p = new (std::nothrow) qs_plan();
     if (!p) return fail(QS_ENOMEM, "host allocation failed");
     p->s = s;
@@ -372,6 +384,65 @@ qs_status qs_plan_destroy(qs_plan* p) {
     if (p->d_ops) cudaFree(p->d_ops);
     if (p->d_ops_f64) cudaFree(p->d_ops_f64);
     delete p;
+    return QS_OK;
+}
+
+qs_status qs_tune_set(qs_dtype dt, int n, int tile_bits, int run_bits) {
+    if (dt != QS_C64 && dt != QS_C128) return fail(QS_EDTYPE, "unknown dtype");
+    if (n < 1 || n > 40 || tile_bits < 1 || tile_bits > kMaxTileBits || run_bits < 0 || run_bits > tile_bits)
+        return fail(QS_EINVAL, "bad tuning entry");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[{(int)dt, n}] = {tile_bits, run_bits};
+    return QS_OK;
+}
+
+qs_status qs_tune_get(qs_dtype dt, int n, int* tile_bits, int* run_bits) {
+    if (!tile_bits || !run_bits) return fail(QS_EINVAL, "NULL argument");
+    int b, b0;
+    default_tile(dt, n, b, b0);
+    *tile_bits = b;
+    *run_bits = b0;
+    return QS_OK;
+}
+
+qs_status qs_autotune(qs_state* s, const qs_gate* gates, int n_gates, const double* theta, int n_params, int reps,
+                      int* best_tile_bits, int* best_run_bits, float* best_ms) {
+    if (!s || !s->data) return fail(QS_EINVAL, "state handle is NULL");
+    if (reps < 1 || reps > 100) return fail(QS_EINVAL, "reps must be in [1, 100]");
+    const int bmin = s->dt == QS_C128 ? 9 : 10;
+    float best = 1e30f;
+    int bb = 0, bb0 = 0;
+    cudaEvent_t e0, e1;
+    QS_CUDA_TRY(cudaEventCreate(&e0));
+    QS_CUDA_TRY(cudaEventCreate(&e1));
+    qs_status out = QS_OK;
+    for (int b = std::min(bmin, s->n); b <= std::min(kMaxTileBits, s->n) && out == QS_OK; ++b) {
+        for (int b0 = 3; b0 <= 6 && b0 <= b - 2; ++b0) {
+            if (tile_smem_bytes(s->dt, b) + ((size_t)8 << (b - b0)) > smem_optin()) continue;
+            qs_plan* p = nullptr;
+            out = qs_plan_create(s, gates, n_gates, theta, n_params, QS_PLAN_DEFAULT, b | (b0 << 8), &p);
+            if (out != QS_OK) break;
+            out = qs_plan_execute(p);  // warm-up
+            float ms = 0.0f;
+            if (out == QS_OK && cudaEventRecord(e0, s->stream) == cudaSuccess) {
+                for (int r = 0; r < reps && out == QS_OK; ++r) out = qs_plan_execute(p);
+                cudaEventRecord(e1, s->stream);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= reps;
+            }
+            qs_plan_destroy(p);
+            if (out == QS_OK && ms < best) { best = ms; bb = b; bb0 = b0; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (out != QS_OK) return out;
+    if (bb == 0) return fail(QS_EINVAL, "no tile shape fits this state");
+    qs_tune_set(s->dt, s->n, bb, bb0);
+    if (best_tile_bits) *best_tile_bits = bb;
+    if (best_run_bits) *best_run_bits = bb0;
+    if (best_ms) *best_ms = best;
     return QS_OK;
 }
 

@@ -380,3 +380,18 @@ def test_c128_df_error_at_n22_random(qs):
     err = float(np.max(np.abs(got - want)))
     print(f"n={n} 600 gates double-float max-abs error {err:.3e}")
     assert err < 1e-13
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_autotuner_picks_a_valid_shape_and_stays_exact(qs, dt):
+    from paper_1601_07195_gb300 import autotune as A
+    n = 16
+    gates, _ = G.random_circuit(n, 200, 606)
+    entry = A.tune(n, dt, gates=gates, reps=1, cache=None)
+    b, b0 = A.tune_get(dt, n)
+    assert (b, b0) == (entry["tile_bits"], entry["run_bits"]) and 3 <= b0 <= b - 2 and entry["ms"] > 0
+    want = O.simulate(n, gates)
+    with qs.State.create(n, dt) as s:
+        s.run(gates)  # planned with the tuned shape
+        got = s.to_numpy()
+    assert np.max(np.abs(got - want)) < TOL[dt]

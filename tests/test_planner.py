@@ -119,3 +119,26 @@ def test_no_fusion_keeps_circuit_order():
     st = fake_state(n, 1)
     p = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN | qs.PLAN_NO_FUSION)
     assert [g for ps in p.passes() for g in ps["gates"]] == list(range(len(gates)))
+
+
+def test_tuning_table_roundtrip_and_planner_uses_it():
+    from paper_1601_07195_gb300 import autotune as A
+    assert A.tune_get(qs.QS_C64, 17) == (13, 5)  # built-in default
+    A.tune_set(qs.QS_C64, 17, 9, 3)
+    assert A.tune_get(qs.QS_C64, 17) == (9, 3)
+    st = fake_state(17, qs.QS_C64)
+    p = qs.Plan(st, G.random_circuit(17, 100, 2)[0], flags=qs.PLAN_DRY_RUN)
+    assert all(bin(x["mask"]).count("1") == 9 for x in p.passes() if x["kind"] == "tile")
+    A.tune_set(qs.QS_C64, 17, 13, 5)
+    with pytest.raises(qs.QSError):
+        A.tune_set(qs.QS_C64, 17, 20, 3)
+
+
+def test_autotune_cache_file_roundtrip(tmp_path, monkeypatch):
+    from paper_1601_07195_gb300 import autotune as A
+    cache = tmp_path / "tune.json"
+    import json
+    cache.write_text(json.dumps({"FAKE GPU": {"c128/21": {"tile_bits": 11, "run_bits": 4, "ms": 1.0, "gates": 10}}}))
+    assert A.apply_cache(str(cache), device="FAKE GPU") == 1
+    assert A.tune_get(qs.QS_C128, 21) == (11, 4)
+    assert A.apply_cache(str(cache), device="OTHER") == 0
