@@ -109,6 +109,21 @@ def gate_cost(g, n, s, table=None):
     raise ValueError("rotation kinds are not part of this workload")
 
 
+_CLASSES = ["general", "real", "diag", "diag1", "antidiag", "perm"]
+
+
+def kernel_flops(counts, n, table):
+    """Flops of the updates a pass's kernel applies (after fusion), from the plan's
+    per-pass op counts (rows: single-qubit, controlled, swap; columns: classes)."""
+    N = float(1 << n)
+    total = 0.0
+    for c, name in enumerate(_CLASSES):
+        touched_1q = 0.5 if name == "diag1" else 1.0
+        touched_cu = 0.25 if name == "diag1" else 0.5
+        total += counts[0][c] * table[name] * N * touched_1q + counts[1][c] * table[name] * N * touched_cu
+    return total
+
+
 # ---- clocks ----------------------------------------------------------------------
 
 CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -306,6 +321,7 @@ def run_ours(args):
     plan = state.plan(gates)
     plan_ms = 1e3 * (time.perf_counter() - t0)
     passes = plan.passes()
+    device_ops = plan.stats()["device_ops"]
     plan.set_timing(args.steps)
 
     def step():
@@ -351,15 +367,17 @@ def run_ours(args):
     df = dtype == qs.QS_C128
     # FP32 flops of the kernel's own algorithm: double-float update for complex128, plain FP32 for complex64
     table = _DF_FLOPS if df else _FLOPS
-    fp32_flops = sum(sum(gate_cost(gates[j], n, s_bytes, table)[1] for j in passes[i]["gates"]) for i in tile_idx)
+    fp32_flops = sum(kernel_flops(plan.op_counts(i), n, table) for i in tile_idx)
     achieved_tf = fp32_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
     roofline = {"bound": "alu", "kernel": "k_tile_df (fused tile pass, double-float)" if df else "k_tile<float>",
                 "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; MEASURED_PEAKS.json "
                                "has no FP32 figure (an FFMA probe on this GPU measured 74.2 TFLOP/s)",
-                "flops_counted": "FP32 flops of the double-float update per touched amplitude: general 116, "
-                                 "real/diagonal/anti-diagonal 56, permutation 0" if df else "FP32 flops of the update",
+                "flops_counted": ("FP32 flops of the double-float updates the kernel applies (after in-pass "
+                                  "fusion of same-qubit gates) per touched amplitude: general 116, "
+                                  "real/diagonal/anti-diagonal 56, permutation 0") if df else
+                                 "FP32 flops of the updates the kernel applies",
                 "fp64_equivalent_tflops": fp64_tf,
                 "fp64_equivalent_frac_of_fp64_peak": fp64_tf / FP64_PEAK_TFLOPS,
                 "launches_per_step": len(tile_idx), "avg_launch_ms": tile_launch_ms,
@@ -437,6 +455,7 @@ def run_ours(args):
                        if dtype == qs.QS_C128 else "complex64 state, FP32 arithmetic, FP64 reductions"},
             "hbm_frac_of_measured": value / 6794.8,
             "breakdown": {"plan_ms": plan_ms, "gates_ms": gates_ms, "tile_ms": tile_ms, "passes": len(passes),
+                          "device_ops_after_fusion": device_ops,
                           "tile_passes": len(tile_idx), "gates_in_tile_passes": kinds.get("tile", 0),
                           "gates_in_single_passes": kinds.get("single", 0), "gate_bytes": gate_bytes,
                           "gates_per_s": len(gates) / (gates_ms / 1e3)},

@@ -136,7 +136,9 @@ enum {
                                double): faster on GPUs whose FP64 rate is a small fraction of
                                FP32, with a per-gate error of order 2^-44 relative to the
                                amplitudes involved instead of 2^-53. */
-    QS_PLAN_DRY_RUN = 8     /* plan on the host only (no device memory); cannot execute */
+    QS_PLAN_DRY_RUN = 8,    /* plan on the host only (no device memory); cannot execute */
+    QS_PLAN_NO_MERGE = 16   /* keep every gate separate: no product of adjacent single-qubit
+                               gates on the same qubit inside a tile pass */
 };
 
 /* Build an execution plan for `gates` (copied in) on state s: gate classes,
@@ -156,6 +158,17 @@ QS_API qs_status qs_plan_execute(qs_plan* p);
 /* Plan statistics: number of passes over the state, of which tile passes,
  * and the kernel launches one execution makes. */
 QS_API qs_status qs_plan_stats(const qs_plan* p, int* n_passes, int* n_tile_passes, int* n_launches);
+
+/* Gate updates one execution applies after fusing adjacent single-qubit gates
+ * on the same qubit within a tile pass (into their product, where that is
+ * cheaper to apply; exact identities are dropped). */
+QS_API qs_status qs_plan_device_ops(const qs_plan* p, int* n_ops);
+
+/* Gate updates of pass i as the kernels apply them (after fusion): counts[3][6]
+ * by operation (0 = single-qubit, 1 = controlled, 2 = swap) and class
+ * (0 general, 1 real, 2 diagonal, 3 diagonal with q11 = 1, 4 anti-diagonal,
+ * 5 permutation). */
+QS_API qs_status qs_plan_pass_op_counts(const qs_plan* p, int i, int* counts);
 
 /* Per-pass description: for pass i, its kind (0 = single gate, 1 = tile),
  * first gate and gate count in plan order, and the tile's qubit mask. */

@@ -35,6 +35,7 @@ struct PlanPass {
     int n_gates;
     bool moves_only; // every gate is a permutation (X, CNOT, SWAP): run bit-exact on doubles
     std::vector<int> members;  // circuit positions of the pass's gates, in execution order
+    int op_counts[3][6];       // ops the kernel applies, by kind (1q, controlled, swap) and class
 };
 
 inline int popc(uint64_t x) { return __builtin_popcountll(x); }
@@ -67,6 +68,7 @@ struct qs_plan {
     std::vector<cudaEvent_t> events;
     int records = 0;
     int next_record = 0;
+    int device_ops = 0;  // gate updates the kernels apply per execution (after fusion)
 };
 
 namespace qs {
@@ -113,6 +115,75 @@ qs_status upload_ops(const std::vector<OpT>& v, void** dst) {
     return QS_OK;
 }
 
+// ---- matrix fusion of single-qubit gates inside a pass ---------------------------
+// Two single-qubit gates on the same qubit with nothing on that qubit between
+// them (in the pass's execution order) are replaced by their product when the
+// product's class is cheaper to apply than the two classes plus one op's
+// fixed overhead (index math, op read, barrier).  Costs are instructions per
+// amplitude pair of the tile kernels: double-float for complex128, FP32 for
+// complex64.  A product that is exactly the identity is dropped.
+int class_cost(int cls, qs_dtype dt) {
+    static const int df[] = {200, 92, 92, 50, 92, 16};   // general, real, diag, diag1, antidiag, perm
+    static const int f32[] = {48, 32, 32, 20, 32, 16};
+    return dt == QS_C128 ? df[cls] : f32[cls];
+}
+
+void matmul2(const double* B, const double* A, double* M) {  // M = B A (A applied first)
+    auto mul = [](double ar, double ai, double br, double bi, double& r, double& i) { r = ar * br - ai * bi; i = ar * bi + ai * br; };
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) {
+            double x1r, x1i, x2r, x2i;
+            mul(B[2 * (2 * r + 0)], B[2 * (2 * r + 0) + 1], A[2 * (2 * 0 + c)], A[2 * (2 * 0 + c) + 1], x1r, x1i);
+            mul(B[2 * (2 * r + 1)], B[2 * (2 * r + 1) + 1], A[2 * (2 * 1 + c)], A[2 * (2 * 1 + c) + 1], x2r, x2i);
+            M[2 * (2 * r + c)] = x1r + x2r;
+            M[2 * (2 * r + c) + 1] = x1i + x2i;
+        }
+}
+
+bool is_identity(const double* m) {
+    return m[0] == 1.0 && m[1] == 0.0 && m[2] == 0.0 && m[3] == 0.0 && m[4] == 0.0 && m[5] == 0.0 && m[6] == 1.0 &&
+           m[7] == 0.0;
+}
+
+std::vector<Op> fuse_single_qubit(const std::vector<Op>& ops, const std::vector<int>& members, qs_dtype dt,
+                                  bool enable) {
+    std::vector<Op> out;
+    std::vector<char> dead;
+    int pending[64];
+    for (int q = 0; q < 64; ++q) pending[q] = -1;
+    const int overhead = 12;
+    for (int j : members) {
+        const Op& o = ops[j];
+        if (enable && o.kind == OP_1Q && pending[o.t] >= 0) {
+            Op& a = out[pending[o.t]];
+            Op m = a;
+            matmul2(o.m, a.m, m.m);
+            m.cls = classify(m.m);
+            if (is_identity(m.m)) {
+                dead[pending[o.t]] = 1;
+                pending[o.t] = -1;
+                continue;
+            }
+            if (class_cost(m.cls, dt) <= class_cost(a.cls, dt) + class_cost(o.cls, dt) + overhead) {
+                a = m;
+                continue;
+            }
+        }
+        if (o.kind == OP_1Q) {
+            pending[o.t] = (int)out.size();
+        } else {
+            pending[o.t] = -1;
+            if (o.c >= 0) pending[o.c] = -1;
+        }
+        out.push_back(o);
+        dead.push_back(0);
+    }
+    std::vector<Op> live;
+    for (size_t i = 0; i < out.size(); ++i)
+        if (!dead[i]) live.push_back(out[i]);
+    return live;
+}
+
 template <class OpT>
 qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse, bool upload) {
     std::vector<PassDesc> descs;
@@ -128,19 +199,24 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
         if (!d.tile) {
             pp.kind = 0;
             pp.op = ops[d.members[0]];
+            pp.op_counts[pp.op.kind][pp.op.cls] += 1;
+            p->device_ops += 1;
             p->passes.push_back(pp);
             continue;
         }
         pp.kind = 1;
         pp.tp = d.tp;
         pp.tp.op0 = (int)tops.size();
-        pp.tp.nops = (int)d.members.size();
+        const std::vector<Op> fused = fuse_single_qubit(ops, d.members, p->s->dt, !(p->flags & QS_PLAN_NO_MERGE));
+        pp.tp.nops = (int)fused.size();
         pp.moves_only = true;
-        for (int j : d.members) {
-            tops.push_back(to_tile_op<OpT>(ops[j], d.bit_of));
-            if (df) t64.push_back(to_tile_op<TileOp<double>>(ops[j], d.bit_of));
-            if (!(ops[j].kind == OP_SWAP || ops[j].cls == GC_PERM)) pp.moves_only = false;
+        for (const Op& o : fused) {
+            pp.op_counts[o.kind][o.cls] += 1;
+            tops.push_back(to_tile_op<OpT>(o, d.bit_of));
+            if (df) t64.push_back(to_tile_op<TileOp<double>>(o, d.bit_of));
+            if (!(o.kind == OP_SWAP || o.cls == GC_PERM)) pp.moves_only = false;
         }
+        p->device_ops += (int)fused.size();
         p->passes.push_back(pp);
     }
     if (upload) {
@@ -316,6 +392,19 @@ qs_status qs_plan_execute(qs_plan* p) {
         QS_CUDA_TRY(cudaGraphInstantiate(&p->gexec, g, 0));
     }
     QS_CUDA_TRY(cudaGraphLaunch(p->gexec, p->s->stream));
+    return QS_OK;
+}
+
+qs_status qs_plan_pass_op_counts(const qs_plan* p, int i, int* counts) {
+    if (!p || !counts) return fail(QS_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
+    std::memcpy(counts, p->passes[i].op_counts, sizeof(p->passes[i].op_counts));
+    return QS_OK;
+}
+
+qs_status qs_plan_device_ops(const qs_plan* p, int* n_ops) {
+    if (!p || !n_ops) return fail(QS_EINVAL, "NULL argument");
+    *n_ops = p->device_ops;
     return QS_OK;
 }
 

@@ -14,7 +14,7 @@ namespace qs {
 namespace {
 
 #ifndef QS_TILE_DF_THREADS
-#define QS_TILE_DF_THREADS 512
+#define QS_TILE_DF_THREADS 256
 #endif
 constexpr int kThreads = QS_TILE_DF_THREADS;
 

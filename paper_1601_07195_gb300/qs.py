@@ -17,7 +17,7 @@ QS_C64, QS_C128 = 0, 1
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EDTYPE = range(6)
 QS_G_U1, QS_G_CU, QS_G_SWAP, QS_G_RX, QS_G_RY, QS_G_RZ = range(6)
 QS_P_Z, QS_P_ZZ, QS_P_X = range(3)
-PLAN_DEFAULT, PLAN_NO_FUSION, PLAN_GRAPH, PLAN_ARITH_F64, PLAN_DRY_RUN = 0, 1, 2, 4, 8
+PLAN_DEFAULT, PLAN_NO_FUSION, PLAN_GRAPH, PLAN_ARITH_F64, PLAN_DRY_RUN, PLAN_NO_MERGE = 0, 1, 2, 4, 8, 16
 
 _STATUS = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EDTYPE"}
 
@@ -57,6 +57,8 @@ _SIGS = {
     "qs_plan_pass": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                      ctypes.POINTER(ctypes.c_uint64)],
     "qs_plan_pass_gates": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "qs_plan_device_ops": [_vp, ctypes.POINTER(ctypes.c_int)],
+    "qs_plan_pass_op_counts": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "qs_plan_set_timing": [_vp, ctypes.c_int],
     "qs_plan_pass_times": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)],
     "qs_plan_destroy": [_vp],
@@ -261,9 +263,10 @@ class Plan:
         _check(load().qs_plan_execute(self._h))
 
     def stats(self):
-        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(load().qs_plan_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-        return {"passes": a.value, "tile_passes": b.value, "launches": c.value}
+        _check(load().qs_plan_device_ops(self._h, ctypes.byref(d)))
+        return {"passes": a.value, "tile_passes": b.value, "launches": c.value, "device_ops": d.value}
 
     def passes(self):
         out = []
@@ -284,6 +287,12 @@ class Plan:
         out = (ctypes.c_float * max(1, n))()
         _check(load().qs_plan_pass_times(self._h, record, out))
         return np.array(out[:n], dtype=np.float64)
+
+    def op_counts(self, i):
+        """3x6 array: ops of pass i by (single-qubit, controlled, swap) x gate class."""
+        buf = (ctypes.c_int * 18)()
+        _check(load().qs_plan_pass_op_counts(self._h, i, buf))
+        return np.array(buf[:], dtype=np.int64).reshape(3, 6)
 
     def close(self):
         if self._h is not None and self._h.value:

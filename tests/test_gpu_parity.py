@@ -395,3 +395,34 @@ def test_autotuner_picks_a_valid_shape_and_stays_exact(qs, dt):
         s.run(gates)  # planned with the tuned shape
         got = s.to_numpy()
     assert np.max(np.abs(got - want)) < TOL[dt]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_single_qubit_fusion_matches_unfused_and_oracle(qs, dt):
+    """Adjacent single-qubit gates on a qubit are multiplied into one matrix inside
+    a tile pass; the result matches the unmerged plan and the oracle, and an
+    exact identity (X X) disappears from the launch while the state stays bit-exact."""
+    n = 15
+    gates = G.concat([G.random_circuit(n, 600, 8080)[0], G.gate_u1(3, G.MAT_H), G.gate_u1(3, G.MAT_T),
+                      G.gate_u1(3, G.haar_2x2(G.SplitMix64(1)))])
+    psi = rand_state(n, 77)
+    want = O.run(expected_input(psi, dt), gates)
+    outs = {}
+    for flags in (qs.PLAN_DEFAULT, qs.PLAN_NO_MERGE):
+        with upload(qs, n, dt, psi) as s:
+            p = s.plan(gates, flags=flags)
+            outs[flags] = (p.stats()["device_ops"], None)
+            p.execute()
+            outs[flags] = (outs[flags][0], s.to_numpy())
+            p.close()
+    assert outs[qs.PLAN_DEFAULT][0] < outs[qs.PLAN_NO_MERGE][0] == len(gates)
+    for flags, (_, got) in outs.items():
+        assert np.max(np.abs(got - want)) < 5 * TOL[dt]
+    xx = G.concat([G.gate_u1(2, G.MAT_X), G.gate_u1(2, G.MAT_X), G.gate_cu(0, 5, G.MAT_X), G.gate_u1(9, G.MAT_X)])
+    with upload(qs, n, dt, psi) as s:
+        p = s.plan(xx)
+        assert p.stats()["device_ops"] == 2
+        p.execute()
+        got = s.to_numpy()
+        p.close()
+    assert np.array_equal(got, O.run(expected_input(psi, dt), xx).astype(got.dtype))
