@@ -333,7 +333,7 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         nrm, marg = step()
-    if abs(nrm - 1.0) > 1e-9:
+    if abs(nrm - 1.0) > (1e-9 if dtype == qs.QS_C128 else 1e-4):  # complex64: FP32 rounding drift
         raise RuntimeError(f"norm drifted: {nrm}")
 
     def barrier():

@@ -33,37 +33,56 @@ __device__ __forceinline__ void df_pair_update(const float* c, float4& a, float4
     }
 }
 
+// Each thread takes two pairs per step (p and p + THREADS), loads both before
+// computing: the two double-float updates are independent chains the
+// scheduler can interleave.
 template <int CLS, int THREADS>
 __device__ __forceinline__ void df_tile_1q(float4* sm, uint32_t N, int tb, const float* c) {
-#pragma unroll 2
-    for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
+    const uint32_t half = N >> 1;
+    for (uint32_t p = threadIdx.x; p < half; p += 2 * THREADS) {
+        const uint32_t q = p + THREADS;
+        const bool two = q < half;
         const uint32_t i0 = insert_zero32(p, tb), i1 = i0 | (1u << tb);
-        float4 a, b;
-        if (CLS != GC_DIAG1) a = sm[i0];
+        const uint32_t j0 = insert_zero32(two ? q : p, tb), j1 = j0 | (1u << tb);
+        float4 a, b, x, y;
+        if (CLS != GC_DIAG1) { a = sm[i0]; x = sm[j0]; }
         b = sm[i1];
+        y = sm[j1];
         df_pair_update<CLS>(c, a, b);
+        df_pair_update<CLS>(c, x, y);
         if (CLS != GC_DIAG1) sm[i0] = a;
         sm[i1] = b;
+        if (two) {
+            if (CLS != GC_DIAG1) sm[j0] = x;
+            sm[j1] = y;
+        }
     }
 }
 
 template <int CLS, int THREADS>
 __device__ __forceinline__ void df_tile_cu(float4* sm, uint32_t N, int cb, int tb, const float* c) {
     const int lo = min(cb, tb), hi = max(cb, tb);
-#pragma unroll 2
-    for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
+    const uint32_t quarter = N >> 2;
+    for (uint32_t p = threadIdx.x; p < quarter; p += 2 * THREADS) {
+        const uint32_t q = p + THREADS;
+        const bool two = q < quarter;
         const uint32_t i0 = insert_two_zeros32(p, lo, hi) | (1u << cb), i1 = i0 | (1u << tb);
-        float4 a, b;
-        if (CLS != GC_DIAG1) a = sm[i0];
+        const uint32_t j0 = insert_two_zeros32(two ? q : p, lo, hi) | (1u << cb), j1 = j0 | (1u << tb);
+        float4 a, b, x, y;
+        if (CLS != GC_DIAG1) { a = sm[i0]; x = sm[j0]; }
         b = sm[i1];
+        y = sm[j1];
         df_pair_update<CLS>(c, a, b);
+        df_pair_update<CLS>(c, x, y);
         if (CLS != GC_DIAG1) sm[i0] = a;
         sm[i1] = b;
+        if (two) {
+            if (CLS != GC_DIAG1) sm[j0] = x;
+            sm[j1] = y;
+        }
     }
 }
 
-// Multiply the tile (or the half with tile bit cb = 1) by matrix entry q11
-// (use22 = false) or q22 (use22 = true).
 template <bool USE22, int THREADS>
 __device__ __forceinline__ void df_tile_scale(float4* sm, uint32_t N, const float* c, int cb) {
     if (cb < 0) {

@@ -10,17 +10,29 @@
 
 namespace qs {
 
+// Two pairs per step (p and p + THREADS), both loaded before either is
+// updated, so the two updates are independent instruction chains.
 template <class R, int CLS, int THREADS>
 __device__ __forceinline__ void tile_1q(typename Amp<R>::T* sm, uint32_t N, int tb, const R* m) {
     using T = typename Amp<R>::T;
-    for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
+    const uint32_t half = N >> 1;
+    for (uint32_t p = threadIdx.x; p < half; p += 2 * THREADS) {
+        const uint32_t q = p + THREADS;
+        const bool two = q < half;
         const uint32_t i0 = insert_zero32(p, tb), i1 = i0 | (1u << tb);
-        T a, b;
-        if (CLS != GC_DIAG1) a = sm[i0];
+        const uint32_t j0 = insert_zero32(two ? q : p, tb), j1 = j0 | (1u << tb);
+        T a, b, x, y;
+        if (CLS != GC_DIAG1) { a = sm[i0]; x = sm[j0]; }
         b = sm[i1];
+        y = sm[j1];
         pair_update<CLS>(m, a, b);
+        pair_update<CLS>(m, x, y);
         if (CLS != GC_DIAG1) sm[i0] = a;
         sm[i1] = b;
+        if (two) {
+            if (CLS != GC_DIAG1) sm[j0] = x;
+            sm[j1] = y;
+        }
     }
 }
 
@@ -28,14 +40,24 @@ template <class R, int CLS, int THREADS>
 __device__ __forceinline__ void tile_cu(typename Amp<R>::T* sm, uint32_t N, int cb, int tb, const R* m) {
     using T = typename Amp<R>::T;
     const int lo = min(cb, tb), hi = max(cb, tb);
-    for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
+    const uint32_t quarter = N >> 2;
+    for (uint32_t p = threadIdx.x; p < quarter; p += 2 * THREADS) {
+        const uint32_t q = p + THREADS;
+        const bool two = q < quarter;
         const uint32_t i0 = insert_two_zeros32(p, lo, hi) | (1u << cb), i1 = i0 | (1u << tb);
-        T a, b;
-        if (CLS != GC_DIAG1) a = sm[i0];
+        const uint32_t j0 = insert_two_zeros32(two ? q : p, lo, hi) | (1u << cb), j1 = j0 | (1u << tb);
+        T a, b, x, y;
+        if (CLS != GC_DIAG1) { a = sm[i0]; x = sm[j0]; }
         b = sm[i1];
+        y = sm[j1];
         pair_update<CLS>(m, a, b);
+        pair_update<CLS>(m, x, y);
         if (CLS != GC_DIAG1) sm[i0] = a;
         sm[i1] = b;
+        if (two) {
+            if (CLS != GC_DIAG1) sm[j0] = x;
+            sm[j1] = y;
+        }
     }
 }
 
