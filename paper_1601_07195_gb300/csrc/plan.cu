@@ -62,6 +62,9 @@ struct qs_plan {
     std::vector<qs::PlanPass> passes;
     void* d_ops = nullptr;
     void* d_ops_f64 = nullptr;  // complex128 double-float plans: TileOp<double> copy for moves-only passes
+    std::vector<qs::TileOpDF> h_ops_df;  // host copy of double-float records (passed as kernel parameters)
+    std::vector<unsigned char> h_ops;     // host copy of native records (TileOp<float> or TileOp<double>)
+    std::vector<qs::TileOp<double>> h_ops_f64;  // host copy of the moves-only records of double-float plans
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     // optional per-pass timing: `records` sets of (passes + 1) events, used round robin
@@ -223,6 +226,14 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
         if (qs_status st = upload_ops(tops, &p->d_ops)) return st;
         if (qs_status st = upload_ops(t64, &p->d_ops_f64)) return st;
     }
+    if (df) {
+        p->h_ops_df.assign(reinterpret_cast<const TileOpDF*>(tops.data()),
+                           reinterpret_cast<const TileOpDF*>(tops.data()) + tops.size());
+        p->h_ops_f64 = t64;
+    } else {
+        const unsigned char* b = reinterpret_cast<const unsigned char*>(tops.data());
+        p->h_ops.assign(b, b + tops.size() * sizeof(OpT));
+    }
     return QS_OK;
 }
 
@@ -233,8 +244,22 @@ qs_status launch_all(qs_plan* p, cudaEvent_t* ev) {
         if (ev) QS_CUDA_TRY(cudaEventRecord(ev[i], p->s->stream));
         qs_status st;
         if (pp.kind == 0) st = launch_op(p->s, pp.op, f64);
-        else if (p->d_ops_f64 && pp.moves_only) st = launch_tile_pass(p->s, p->d_ops_f64, pp.tp, true);
-        else st = launch_tile_pass(p->s, p->d_ops, pp.tp, f64);
+        else if (!p->h_ops_df.empty()) {  // complex128 in double-float
+            if (pp.moves_only) {
+                st = pp.tp.nops <= tile_param_ops(true)
+                         ? launch_tile_pass_params(p->s, p->h_ops_f64.data(), pp.tp, true)
+                         : launch_tile_pass(p->s, p->d_ops_f64, pp.tp, true);
+            } else if (pp.tp.nops <= tile_df_param_ops()) {
+                cudaError_t e = launch_tile_df_params(p->s, p->h_ops_df.data(), pp.tp);
+                st = e == cudaSuccess ? QS_OK : cuda_fail(e, "tile kernel launch");
+            } else {
+                st = launch_tile_pass(p->s, p->d_ops, pp.tp, false);
+            }
+        } else {  // native FP32 (complex64) or FP64 (QS_PLAN_ARITH_F64) records
+            const bool dbl = p->s->dt == QS_C128;
+            st = pp.tp.nops <= tile_param_ops(dbl) ? launch_tile_pass_params(p->s, p->h_ops.data(), pp.tp, dbl)
+                                                    : launch_tile_pass(p->s, p->d_ops, pp.tp, f64);
+        }
         if (st != QS_OK) return st;
     }
     if (ev) QS_CUDA_TRY(cudaEventRecord(ev[p->passes.size()], p->s->stream));

@@ -134,6 +134,15 @@ qs_status launch_op(qs_state* s, const Op& op, bool arith_f64);
 // count > 1 runs `count` instances side by side (grid.y), strides in `pass`.
 qs_status launch_tile_pass(qs_state* s, const void* d_ops, const TilePass& pass, bool arith_f64, unsigned count = 1);
 cudaError_t launch_tile_df(qs_state* s, const void* d_ops, const TilePass& pass, unsigned count);
+// Double-float pass whose op records (host copies, pass.op0 indexes h_ops) travel
+// in the kernel's parameter block; at most tile_df_param_ops() ops.
+cudaError_t launch_tile_df_params(qs_state* s, const TileOpDF* h_ops, const TilePass& pass);
+int tile_df_param_ops();
+// Native-arithmetic pass (TileOp<float> for complex64, TileOp<double> with f64)
+// whose op records travel in the kernel's parameter block; at most
+// tile_param_ops(f64) ops.
+qs_status launch_tile_pass_params(qs_state* s, const void* h_ops, const TilePass& pass, bool f64);
+int tile_param_ops(bool f64);
 void split_to_floats(double x, float& hi, float& lo);
 size_t tile_smem_bytes(qs_dtype dt, int b);
 

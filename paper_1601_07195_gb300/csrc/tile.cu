@@ -10,6 +10,8 @@
 // controlled phase) on qubits outside the tile are a per-tile constant factor,
 // and controls outside the tile are a per-tile predicate.  One pass therefore
 // reads and writes the state once for the whole run of gates.
+#include <cstring>
+
 #include "device.cuh"
 #include "tile_ops.cuh"
 
@@ -17,16 +19,13 @@ namespace qs {
 
 namespace {
 
-constexpr int kTileThreads = 512;
+constexpr int kTileThreads = 256;
 
-template <class R>
-__global__ void __launch_bounds__(kTileThreads) k_tile(typename Amp<R>::T* __restrict__ psi,
-                                                       const TileOp<R>* __restrict__ ops, TilePass P) {
+template <class R, class OpAt>
+__device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, const TilePass& P, OpAt op_at) {
     using T = typename Amp<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
-    psi += (uint64_t)blockIdx.y * P.inst_stride;
-    ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride;
     const int b = P.b, b0 = P.b0, nh = b - b0;
     const uint32_t N = 1u << b;
     uint64_t* hioff = reinterpret_cast<uint64_t*>(sm + N);
@@ -42,10 +41,31 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(typename Amp<R>::T* __res
     for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) sm[e] = psi[base + hioff[e >> b0] + (e & lomask)];
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
-        const TileOp<R> op = ops[P.op0 + g];
-        if (tile_apply<R, kTileThreads>(sm, N, op, base)) __syncthreads();
+        if (tile_apply<R, kTileThreads>(sm, N, op_at(g), base)) __syncthreads();
     }
     for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) psi[base + hioff[e >> b0] + (e & lomask)] = sm[e];
+}
+
+// ops in device memory (batched launches: one op array per instance)
+template <class R>
+__global__ void __launch_bounds__(kTileThreads) k_tile(typename Amp<R>::T* __restrict__ psi,
+                                                       const TileOp<R>* __restrict__ ops, TilePass P) {
+    psi += (uint64_t)blockIdx.y * P.inst_stride;
+    ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride + P.op0;
+    tile_body<R>(psi, P, [&](int g) { return ops[g]; });
+}
+
+// ops in the kernel's parameter block (constant cache, no global load per op)
+template <class R> struct TileParams {
+    static constexpr int kOps = (31000 - (int)sizeof(TilePass)) / (int)sizeof(TileOp<R>);
+    TilePass P;
+    TileOp<R> ops[kOps];
+};
+
+template <class R>
+__global__ void __launch_bounds__(kTileThreads) k_tile_p(typename Amp<R>::T* __restrict__ psi,
+                                                         const __grid_constant__ TileParams<R> L) {
+    tile_body<R>(psi, L.P, [&](int g) -> const TileOp<R>& { return L.ops[g]; });
 }
 
 template <class R>
@@ -64,9 +84,39 @@ cudaError_t launch_tile(qs_state* s, const void* d_ops, const TilePass& P, unsig
     return cudaGetLastError();
 }
 
+template <class R>
+cudaError_t launch_tile_p(qs_state* s, const void* h_ops, const TilePass& P) {
+    if (P.nops > TileParams<R>::kOps) return cudaErrorInvalidValue;
+    const size_t smem = tile_smem_bytes(s->dt, P.b) + ((size_t)8 << (P.b - P.b0));
+    static bool configured[2] = {false, false};
+    const int which = sizeof(R) == 8 ? 1 : 0;
+    if (!configured[which]) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
+        if (e != cudaSuccess) return e;
+        configured[which] = true;
+    }
+    static thread_local TileParams<R> L;
+    L.P = P;
+    L.P.op0 = 0;
+    std::memcpy(L.ops, reinterpret_cast<const TileOp<R>*>(h_ops) + P.op0, sizeof(TileOp<R>) * (size_t)P.nops);
+    const dim3 grid((unsigned)(1ull << (s->n - P.b)), 1);
+    k_tile_p<R><<<grid, kTileThreads, smem, s->stream>>>(reinterpret_cast<typename Amp<R>::T*>(s->data), L);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t tile_smem_bytes(qs_dtype dt, int b) { return amp_bytes(dt) << b; }
+
+int tile_param_ops(bool f64) { return f64 ? TileParams<double>::kOps : TileParams<float>::kOps; }
+
+qs_status launch_tile_pass_params(qs_state* s, const void* h_ops, const TilePass& pass, bool f64) {
+    if (tile_smem_bytes(s->dt, pass.b) + ((size_t)8 << (pass.b - pass.b0)) > smem_optin())
+        return fail(QS_EINVAL, "tile does not fit in shared memory");
+    cudaError_t e = f64 ? launch_tile_p<double>(s, h_ops, pass) : launch_tile_p<float>(s, h_ops, pass);
+    if (e != cudaSuccess) return cuda_fail(e, "tile kernel launch");
+    return QS_OK;
+}
 
 qs_status launch_tile_pass(qs_state* s, const void* d_ops, const TilePass& pass, bool arith_f64, unsigned count) {
     if (tile_smem_bytes(s->dt, pass.b) + ((size_t)8 << (pass.b - pass.b0)) > smem_optin())

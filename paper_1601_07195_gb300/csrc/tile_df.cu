@@ -6,6 +6,8 @@
 // rounded back to doubles once when the tile is stored.  Layout, planner
 // contract and control/diagonal handling are those of tile.cu (Section 4.4,
 // Fig. 5, on a shared-memory tile over any qubit set).
+#include <cstring>
+
 #include "device.cuh"
 #include "df.cuh"
 #include "tile_df_ops.cuh"
@@ -18,12 +20,11 @@ namespace {
 #endif
 constexpr int kThreads = QS_TILE_DF_THREADS;
 
-__global__ void __launch_bounds__(kThreads) k_tile_df(double2* __restrict__ psi, const TileOpDF* __restrict__ ops,
-                                                      TilePass P) {
+// The pass body; OpAt(g) yields op g of the pass.
+template <class OpAt>
+__device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const TilePass& P, OpAt op_at) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* sm = reinterpret_cast<float4*>(smem_raw);
-    psi += (uint64_t)blockIdx.y * P.inst_stride;
-    ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride;
     const int b = P.b, b0 = P.b0, nh = b - b0;
     const uint32_t N = 1u << b;
     uint64_t* hioff = reinterpret_cast<uint64_t*>(sm + N);
@@ -39,10 +40,31 @@ __global__ void __launch_bounds__(kThreads) k_tile_df(double2* __restrict__ psi,
     for (uint32_t e = threadIdx.x; e < N; e += kThreads) sm[e] = df_load(psi[base + hioff[e >> b0] + (e & lomask)]);
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
-        const TileOpDF op = ops[P.op0 + g];
-        if (df_tile_apply<kThreads>(sm, N, op, base)) __syncthreads();
+        if (df_tile_apply<kThreads>(sm, N, op_at(g), base)) __syncthreads();
     }
     for (uint32_t e = threadIdx.x; e < N; e += kThreads) psi[base + hioff[e >> b0] + (e & lomask)] = df_store(sm[e]);
+}
+
+// ops in device memory (batched launches: one op array per instance)
+__global__ void __launch_bounds__(kThreads) k_tile_df(double2* __restrict__ psi, const TileOpDF* __restrict__ ops,
+                                                      TilePass P) {
+    psi += (uint64_t)blockIdx.y * P.inst_stride;
+    ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride + P.op0;
+    tile_df_body(psi, P, [&](int g) { return ops[g]; });
+}
+
+// ops in the kernel's parameter block: read through the constant cache,
+// uniform across the CTA, with no global-memory load per op
+constexpr int kParamOps = 296;
+struct TileParamsDF {
+    TilePass P;
+    TileOpDF ops[kParamOps];
+};
+static_assert(sizeof(TileParamsDF) <= 32000, "kernel parameter block too large");
+
+__global__ void __launch_bounds__(kThreads) k_tile_df_p(double2* __restrict__ psi,
+                                                        const __grid_constant__ TileParamsDF L) {
+    tile_df_body(psi, L.P, [&](int g) -> const TileOpDF& { return L.ops[g]; });
 }
 
 }  // namespace
@@ -51,6 +73,26 @@ void split_to_floats(double x, float& hi, float& lo) {
     hi = (float)x;
     lo = (float)(x - (double)hi);
 }
+
+cudaError_t launch_tile_df_params(qs_state* s, const TileOpDF* h_ops, const TilePass& P) {
+    if (P.nops > kParamOps) return cudaErrorInvalidValue;
+    const size_t smem = tile_smem_bytes(s->dt, P.b) + ((size_t)8 << (P.b - P.b0));
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_df_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    static thread_local TileParamsDF L;
+    L.P = P;
+    L.P.op0 = 0;
+    std::memcpy(L.ops, h_ops + P.op0, sizeof(TileOpDF) * (size_t)P.nops);
+    const dim3 grid((unsigned)(1ull << (s->n - P.b)), 1);
+    k_tile_df_p<<<grid, kThreads, smem, s->stream>>>(reinterpret_cast<double2*>(s->data), L);
+    return cudaGetLastError();
+}
+
+int tile_df_param_ops() { return kParamOps; }
 
 cudaError_t launch_tile_df(qs_state* s, const void* d_ops, const TilePass& P, unsigned count) {
     const size_t smem = tile_smem_bytes(s->dt, P.b) + ((size_t)8 << (P.b - P.b0));

@@ -35,13 +35,13 @@ __device__ __forceinline__ void df_pair_update(const float* c, float4& a, float4
 
 // Each thread takes two pairs per step (p and p + THREADS), loads both before
 // computing: the two double-float updates are independent chains the
-// scheduler can interleave.
-template <int CLS, int THREADS>
-__device__ __forceinline__ void df_tile_1q(float4* sm, uint32_t N, int tb, const float* c) {
-    const uint32_t half = N >> 1;
+// scheduler can interleave.  GUARD is needed only when the pair count is not
+// a multiple of 2 * THREADS (tiles smaller than 4 * THREADS amplitudes).
+template <int CLS, int THREADS, bool GUARD>
+__device__ __forceinline__ void df_tile_1q_body(float4* sm, uint32_t half, int tb, const float* c) {
     for (uint32_t p = threadIdx.x; p < half; p += 2 * THREADS) {
         const uint32_t q = p + THREADS;
-        const bool two = q < half;
+        const bool two = !GUARD || q < half;
         const uint32_t i0 = insert_zero32(p, tb), i1 = i0 | (1u << tb);
         const uint32_t j0 = insert_zero32(two ? q : p, tb), j1 = j0 | (1u << tb);
         float4 a, b, x, y;
@@ -60,12 +60,18 @@ __device__ __forceinline__ void df_tile_1q(float4* sm, uint32_t N, int tb, const
 }
 
 template <int CLS, int THREADS>
-__device__ __forceinline__ void df_tile_cu(float4* sm, uint32_t N, int cb, int tb, const float* c) {
+__device__ __forceinline__ void df_tile_1q(float4* sm, uint32_t N, int tb, const float* c) {
+    const uint32_t half = N >> 1;
+    if ((half & (2 * THREADS - 1)) == 0) df_tile_1q_body<CLS, THREADS, false>(sm, half, tb, c);
+    else df_tile_1q_body<CLS, THREADS, true>(sm, half, tb, c);
+}
+
+template <int CLS, int THREADS, bool GUARD>
+__device__ __forceinline__ void df_tile_cu_body(float4* sm, uint32_t quarter, int cb, int tb, const float* c) {
     const int lo = min(cb, tb), hi = max(cb, tb);
-    const uint32_t quarter = N >> 2;
     for (uint32_t p = threadIdx.x; p < quarter; p += 2 * THREADS) {
         const uint32_t q = p + THREADS;
-        const bool two = q < quarter;
+        const bool two = !GUARD || q < quarter;
         const uint32_t i0 = insert_two_zeros32(p, lo, hi) | (1u << cb), i1 = i0 | (1u << tb);
         const uint32_t j0 = insert_two_zeros32(two ? q : p, lo, hi) | (1u << cb), j1 = j0 | (1u << tb);
         float4 a, b, x, y;
@@ -81,6 +87,13 @@ __device__ __forceinline__ void df_tile_cu(float4* sm, uint32_t N, int cb, int t
             sm[j1] = y;
         }
     }
+}
+
+template <int CLS, int THREADS>
+__device__ __forceinline__ void df_tile_cu(float4* sm, uint32_t N, int cb, int tb, const float* c) {
+    const uint32_t quarter = N >> 2;
+    if ((quarter & (2 * THREADS - 1)) == 0) df_tile_cu_body<CLS, THREADS, false>(sm, quarter, cb, tb, c);
+    else df_tile_cu_body<CLS, THREADS, true>(sm, quarter, cb, tb, c);
 }
 
 template <bool USE22, int THREADS>
