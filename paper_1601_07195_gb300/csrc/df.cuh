@@ -67,39 +67,42 @@ __device__ __forceinline__ dfl df_dot4(dfl a, dfl b, dfl c, dfl d) {
 
 // Exact split of a double into hi = its leading 24 significant bits and lo =
 // the next 24 bits (truncated; the dropped tail is below 2^-47 of |x|), built
-// from the IEEE bit fields with integer instructions only.  |x| < 2^-126 is
-// flushed to zero (an absolute change below 1.2e-38); |x| >= 2^128 saturates
-// to an infinity (not reachable from a normalised state).
+// from the IEEE bit fields with integer instructions only, branch-free.
+// |x| < 2^-126 is flushed to zero (an absolute change below 1.2e-38); a lo
+// part below 2^-126 is flushed likewise; |x| >= 2^128 saturates to an
+// infinity (not reachable from a normalised state).
 __device__ __forceinline__ dfl split_double(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
     const unsigned sign = hw & 0x80000000u;
     const int e = (int)((hw >> 20) & 0x7FFu);
     const int e32 = e - 1023 + 127;
-    if (e32 <= 0) return {__int_as_float((int)sign), __int_as_float((int)sign)};
-    if (e32 >= 255) return {__int_as_float((int)(sign | 0x7F800000u)), 0.0f};
     const unsigned top23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
-    const float hi = __int_as_float((int)(sign | ((unsigned)e32 << 23) | top23));
+    unsigned hi = sign | ((unsigned)e32 << 23) | top23;
+    hi = e32 <= 0 ? sign : hi;
+    hi = e32 >= 255 ? (sign | 0x7F800000u) : hi;
     const unsigned rem = lw & 0x1FFFFFFFu;  // 29 bits, weight 2^(e-1023-52)
-    if (rem == 0u) return {hi, __int_as_float((int)sign)};
-    const int p = 31 - __clz((int)rem);      // 0..28
+    const int p = 31 - __clz((int)rem);      // -1 when rem == 0
     const int elo = e - 1023 - 52 + p + 127;
-    if (elo <= 0) return {hi, __int_as_float((int)sign)};
-    const unsigned m = (p >= 23 ? (rem >> (p - 23)) : (rem << (23 - p))) & 0x7FFFFFu;
-    return {hi, __int_as_float((int)(sign | ((unsigned)elo << 23) | m))};
+    const unsigned up = rem << ((23 - p) & 31), down = rem >> ((p - 23) & 31);
+    const unsigned m = (p >= 23 ? down : up) & 0x7FFFFFu;
+    unsigned lo = sign | ((unsigned)elo << 23) | m;
+    lo = (rem == 0u || elo <= 0 || e32 <= 0 || e32 >= 255) ? sign : lo;
+    return {__int_as_float((int)hi), __int_as_float((int)lo)};
 }
 
-// float -> double by the bit fields (exact; no FP64 instruction).  Zero and
-// normal floats only (DF parts are never subnormal: see split_double).
+// float -> double by the bit fields (exact; no FP64 instruction), branch-free.
+// Zero and normal floats (a subnormal maps to a signed zero: below 1.2e-38).
 __device__ __forceinline__ double float_to_double_bits(float f) {
     const unsigned u = (unsigned)__float_as_int(f);
-    const unsigned sign = u & 0x80000000u;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
     const unsigned ef = (u >> 23) & 0xFFu;
-    if (ef == 0u) return __longlong_as_double((long long)((unsigned long long)sign << 32));
-    if (ef == 0xFFu) return __longlong_as_double((long long)(((unsigned long long)(sign | 0x7FF00000u)) << 32));
-    const unsigned long long ed = (unsigned long long)(ef - 127 + 1023);
+    const unsigned long long ed = (unsigned long long)(ef + (1023 - 127)) << 52;
     const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
-    return __longlong_as_double((long long)(((unsigned long long)sign << 32) | (ed << 52) | m));
+    unsigned long long r = sign | ed | m;
+    r = ef == 0u ? sign : r;
+    r = ef == 0xFFu ? (sign | 0x7FF0000000000000ull) : r;
+    return __longlong_as_double((long long)r);
 }
 
 // hi + lo rounded to the nearest double (one FP64 addition).

@@ -20,8 +20,9 @@ namespace {
 #endif
 constexpr int kThreads = QS_TILE_DF_THREADS;
 
-// The pass body; OpAt(g) yields op g of the pass.
-template <class OpAt>
+// The pass body; OpAt(g) yields op g of the pass.  B > 0: the tile has
+// exactly 2^B amplitudes and the fixed-size gate paths are used.
+template <int B = 0, class OpAt>
 __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const TilePass& P, OpAt op_at) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* sm = reinterpret_cast<float4*>(smem_raw);
@@ -40,7 +41,7 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
     for (uint32_t e = threadIdx.x; e < N; e += kThreads) sm[e] = df_load(psi[base + hioff[e >> b0] + (e & lomask)]);
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
-        if (df_tile_apply<kThreads>(sm, N, op_at(g), base)) __syncthreads();
+        if (df_tile_apply<kThreads, B>(sm, N, op_at(g), base)) __syncthreads();
     }
     for (uint32_t e = threadIdx.x; e < N; e += kThreads) psi[base + hioff[e >> b0] + (e & lomask)] = df_store(sm[e]);
 }
@@ -62,9 +63,23 @@ struct TileParamsDF {
 };
 static_assert(sizeof(TileParamsDF) <= 32000, "kernel parameter block too large");
 
+template <int B>
 __global__ void __launch_bounds__(kThreads) k_tile_df_p(double2* __restrict__ psi,
                                                         const __grid_constant__ TileParamsDF L) {
-    tile_df_body(psi, L.P, [&](int g) -> const TileOpDF& { return L.ops[g]; });
+    tile_df_body<B>(psi, L.P, [&](int g) -> const TileOpDF& { return L.ops[g]; });
+}
+
+template <int B>
+cudaError_t launch_df_p(qs_state* s, const TileParamsDF& L, size_t smem) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_df_p<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const dim3 grid((unsigned)(1ull << (s->n - L.P.b)), 1);
+    k_tile_df_p<B><<<grid, kThreads, smem, s->stream>>>(reinterpret_cast<double2*>(s->data), L);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -77,19 +92,18 @@ void split_to_floats(double x, float& hi, float& lo) {
 cudaError_t launch_tile_df_params(qs_state* s, const TileOpDF* h_ops, const TilePass& P) {
     if (P.nops > kParamOps) return cudaErrorInvalidValue;
     const size_t smem = tile_smem_bytes(s->dt, P.b) + ((size_t)8 << (P.b - P.b0));
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_df_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
     static thread_local TileParamsDF L;
     L.P = P;
     L.P.op0 = 0;
     std::memcpy(L.ops, h_ops + P.op0, sizeof(TileOpDF) * (size_t)P.nops);
-    const dim3 grid((unsigned)(1ull << (s->n - P.b)), 1);
-    k_tile_df_p<<<grid, kThreads, smem, s->stream>>>(reinterpret_cast<double2*>(s->data), L);
-    return cudaGetLastError();
+    // fixed-size instantiations for the tile sizes the planner and autotuner use
+    switch (P.b) {
+    case 10: return launch_df_p<10>(s, L, smem);
+    case 11: return launch_df_p<11>(s, L, smem);
+    case 12: return launch_df_p<12>(s, L, smem);
+    case 13: return launch_df_p<13>(s, L, smem);
+    default: return launch_df_p<0>(s, L, smem);
+    }
 }
 
 int tile_df_param_ops() { return kParamOps; }

@@ -59,6 +59,57 @@ __device__ __forceinline__ void df_tile_1q_body(float4* sm, uint32_t half, int t
     }
 }
 
+// Tiles of exactly 2^B amplitudes with 2^(B-1) >= 2 * THREADS: thread t's
+// pairs are p = t + m * THREADS, and since t < THREADS and m * THREADS share no
+// bit, insert_zero(p) = insert_zero(t) + insert_zero(m * THREADS).  One
+// per-thread base index per op plus per-step offsets that are uniform over the
+// CTA (compile-time m, per-op tb) leave almost no integer work per pair, and
+// the fully unrolled steps expose independent pairs to the scheduler.
+template <int CLS, int THREADS, int B>
+__device__ __forceinline__ void df_tile_1q_fixed(float4* sm, int tb, const float* c) {
+    constexpr int PAIRS = (1 << (B - 1)) / THREADS;
+    static_assert(PAIRS >= 2 && PAIRS % 2 == 0, "tile too small for the fixed path");
+    float4* s0 = sm + insert_zero32(threadIdx.x, tb);
+    float4* s1 = s0 + (1u << tb);
+#pragma unroll
+    for (int m = 0; m < PAIRS; m += 2) {
+        const uint32_t d0 = insert_zero32((uint32_t)(m * THREADS), tb);
+        const uint32_t d1 = insert_zero32((uint32_t)((m + 1) * THREADS), tb);
+        float4 a, b, x, y;
+        if (CLS != GC_DIAG1) { a = s0[d0]; x = s0[d1]; }
+        b = s1[d0];
+        y = s1[d1];
+        df_pair_update<CLS>(c, a, b);
+        df_pair_update<CLS>(c, x, y);
+        if (CLS != GC_DIAG1) { s0[d0] = a; s0[d1] = x; }
+        s1[d0] = b;
+        s1[d1] = y;
+    }
+}
+
+template <int CLS, int THREADS, int B>
+__device__ __forceinline__ void df_tile_cu_fixed(float4* sm, int cb, int tb, const float* c) {
+    constexpr int ITEMS = (1 << (B - 2)) / THREADS;
+    static_assert(ITEMS >= 2 && ITEMS % 2 == 0, "tile too small for the fixed path");
+    const int lo = min(cb, tb), hi = max(cb, tb);
+    float4* s0 = sm + (insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb));
+    float4* s1 = s0 + (1u << tb);
+#pragma unroll
+    for (int m = 0; m < ITEMS; m += 2) {
+        const uint32_t d0 = insert_two_zeros32((uint32_t)(m * THREADS), lo, hi);
+        const uint32_t d1 = insert_two_zeros32((uint32_t)((m + 1) * THREADS), lo, hi);
+        float4 a, b, x, y;
+        if (CLS != GC_DIAG1) { a = s0[d0]; x = s0[d1]; }
+        b = s1[d0];
+        y = s1[d1];
+        df_pair_update<CLS>(c, a, b);
+        df_pair_update<CLS>(c, x, y);
+        if (CLS != GC_DIAG1) { s0[d0] = a; s0[d1] = x; }
+        s1[d0] = b;
+        s1[d1] = y;
+    }
+}
+
 template <int CLS, int THREADS>
 __device__ __forceinline__ void df_tile_1q(float4* sm, uint32_t N, int tb, const float* c) {
     const uint32_t half = N >> 1;
@@ -121,30 +172,42 @@ __device__ __forceinline__ void df_tile_swap(float4* sm, uint32_t N, int ab, int
     }
 }
 
-template <int THREADS>
+template <int CLS, int THREADS, int B>
+__device__ __forceinline__ void df_tile_1q_any(float4* sm, uint32_t N, int tb, const float* c) {
+    if constexpr (B > 0 && (1 << (B - 1)) / THREADS >= 2) df_tile_1q_fixed<CLS, THREADS, B>(sm, tb, c);
+    else df_tile_1q<CLS, THREADS>(sm, N, tb, c);
+}
+template <int CLS, int THREADS, int B>
+__device__ __forceinline__ void df_tile_cu_any(float4* sm, uint32_t N, int cb, int tb, const float* c) {
+    if constexpr (B > 0 && (1 << (B - 2)) / THREADS >= 2) df_tile_cu_fixed<CLS, THREADS, B>(sm, cb, tb, c);
+    else df_tile_cu<CLS, THREADS>(sm, N, cb, tb, c);
+}
+
+// B > 0: the tile has exactly 2^B amplitudes (fixed-size paths); B = 0: any size.
+template <int THREADS, int B = 0>
 __device__ __forceinline__ void df_tile_pairs(float4* sm, uint32_t N, int cls, int cb, int tb, const float* c) {
     if (cb < 0) {
         switch (cls) {
-        case GC_GENERAL: df_tile_1q<GC_GENERAL, THREADS>(sm, N, tb, c); break;
-        case GC_REAL: df_tile_1q<GC_REAL, THREADS>(sm, N, tb, c); break;
-        case GC_DIAG: df_tile_1q<GC_DIAG, THREADS>(sm, N, tb, c); break;
-        case GC_DIAG1: df_tile_1q<GC_DIAG1, THREADS>(sm, N, tb, c); break;
-        case GC_ANTIDIAG: df_tile_1q<GC_ANTIDIAG, THREADS>(sm, N, tb, c); break;
-        default: df_tile_1q<GC_PERM, THREADS>(sm, N, tb, c); break;
+        case GC_GENERAL: df_tile_1q_any<GC_GENERAL, THREADS, B>(sm, N, tb, c); break;
+        case GC_REAL: df_tile_1q_any<GC_REAL, THREADS, B>(sm, N, tb, c); break;
+        case GC_DIAG: df_tile_1q_any<GC_DIAG, THREADS, B>(sm, N, tb, c); break;
+        case GC_DIAG1: df_tile_1q_any<GC_DIAG1, THREADS, B>(sm, N, tb, c); break;
+        case GC_ANTIDIAG: df_tile_1q_any<GC_ANTIDIAG, THREADS, B>(sm, N, tb, c); break;
+        default: df_tile_1q_any<GC_PERM, THREADS, B>(sm, N, tb, c); break;
         }
     } else {
         switch (cls) {
-        case GC_GENERAL: df_tile_cu<GC_GENERAL, THREADS>(sm, N, cb, tb, c); break;
-        case GC_REAL: df_tile_cu<GC_REAL, THREADS>(sm, N, cb, tb, c); break;
-        case GC_DIAG: df_tile_cu<GC_DIAG, THREADS>(sm, N, cb, tb, c); break;
-        case GC_DIAG1: df_tile_cu<GC_DIAG1, THREADS>(sm, N, cb, tb, c); break;
-        case GC_ANTIDIAG: df_tile_cu<GC_ANTIDIAG, THREADS>(sm, N, cb, tb, c); break;
-        default: df_tile_cu<GC_PERM, THREADS>(sm, N, cb, tb, c); break;
+        case GC_GENERAL: df_tile_cu_any<GC_GENERAL, THREADS, B>(sm, N, cb, tb, c); break;
+        case GC_REAL: df_tile_cu_any<GC_REAL, THREADS, B>(sm, N, cb, tb, c); break;
+        case GC_DIAG: df_tile_cu_any<GC_DIAG, THREADS, B>(sm, N, cb, tb, c); break;
+        case GC_DIAG1: df_tile_cu_any<GC_DIAG1, THREADS, B>(sm, N, cb, tb, c); break;
+        case GC_ANTIDIAG: df_tile_cu_any<GC_ANTIDIAG, THREADS, B>(sm, N, cb, tb, c); break;
+        default: df_tile_cu_any<GC_PERM, THREADS, B>(sm, N, cb, tb, c); break;
         }
     }
 }
 
-template <int THREADS>
+template <int THREADS, int B = 0>
 __device__ __forceinline__ bool df_tile_apply(float4* sm, uint32_t N, const TileOpDF& op, uint64_t base) {
     if (op.kind == OP_SWAP) {
         df_tile_swap<THREADS>(sm, N, op.tb, op.cb);
@@ -165,7 +228,7 @@ __device__ __forceinline__ bool df_tile_apply(float4* sm, uint32_t N, const Tile
         else df_tile_scale<false, THREADS>(sm, N, op.c, cb);
         return true;
     }
-    df_tile_pairs<THREADS>(sm, N, op.cls, cb, op.tb, op.c);
+    df_tile_pairs<THREADS, B>(sm, N, op.cls, cb, op.tb, op.c);
     return true;
 }
 

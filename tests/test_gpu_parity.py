@@ -155,7 +155,7 @@ def test_random_circuit_n20(qs, dt, mode):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
-@pytest.mark.parametrize("tile_bits", [2, 3, 5, 8, 11, 12])
+@pytest.mark.parametrize("tile_bits", [2, 3, 5, 8, 10, 11, 12, 13])
 def test_tile_sizes(qs, dt, tile_bits):
     if dt == 1 and tile_bits > 13:
         pytest.skip("does not fit")
