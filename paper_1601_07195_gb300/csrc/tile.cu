@@ -21,7 +21,7 @@ namespace {
 
 constexpr int kTileThreads = 256;
 
-template <class R, class OpAt>
+template <class R, int B = 0, class OpAt>
 __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, const TilePass& P, OpAt op_at) {
     using T = typename Amp<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -41,7 +41,7 @@ __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, 
     for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) sm[e] = psi[base + hioff[e >> b0] + (e & lomask)];
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
-        if (tile_apply<R, kTileThreads>(sm, N, op_at(g), base)) __syncthreads();
+        if (tile_apply<R, kTileThreads, B>(sm, N, op_at(g), base)) __syncthreads();
     }
     for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) psi[base + hioff[e >> b0] + (e & lomask)] = sm[e];
 }
@@ -62,10 +62,23 @@ template <class R> struct TileParams {
     TileOp<R> ops[kOps];
 };
 
-template <class R>
+template <class R, int B>
 __global__ void __launch_bounds__(kTileThreads) k_tile_p(typename Amp<R>::T* __restrict__ psi,
                                                          const __grid_constant__ TileParams<R> L) {
-    tile_body<R>(psi, L.P, [&](int g) -> const TileOp<R>& { return L.ops[g]; });
+    tile_body<R, B>(psi, L.P, [&](int g) -> const TileOp<R>& { return L.ops[g]; });
+}
+
+template <class R, int B>
+cudaError_t launch_p(qs_state* s, const TileParams<R>& L, size_t smem) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_p<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const dim3 grid((unsigned)(1ull << (s->n - L.P.b)), 1);
+    k_tile_p<R, B><<<grid, kTileThreads, smem, s->stream>>>(reinterpret_cast<typename Amp<R>::T*>(s->data), L);
+    return cudaGetLastError();
 }
 
 template <class R>
@@ -88,20 +101,17 @@ template <class R>
 cudaError_t launch_tile_p(qs_state* s, const void* h_ops, const TilePass& P) {
     if (P.nops > TileParams<R>::kOps) return cudaErrorInvalidValue;
     const size_t smem = tile_smem_bytes(s->dt, P.b) + ((size_t)8 << (P.b - P.b0));
-    static bool configured[2] = {false, false};
-    const int which = sizeof(R) == 8 ? 1 : 0;
-    if (!configured[which]) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
-        if (e != cudaSuccess) return e;
-        configured[which] = true;
-    }
     static thread_local TileParams<R> L;
     L.P = P;
     L.P.op0 = 0;
     std::memcpy(L.ops, reinterpret_cast<const TileOp<R>*>(h_ops) + P.op0, sizeof(TileOp<R>) * (size_t)P.nops);
-    const dim3 grid((unsigned)(1ull << (s->n - P.b)), 1);
-    k_tile_p<R><<<grid, kTileThreads, smem, s->stream>>>(reinterpret_cast<typename Amp<R>::T*>(s->data), L);
-    return cudaGetLastError();
+    switch (P.b) {
+    case 11: return launch_p<R, 11>(s, L, smem);
+    case 12: return launch_p<R, 12>(s, L, smem);
+    case 13: return launch_p<R, 13>(s, L, smem);
+    case 14: return launch_p<R, 14>(s, L, smem);
+    default: return launch_p<R, 0>(s, L, smem);
+    }
 }
 
 }  // namespace

@@ -61,6 +61,65 @@ __device__ __forceinline__ void tile_cu(typename Amp<R>::T* sm, uint32_t N, int 
     }
 }
 
+// Fixed-size tiles (2^B amplitudes): one per-thread base index per op plus
+// offsets uniform over the CTA (insert_zero is additive over the disjoint bits
+// of t < THREADS and m * THREADS), fully unrolled.
+template <class R, int CLS, int THREADS, int B>
+__device__ __forceinline__ void tile_1q_fixed(typename Amp<R>::T* sm, int tb, const R* m) {
+    using T = typename Amp<R>::T;
+    constexpr int PAIRS = (1 << (B - 1)) / THREADS;
+    T* s0 = sm + insert_zero32(threadIdx.x, tb);
+    T* s1 = s0 + (1u << tb);
+#pragma unroll
+    for (int k = 0; k < PAIRS; k += 2) {
+        const uint32_t d0 = insert_zero32((uint32_t)(k * THREADS), tb);
+        const uint32_t d1 = insert_zero32((uint32_t)((k + 1) * THREADS), tb);
+        T a, b, x, y;
+        if (CLS != GC_DIAG1) { a = s0[d0]; x = s0[d1]; }
+        b = s1[d0];
+        y = s1[d1];
+        pair_update<CLS>(m, a, b);
+        pair_update<CLS>(m, x, y);
+        if (CLS != GC_DIAG1) { s0[d0] = a; s0[d1] = x; }
+        s1[d0] = b;
+        s1[d1] = y;
+    }
+}
+
+template <class R, int CLS, int THREADS, int B>
+__device__ __forceinline__ void tile_cu_fixed(typename Amp<R>::T* sm, int cb, int tb, const R* m) {
+    using T = typename Amp<R>::T;
+    constexpr int ITEMS = (1 << (B - 2)) / THREADS;
+    const int lo = min(cb, tb), hi = max(cb, tb);
+    T* s0 = sm + (insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb));
+    T* s1 = s0 + (1u << tb);
+#pragma unroll
+    for (int k = 0; k < ITEMS; k += 2) {
+        const uint32_t d0 = insert_two_zeros32((uint32_t)(k * THREADS), lo, hi);
+        const uint32_t d1 = insert_two_zeros32((uint32_t)((k + 1) * THREADS), lo, hi);
+        T a, b, x, y;
+        if (CLS != GC_DIAG1) { a = s0[d0]; x = s0[d1]; }
+        b = s1[d0];
+        y = s1[d1];
+        pair_update<CLS>(m, a, b);
+        pair_update<CLS>(m, x, y);
+        if (CLS != GC_DIAG1) { s0[d0] = a; s0[d1] = x; }
+        s1[d0] = b;
+        s1[d1] = y;
+    }
+}
+
+template <class R, int CLS, int THREADS, int B>
+__device__ __forceinline__ void tile_1q_any(typename Amp<R>::T* sm, uint32_t N, int tb, const R* m) {
+    if constexpr (B > 0 && (1 << (B - 1)) / THREADS >= 2) tile_1q_fixed<R, CLS, THREADS, B>(sm, tb, m);
+    else tile_1q<R, CLS, THREADS>(sm, N, tb, m);
+}
+template <class R, int CLS, int THREADS, int B>
+__device__ __forceinline__ void tile_cu_any(typename Amp<R>::T* sm, uint32_t N, int cb, int tb, const R* m) {
+    if constexpr (B > 0 && (1 << (B - 2)) / THREADS >= 2) tile_cu_fixed<R, CLS, THREADS, B>(sm, cb, tb, m);
+    else tile_cu<R, CLS, THREADS>(sm, N, cb, tb, m);
+}
+
 // Multiply the tile (or, with cb >= 0, the half whose tile bit cb is 1) by f.
 template <class R, int THREADS>
 __device__ __forceinline__ void tile_scale(typename Amp<R>::T* sm, uint32_t N, R fr, R fi, int cb) {
@@ -86,25 +145,26 @@ __device__ __forceinline__ void tile_swap(typename Amp<R>::T* sm, uint32_t N, in
     }
 }
 
-template <class R, int THREADS>
+// B > 0: the tile has exactly 2^B amplitudes (fixed-size paths); B = 0: any size.
+template <class R, int THREADS, int B = 0>
 __device__ __forceinline__ void tile_pairs(typename Amp<R>::T* sm, uint32_t N, int cls, int cb, int tb, const R* m) {
     if (cb < 0) {
         switch (cls) {
-        case GC_GENERAL: tile_1q<R, GC_GENERAL, THREADS>(sm, N, tb, m); break;
-        case GC_REAL: tile_1q<R, GC_REAL, THREADS>(sm, N, tb, m); break;
-        case GC_DIAG: tile_1q<R, GC_DIAG, THREADS>(sm, N, tb, m); break;
-        case GC_DIAG1: tile_1q<R, GC_DIAG1, THREADS>(sm, N, tb, m); break;
-        case GC_ANTIDIAG: tile_1q<R, GC_ANTIDIAG, THREADS>(sm, N, tb, m); break;
-        default: tile_1q<R, GC_PERM, THREADS>(sm, N, tb, m); break;
+        case GC_GENERAL: tile_1q_any<R, GC_GENERAL, THREADS, B>(sm, N, tb, m); break;
+        case GC_REAL: tile_1q_any<R, GC_REAL, THREADS, B>(sm, N, tb, m); break;
+        case GC_DIAG: tile_1q_any<R, GC_DIAG, THREADS, B>(sm, N, tb, m); break;
+        case GC_DIAG1: tile_1q_any<R, GC_DIAG1, THREADS, B>(sm, N, tb, m); break;
+        case GC_ANTIDIAG: tile_1q_any<R, GC_ANTIDIAG, THREADS, B>(sm, N, tb, m); break;
+        default: tile_1q_any<R, GC_PERM, THREADS, B>(sm, N, tb, m); break;
         }
     } else {
         switch (cls) {
-        case GC_GENERAL: tile_cu<R, GC_GENERAL, THREADS>(sm, N, cb, tb, m); break;
-        case GC_REAL: tile_cu<R, GC_REAL, THREADS>(sm, N, cb, tb, m); break;
-        case GC_DIAG: tile_cu<R, GC_DIAG, THREADS>(sm, N, cb, tb, m); break;
-        case GC_DIAG1: tile_cu<R, GC_DIAG1, THREADS>(sm, N, cb, tb, m); break;
-        case GC_ANTIDIAG: tile_cu<R, GC_ANTIDIAG, THREADS>(sm, N, cb, tb, m); break;
-        default: tile_cu<R, GC_PERM, THREADS>(sm, N, cb, tb, m); break;
+        case GC_GENERAL: tile_cu_any<R, GC_GENERAL, THREADS, B>(sm, N, cb, tb, m); break;
+        case GC_REAL: tile_cu_any<R, GC_REAL, THREADS, B>(sm, N, cb, tb, m); break;
+        case GC_DIAG: tile_cu_any<R, GC_DIAG, THREADS, B>(sm, N, cb, tb, m); break;
+        case GC_DIAG1: tile_cu_any<R, GC_DIAG1, THREADS, B>(sm, N, cb, tb, m); break;
+        case GC_ANTIDIAG: tile_cu_any<R, GC_ANTIDIAG, THREADS, B>(sm, N, cb, tb, m); break;
+        default: tile_cu_any<R, GC_PERM, THREADS, B>(sm, N, cb, tb, m); break;
         }
     }
 }
@@ -112,7 +172,7 @@ __device__ __forceinline__ void tile_pairs(typename Amp<R>::T* sm, uint32_t N, i
 // Apply one op to the tile whose non-tile qubits are fixed by `base`.  Every
 // branch depends only on the op and on base, so it is uniform over the CTA.
 // Returns false when the op leaves this tile unchanged (no barrier needed).
-template <class R, int THREADS>
+template <class R, int THREADS, int B = 0>
 __device__ __forceinline__ bool tile_apply(typename Amp<R>::T* sm, uint32_t N, const TileOp<R>& op, uint64_t base) {
     if (op.kind == OP_SWAP) {
         tile_swap<R, THREADS>(sm, N, op.tb, op.cb);
@@ -132,7 +192,7 @@ __device__ __forceinline__ bool tile_apply(typename Amp<R>::T* sm, uint32_t N, c
         tile_scale<R, THREADS>(sm, N, bit ? op.m[6] : op.m[0], bit ? op.m[7] : op.m[1], cb);
         return true;
     }
-    tile_pairs<R, THREADS>(sm, N, op.cls, cb, op.tb, op.m);
+    tile_pairs<R, THREADS, B>(sm, N, op.cls, cb, op.tb, op.m);
     return true;
 }
 
