@@ -19,7 +19,10 @@ namespace qs {
 
 namespace {
 
-constexpr int kTileThreads = 256;
+#ifndef QS_TILE_THREADS
+#define QS_TILE_THREADS 256
+#endif
+constexpr int kTileThreads = QS_TILE_THREADS;
 
 template <class R, int B = 0, class OpAt>
 __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, const TilePass& P, OpAt op_at) {
