@@ -88,6 +88,11 @@ _FLOPS = {"general": 14.0, "real": 6.0, "diag": 6.0, "diag1": 6.0, "antidiag": 6
 # dot4 = 4 df_mul + 3 TwoSum + 6 adds + TwoSum = 58; a complex output = 2 dots.
 _DF_FLOPS = {"general": 116.0, "real": 56.0, "diag": 56.0, "diag1": 56.0, "antidiag": 56.0, "perm": 0.0}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+# DRAM bytes (read + write) of one double-float tile launch, from the ncu capture
+# of the n=26 case (profiles/k_tile_df_c128_n26_full.md); a tile pass reads and
+# writes the whole state once, so traffic scales with 2^n.  Update (or set to
+# None) whenever the kernel changes.
+DF_TILE_TRAFFIC_N26 = 1.074563e9 + 1.012196e9
 
 
 def gate_cost(g, n, s, table=None):
@@ -371,7 +376,10 @@ def run_ours(args):
     achieved_tf = fp32_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
     roofline = {"bound": "alu", "kernel": "k_tile_df (fused tile pass, double-float)" if df else "k_tile<float>",
                 "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved_tf / FP32_PEAK_TFLOPS,
+                "traffic": (DF_TILE_TRAFFIC_N26 * 2.0 ** (n - 26)) if (df and DF_TILE_TRAFFIC_N26) else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one n=26 launch, "
+                                  "scaled by 2^(n-26)" if df else None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; MEASURED_PEAKS.json "
                                "has no FP32 figure (an FFMA probe on this GPU measured 74.2 TFLOP/s)",
                 "flops_counted": ("FP32 flops of the double-float updates the kernel applies (after in-pass "
