@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 comparison step")
-    ap.add_argument("--workload", default="qft30", choices=["qft30", "random33", "adjoint28"],
+    ap.add_argument("--workload", default="qft30", choices=["qft30", "random33", "adjoint28", "sweeps"],
                     help="qft30: the headline n=30 step; random33: n=33 complex128 / n=34 complex64 500-gate "
                          "circuits and the n=26 error table; adjoint28: n=28 complex64 adjoint vs parameter shift")
     return ap.parse_args()
@@ -596,6 +596,61 @@ def run_adjoint28(args):
     print(json.dumps(res), flush=True)
 
 
+def run_sweeps(args):
+    """Per-target single-gate GB/s at n=30 complex128 (strided kernels), the
+    controlled-gate (c, t) grid at n=30 (the Fig. 6 analogue), and IQFT fused
+    vs unfused for n = 18..30 (the Fig. 8 analogue)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1601_07195_gb300 import qs
+    n = 30
+    stream = torch.cuda.Stream()
+    out = {"workload": "sweeps", "n": n, "dtype": "c128"}
+    haar = G.gate_u1(0, G.haar_2x2(G.SplitMix64(9)))[0]["m"]
+    N = float(1 << n)
+    with qs.State.create(n, qs.QS_C128, stream=stream) as st:
+        st.init_basis(0)
+        for name, native in (("df", False), ("f64", True)):
+            st.set_arith(native)
+            st.apply_1q(0, haar)
+            per_k = []
+            for k in range(n):
+                ms, _ = _timed(lambda: [st.apply_1q(k, haar) for _ in range(3)], stream, torch)
+                per_k.append(2 * N * 16 / (ms / 3 / 1e3) / 1e9)
+            out[f"gate1q_GBps_by_target_{name}"] = per_k
+        st.set_arith(False)
+        grid = [[None] * n for _ in range(n)]
+        for c in range(n):
+            for t in range(n):
+                if c == t:
+                    continue
+                ms, _ = _timed(lambda: st.apply_ctrl(c, t, haar), stream, torch)
+                grid[c][t] = N * 16 / (ms / 1e3) / 1e9
+        flat = [v for row in grid for v in row if v is not None]
+        out["ctrl_GBps_grid"] = grid
+        out["ctrl_GBps_summary"] = {"min": min(flat), "max": max(flat), "mean": statistics.mean(flat),
+                                   "c0_mean": statistics.mean(v for v in grid[0] if v is not None),
+                                   "c_ge_10_mean": statistics.mean(v for c in range(10, n) for v in grid[c] if v is not None)}
+    torch.cuda.empty_cache()
+    iqft = []
+    for m in range(18, 31):
+        gates = G.inverse_circuit(G.qft_circuit(m))
+        bytes_ = sum(gate_cost(g, m, 16)[0] for g in gates)
+        row = {"n": m, "gates": len(gates)}
+        with qs.State.create(m, qs.QS_C128, stream=stream) as st:
+            for name, flags in (("fused", qs.PLAN_DEFAULT), ("unfused", qs.PLAN_NO_FUSION)):
+                p = st.plan(gates, flags=flags)
+                st.init_basis(1)
+                p.execute()
+                ms, _ = _timed(p.execute, stream, torch)
+                row[f"{name}_GBps"] = bytes_ / (ms / 1e3) / 1e9
+                row[f"{name}_passes"] = p.stats()["passes"]
+                p.close()
+        iqft.append(row)
+    out["iqft_fused_vs_unfused"] = iqft
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -604,6 +659,8 @@ def main():
         run_random33(args)
     elif args.workload == "adjoint28":
         run_adjoint28(args)
+    elif args.workload == "sweeps":
+        run_sweeps(args)
     else:
         run_ours(args)
 

@@ -101,6 +101,11 @@ QS_API qs_status qs_destroy(qs_state* s);
 /* Rebind the state to another stream of the same device. */
 QS_API qs_status qs_set_stream(qs_state* s, void* cuda_stream);
 
+/* Arithmetic of the single-gate calls (qs_apply_*) on a complex128 state:
+ * native_f64 = 0 (default) evaluates the 2x2 update in double-float form on
+ * the FP32 pipes, 1 uses native FP64 instructions (see QS_PLAN_ARITH_F64). */
+QS_API qs_status qs_set_arith(qs_state* s, int native_f64);
+
 /* Device address, qubit count and dtype of a state. */
 QS_API qs_status qs_info(const qs_state* s, void** dev_ptr, int* n, qs_dtype* dt);
 

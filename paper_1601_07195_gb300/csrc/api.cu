@@ -198,6 +198,12 @@ qs_status qs_set_stream(qs_state* s, void* stream) {
     return QS_OK;
 }
 
+qs_status qs_set_arith(qs_state* s, int native_f64) {
+    if (qs_status st = check_state(s)) return st;
+    s->arith_f64 = native_f64 != 0;
+    return QS_OK;
+}
+
 qs_status qs_info(const qs_state* s, void** dev_ptr, int* n, qs_dtype* dt) {
     if (!s) return fail(QS_EINVAL, "state handle is NULL");
     if (dev_ptr) *dev_ptr = s->data;
@@ -247,7 +253,7 @@ qs_status qs_apply_1q(qs_state* s, int k, const double U[8]) {
     std::memcpy(g.m, U, sizeof(g.m));
     std::vector<Op> ops;
     if (qs_status st = lower_gates(&g, 1, nullptr, 0, s->n, ops)) return st;
-    return launch_op(s, ops[0], false);
+    return launch_op(s, ops[0], s->arith_f64);
 }
 
 qs_status qs_apply_ctrl(qs_state* s, int c, int t, const double U[8]) {
@@ -258,7 +264,7 @@ qs_status qs_apply_ctrl(qs_state* s, int c, int t, const double U[8]) {
     std::memcpy(g.m, U, sizeof(g.m));
     std::vector<Op> ops;
     if (qs_status st = lower_gates(&g, 1, nullptr, 0, s->n, ops)) return st;
-    return launch_op(s, ops[0], false);
+    return launch_op(s, ops[0], s->arith_f64);
 }
 
 qs_status qs_apply_swap(qs_state* s, int a, int b) {
@@ -267,7 +273,7 @@ qs_status qs_apply_swap(qs_state* s, int a, int b) {
     g.kind = QS_G_SWAP; g.t = a; g.c = b; g.param = -1;
     std::vector<Op> ops;
     if (qs_status st = lower_gates(&g, 1, nullptr, 0, s->n, ops)) return st;
-    return launch_op(s, ops[0], false);
+    return launch_op(s, ops[0], s->arith_f64);
 }
 
 }  // extern "C"

@@ -102,6 +102,7 @@ struct qs_state {
     size_t partials_cap; // doubles
     double* h_result;    // pinned host staging for reduction results
     size_t h_result_cap;
+    bool arith_f64;      // complex128 single-gate kernels: native FP64 instead of double-float
 };
 
 namespace qs {

@@ -44,6 +44,7 @@ _SIGS = {
     "qs_wrap": [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)],
     "qs_destroy": [_vp],
     "qs_set_stream": [_vp, _vp],
+    "qs_set_arith": [_vp, ctypes.c_int],
     "qs_info": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "qs_init_basis": [_vp, ctypes.c_uint64],
     "qs_copy_out": [_vp, ctypes.c_uint64, ctypes.c_uint64, _vp],
@@ -197,6 +198,10 @@ class State:
 
     def set_stream(self, stream):
         _check(load().qs_set_stream(self._h, _stream_handle(stream)))
+
+    def set_arith(self, native_f64):
+        """complex128 single-gate calls: native FP64 (True) or double-float (False, default)."""
+        _check(load().qs_set_arith(self._h, 1 if native_f64 else 0))
 
     # ---- gates
     def apply_1q(self, k, m8):

@@ -57,13 +57,14 @@ MATS = {
 }
 
 
-@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("dt,native", [(1, False), (1, True), (0, False)])
 @pytest.mark.parametrize("n", [1, 5, 13])
-def test_single_qubit_gate_every_qubit_every_class(qs, dt, n):
+def test_single_qubit_gate_every_qubit_every_class(qs, dt, native, n):
     for name, m in MATS.items():
         for k in range(n):
             psi = rand_state(n, 100 * k + n)
             with upload(qs, n, dt, psi) as s:
+                s.set_arith(native)
                 s.apply_1q(k, m)
                 got = s.to_numpy()
             want = expected_input(psi, dt)
