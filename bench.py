@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 comparison step")
-    ap.add_argument("--workload", default="qft30", choices=["qft30", "random33", "adjoint28", "sweeps"],
+    ap.add_argument("--workload", default="qft30", choices=["qft30", "random33", "adjoint28", "sweeps", "batch512"],
                     help="qft30: the headline n=30 step; random33: n=33 complex128 / n=34 complex64 500-gate "
                          "circuits and the n=26 error table; adjoint28: n=28 complex64 adjoint vs parameter shift")
     return ap.parse_args()
@@ -255,6 +255,10 @@ def secondary_gradients(qs, dtype, torch):
     for r in range(reps):            # new angles each time: matrices re-staged, graph replayed
         batch.execute([G.angles(len(x["theta"]), 7000 + 1000 * r + k) for k, x in enumerate(insts)])
     t_adj = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for r in range(reps):            # same angles: graph replay only (no host-side matrix staging)
+        batch.execute()
+    t_replay = (time.perf_counter() - t0) / reps
     bstats = batch.stats()
     batch.close()
     # finite-difference comparator: 2P+1 energy evaluations per instance, on a sample
@@ -277,6 +281,7 @@ def secondary_gradients(qs, dtype, torch):
     t_fd = (time.perf_counter() - t0) / len(sample)
     return {"metric": "batched adjoint-gradient circuits/sec", "value": len(insts) / t_adj, "unit": "circuits/s",
             "instances": len(insts), "dtype": "c128" if dtype == 1 else "c64", "setup_s": t_setup,
+            "s_per_execution_new_angles": t_adj, "s_per_execution_same_angles": t_replay,
             "persistent_small_instances": bstats["small"], "structure_groups": bstats["groups"],
             "launches_per_execution": bstats["launches"],
             "timing": "host wall clock per qs_batch_execute (angle staging + graph replay + results), mean of 3",
@@ -661,6 +666,12 @@ def main():
         run_adjoint28(args)
     elif args.workload == "sweeps":
         run_sweeps(args)
+    elif args.workload == "batch512":
+        import torch
+        torch.cuda.set_device(0)
+        from paper_1601_07195_gb300 import qs
+        for dt in (qs.QS_C128, qs.QS_C64):
+            print(json.dumps(secondary_gradients(qs, dt, torch)), flush=True)
     else:
         run_ours(args)
 

@@ -170,7 +170,68 @@ __device__ __forceinline__ void adj_pairs(typename Tr::E* f, typename Tr::E* l, 
     }
 }
 
-template <class Tr, int THREADS>
+// Fixed-size tiles (2^B amplitudes): per-thread base index plus CTA-uniform
+// offsets, two pairs of both states per unrolled step (see tile_df_ops.cuh).
+template <class Tr, int CLS, int THREADS, int B>
+__device__ __forceinline__ void adj_pairs_fixed(typename Tr::E* f, typename Tr::E* l, int cb, int tb,
+                                                const typename Tr::Op& op, int gen, GAcc& acc) {
+    using E = typename Tr::E;
+    if (cb < 0) {
+        constexpr int PAIRS = (1 << (B - 1)) / THREADS;
+        const uint32_t i0 = insert_zero32(threadIdx.x, tb), h = 1u << tb;
+#pragma unroll
+        for (int m = 0; m < PAIRS; m += 2) {
+            const uint32_t a = i0 + insert_zero32((uint32_t)(m * THREADS), tb);
+            const uint32_t b = i0 + insert_zero32((uint32_t)((m + 1) * THREADS), tb);
+            E f0 = f[a], f1 = f[a + h], l0 = l[a], l1 = l[a + h];
+            E g0 = f[b], g1 = f[b + h], k0 = l[b], k1 = l[b + h];
+            if (gen) { gen_acc<Tr>(acc, gen, f0, f1, l0, l1); gen_acc<Tr>(acc, gen, g0, g1, k0, k1); }
+            Tr::template pair<CLS>(op, f0, f1);
+            Tr::template pair<CLS>(op, l0, l1);
+            Tr::template pair<CLS>(op, g0, g1);
+            Tr::template pair<CLS>(op, k0, k1);
+            f[a] = f0; f[a + h] = f1; l[a] = l0; l[a + h] = l1;
+            f[b] = g0; f[b + h] = g1; l[b] = k0; l[b + h] = k1;
+        }
+    } else {
+        constexpr int ITEMS = (1 << (B - 2)) / THREADS;
+        const int lo = min(cb, tb), hi = max(cb, tb);
+        const uint32_t i0 = insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb), h = 1u << tb;
+#pragma unroll
+        for (int m = 0; m < ITEMS; m += 2) {
+            const uint32_t a = i0 + insert_two_zeros32((uint32_t)(m * THREADS), lo, hi);
+            const uint32_t b = i0 + insert_two_zeros32((uint32_t)((m + 1) * THREADS), lo, hi);
+            E f0 = f[a], f1 = f[a + h], l0 = l[a], l1 = l[a + h];
+            E g0 = f[b], g1 = f[b + h], k0 = l[b], k1 = l[b + h];
+            if (gen) { gen_acc<Tr>(acc, gen, f0, f1, l0, l1); gen_acc<Tr>(acc, gen, g0, g1, k0, k1); }
+            Tr::template pair<CLS>(op, f0, f1);
+            Tr::template pair<CLS>(op, l0, l1);
+            Tr::template pair<CLS>(op, g0, g1);
+            Tr::template pair<CLS>(op, k0, k1);
+            f[a] = f0; f[a + h] = f1; l[a] = l0; l[a + h] = l1;
+            f[b] = g0; f[b + h] = g1; l[b] = k0; l[b + h] = k1;
+        }
+    }
+}
+
+template <class Tr, int CLS, int THREADS, int B>
+__device__ __forceinline__ void adj_pairs_any(typename Tr::E* f, typename Tr::E* l, uint32_t N, int cb, int tb,
+                                              const typename Tr::Op& op, int gen, GAcc& acc) {
+    if constexpr (B > 0 && (1 << (B - 2)) / THREADS >= 2) adj_pairs_fixed<Tr, CLS, THREADS, B>(f, l, cb, tb, op, gen, acc);
+    else adj_pairs<Tr, CLS, THREADS>(f, l, N, cb, tb, op, gen, acc);
+}
+
+__device__ __forceinline__ double warp_sum_only(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One reversed op on the (phi, lambda) tiles.  A rotation's gradient partial is
+// written to out[op.pad1]: reduced over the CTA (WARP_SLOTS = false), or only
+// over each warp into out[op.pad1 * warps + warp] (WARP_SLOTS = true; the caller
+// sums the warps once after the pass, saving two barriers per rotation).
+template <class Tr, int THREADS, int B = 0, bool WARP_SLOTS = false>
 __device__ __forceinline__ void adj_apply(typename Tr::E* f, typename Tr::E* l, uint32_t N, const typename Tr::Op& op,
                                           uint64_t base, double* red, double* out) {
     using E = typename Tr::E;
@@ -209,35 +270,44 @@ __device__ __forceinline__ void adj_apply(typename Tr::E* f, typename Tr::E* l, 
             }
         } else {
             switch (op.cls) {
-            case GC_GENERAL: adj_pairs<Tr, GC_GENERAL, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
-            case GC_REAL: adj_pairs<Tr, GC_REAL, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
-            case GC_DIAG: adj_pairs<Tr, GC_DIAG, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
-            case GC_DIAG1: adj_pairs<Tr, GC_DIAG1, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
-            case GC_ANTIDIAG: adj_pairs<Tr, GC_ANTIDIAG, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
-            default: adj_pairs<Tr, GC_PERM, THREADS>(f, l, N, cb, op.tb, op, gen, acc); break;
+            case GC_GENERAL: adj_pairs_any<Tr, GC_GENERAL, THREADS, B>(f, l, N, cb, op.tb, op, gen, acc); break;
+            case GC_REAL: adj_pairs_any<Tr, GC_REAL, THREADS, B>(f, l, N, cb, op.tb, op, gen, acc); break;
+            case GC_DIAG: adj_pairs_any<Tr, GC_DIAG, THREADS, B>(f, l, N, cb, op.tb, op, gen, acc); break;
+            case GC_DIAG1: adj_pairs_any<Tr, GC_DIAG1, THREADS, B>(f, l, N, cb, op.tb, op, gen, acc); break;
+            case GC_ANTIDIAG: adj_pairs_any<Tr, GC_ANTIDIAG, THREADS, B>(f, l, N, cb, op.tb, op, gen, acc); break;
+            default: adj_pairs_any<Tr, GC_PERM, THREADS, B>(f, l, N, cb, op.tb, op, gen, acc); break;
             }
         }
     }
     if (gen) {  // uniform over the CTA: every thread takes part in the reduction
-        const double s = block_sum_b(active ? gacc_value(acc) : 0.0, red);
-        if (threadIdx.x == 0) out[op.pad1] = s;
+        if constexpr (WARP_SLOTS) {
+            const double w = warp_sum_only(active ? gacc_value(acc) : 0.0);
+            if ((threadIdx.x & 31) == 0) out[op.pad1 * (THREADS / 32) + (threadIdx.x >> 5)] = w;
+        } else {
+            const double s = block_sum_b(active ? gacc_value(acc) : 0.0, red);
+            if (threadIdx.x == 0) out[op.pad1] = s;
+        }
     }
 }
 
 // ---- reverse tile pass over a group of instances --------------------------------
-template <class Tr>
+constexpr int kMaxAdjSlots = 1024;  // rotation gates per reverse tile pass (per-warp slots in dynamic SMEM)
+
+template <class Tr, int B>
 __global__ void __launch_bounds__(kAdjThreads) k_tile_adj(typename Tr::G* __restrict__ phi,
                                                           typename Tr::G* __restrict__ lam,
                                                           const typename Tr::Op* __restrict__ ops, TilePass P,
                                                           double* __restrict__ partials, int n_slots) {
     using E = typename Tr::E;
+    constexpr int kWarps = kAdjThreads / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     const int b = P.b, b0 = P.b0, nh = b - b0;
     const uint32_t N = 1u << b;
     E* f = reinterpret_cast<E*>(smem_raw);
     E* l = f + N;
-    uint64_t* hioff = reinterpret_cast<uint64_t*>(l + N);
+    double* wslots = reinterpret_cast<double*>(l + N);        // n_slots x warps
+    uint64_t* hioff = reinterpret_cast<uint64_t*>(wslots + (size_t)n_slots * kWarps);
     phi += (uint64_t)blockIdx.y * P.inst_stride;
     lam += (uint64_t)blockIdx.y * P.inst_stride;
     ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride;
@@ -259,13 +329,19 @@ __global__ void __launch_bounds__(kAdjThreads) k_tile_adj(typename Tr::G* __rest
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
         const typename Tr::Op op = ops[P.op0 + g];
-        adj_apply<Tr, kAdjThreads>(f, l, N, op, base, red, out);
+        adj_apply<Tr, kAdjThreads, B, true>(f, l, N, op, base, red, wslots);
         __syncthreads();
     }
     for (uint32_t e = threadIdx.x; e < N; e += kAdjThreads) {
         const uint64_t g = base + hioff[e >> b0] + (e & lomask);
         phi[g] = Tr::store(f[e]);
         lam[g] = Tr::store(l[e]);
+    }
+    // rotation partials: the warps' sums in fixed order (slots this pass does not use are never read)
+    for (int sl = threadIdx.x; sl < n_slots; sl += kAdjThreads) {
+        double acc = 0.0;
+        for (int w = 0; w < kWarps; ++w) acc += wslots[sl * kWarps + w];
+        out[sl] = acc;
     }
 }
 
@@ -688,7 +764,8 @@ qs_status record(qs_batch* bt) {
         QS_CUDA_TRY(cudaGetLastError());
         // reverse sweep
         op0 = 0;
-        const size_t smem = ((size_t)2 * sizeof(T) << g.b_adj) + ((size_t)8 << g.b_adj);
+        const size_t smem = ((size_t)2 * sizeof(T) << g.b_adj) + ((size_t)8 << g.b_adj) +
+                            (size_t)g.n_slots * (kAdjThreads / 32) * sizeof(double);
         for (size_t pi = 0; pi < g.rev.size(); ++pi) {
             const PassDesc& d = g.rev[pi];
             TilePass tp = d.tp;
@@ -697,9 +774,11 @@ qs_status record(qs_batch* bt) {
             tp.inst_stride = N;
             tp.ops_stride = (int)g.rev_per;
             const unsigned tiles = (unsigned)(1ull << (g.n - tp.b));
-            k_tile_adj<Tr><<<dim3(tiles, count), kAdjThreads, smem, st>>>(
-                (T*)g.phi, (T*)g.lam, reinterpret_cast<const OpT*>(bt->d_stage + g.st_rev.off), tp, g.d_part,
-                g.n_slots);
+            const OpT* rops = reinterpret_cast<const OpT*>(bt->d_stage + g.st_rev.off);
+            const dim3 grid(tiles, count);
+            if (tp.b == 11) k_tile_adj<Tr, 11><<<grid, kAdjThreads, smem, st>>>((T*)g.phi, (T*)g.lam, rops, tp, g.d_part, g.n_slots);
+            else if (tp.b == 12) k_tile_adj<Tr, 12><<<grid, kAdjThreads, smem, st>>>((T*)g.phi, (T*)g.lam, rops, tp, g.d_part, g.n_slots);
+            else k_tile_adj<Tr, 0><<<grid, kAdjThreads, smem, st>>>((T*)g.phi, (T*)g.lam, rops, tp, g.d_part, g.n_slots);
             QS_CUDA_TRY(cudaGetLastError());
             if (g.rev_nslot_used[pi] > 0) {
                 const int work = (int)count * g.n_slots;
@@ -822,6 +901,7 @@ qs_status build_batch(qs_batch* bt) {
                 if (rot_gen(in.gates[ops.size() - 1 - j].kind)) ++c;
             g.n_slots = std::max(g.n_slots, c);
         }
+        if (g.n_slots > kMaxAdjSlots) return fail(QS_EINVAL, "batch: more than 1024 rotation gates in one reverse tile pass");
         g.slot_rot.assign(g.rev.size() * g.n_slots, -1);
         g.rev_nslot_used.assign(g.rev.size(), 0);
         for (size_t pi = 0; pi < g.rev.size(); ++pi) {
@@ -927,10 +1007,14 @@ qs_status build_batch(qs_batch* bt) {
     // kernels that take more than 48 KiB of dynamic shared memory (set outside any graph capture)
     if (c128) {
         if (qs_status st = allow_dynamic_smem(k_batch_small<TrDF>)) return st;
-        if (qs_status st = allow_dynamic_smem(k_tile_adj<TrDF>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_tile_adj<TrDF, 0>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_tile_adj<TrDF, 11>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_tile_adj<TrDF, 12>)) return st;
     } else {
         if (qs_status st = allow_dynamic_smem(k_batch_small<TrF>)) return st;
-        if (qs_status st = allow_dynamic_smem(k_tile_adj<TrF>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_tile_adj<TrF, 0>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_tile_adj<TrF, 11>)) return st;
+        if (qs_status st = allow_dynamic_smem(k_tile_adj<TrF, 12>)) return st;
     }
     return QS_OK;
 }

@@ -47,11 +47,26 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
 }
 
 // ops in device memory (batched launches: one op array per instance)
+template <int B>
 __global__ void __launch_bounds__(kThreads) k_tile_df(double2* __restrict__ psi, const TileOpDF* __restrict__ ops,
                                                       TilePass P) {
     psi += (uint64_t)blockIdx.y * P.inst_stride;
     ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride + P.op0;
-    tile_df_body(psi, P, [&](int g) { return ops[g]; });
+    tile_df_body<B>(psi, P, [&](int g) { return ops[g]; });
+}
+
+template <int B>
+cudaError_t launch_df_ptr(qs_state* s, const void* d_ops, const TilePass& P, unsigned count, size_t smem) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_df<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const dim3 grid((unsigned)(1ull << (s->n - P.b)), count);
+    k_tile_df<B><<<grid, kThreads, smem, s->stream>>>(reinterpret_cast<double2*>(s->data),
+                                                      reinterpret_cast<const TileOpDF*>(d_ops), P);
+    return cudaGetLastError();
 }
 
 // ops in the kernel's parameter block: read through the constant cache,
@@ -110,16 +125,11 @@ int tile_df_param_ops() { return kParamOps; }
 
 cudaError_t launch_tile_df(qs_state* s, const void* d_ops, const TilePass& P, unsigned count) {
     const size_t smem = tile_smem_bytes(s->dt, P.b) + ((size_t)8 << (P.b - P.b0));
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
-        if (e != cudaSuccess) return e;
-        configured = true;
+    switch (P.b) {
+    case 12: return launch_df_ptr<12>(s, d_ops, P, count, smem);
+    case 13: return launch_df_ptr<13>(s, d_ops, P, count, smem);
+    default: return launch_df_ptr<0>(s, d_ops, P, count, smem);
     }
-    const dim3 grid((unsigned)(1ull << (s->n - P.b)), count);
-    k_tile_df<<<grid, kThreads, smem, s->stream>>>(reinterpret_cast<double2*>(s->data),
-                                                   reinterpret_cast<const TileOpDF*>(d_ops), P);
-    return cudaGetLastError();
 }
 
 }  // namespace qs
