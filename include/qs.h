@@ -142,8 +142,15 @@ enum {
                                FP32, with a per-gate error of order 2^-44 relative to the
                                amplitudes involved instead of 2^-53. */
     QS_PLAN_DRY_RUN = 8,    /* plan on the host only (no device memory); cannot execute */
-    QS_PLAN_NO_MERGE = 16   /* keep every gate separate: no product of adjacent single-qubit
+    QS_PLAN_NO_MERGE = 16,  /* keep every gate separate: no product of adjacent single-qubit
                                gates on the same qubit inside a tile pass */
+    QS_PLAN_NO_PHASE_RUNS = 32  /* apply runs of phase gates one by one.  Without it, a run of
+                               consecutive gates inside a tile pass that are diagonal with
+                               q11 = 1 (T, S, phase, CZ, controlled phase) and all involve one
+                               tile qubit j (the controlled-phase chains of the QFT, Section 5)
+                               is applied as one update: per tile, a table of phase products
+                               over the low and the high half of the tile bits, and two complex
+                               products per amplitude whose bit j is 1. */
 };
 
 /* Build an execution plan for `gates` (copied in) on state s: gate classes,
@@ -166,13 +173,16 @@ QS_API qs_status qs_plan_stats(const qs_plan* p, int* n_passes, int* n_tile_pass
 
 /* Gate updates one execution applies after fusing adjacent single-qubit gates
  * on the same qubit within a tile pass (into their product, where that is
- * cheaper to apply; exact identities are dropped). */
+ * cheaper to apply; exact identities are dropped) and runs of phase gates
+ * (one update per run, see QS_PLAN_NO_PHASE_RUNS). */
 QS_API qs_status qs_plan_device_ops(const qs_plan* p, int* n_ops);
 
 /* Gate updates of pass i as the kernels apply them (after fusion): counts[3][6]
  * by operation (0 = single-qubit, 1 = controlled, 2 = swap) and class
  * (0 general, 1 real, 2 diagonal, 3 diagonal with q11 = 1, 4 anti-diagonal,
- * 5 permutation). */
+ * 5 permutation).  A fused run of phase gates counts as one single-qubit
+ * diagonal update: two complex products on half the amplitudes, the same
+ * arithmetic. */
 QS_API qs_status qs_plan_pass_op_counts(const qs_plan* p, int i, int* counts);
 
 /* Per-pass description: for pass i, its kind (0 = single gate, 1 = tile),

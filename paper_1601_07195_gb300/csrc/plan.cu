@@ -187,6 +187,125 @@ std::vector<Op> fuse_single_qubit(const std::vector<Op>& ops, const std::vector<
     return live;
 }
 
+// ---- fused runs of phase gates (record layout in qs_internal.h) -----------------
+// A maximal sequence of consecutive ops of the pass (after matrix fusion) that
+// are diagonal with q11 = 1 and all involve one tile qubit j.  Its product
+// changes only amplitudes with bit j = 1, by a factor that is a product of
+// one factor per other qubit: the kernel builds two tables over the low and
+// high halves of the tile index and applies two complex products per changed
+// amplitude instead of one product per gate.  Fused when the gates' cost
+// (class_cost units) is above the run's own.
+bool phase_gate(const Op& o) { return (o.kind == OP_1Q || o.kind == OP_CU) && o.cls == GC_DIAG1; }
+
+int phase_gate_cost(const Op& o, qs_dtype dt) {
+    const int c = class_cost(GC_DIAG1, dt);
+    return (o.kind == OP_1Q ? c : c / 2) + 12;
+}
+int phase_run_cost(qs_dtype dt) { return 2 * class_cost(GC_DIAG1, dt) + 5 * 12; }
+
+void cmul_acc(double* acc, double r, double i) {
+    const double ar = acc[0], ai = acc[1];
+    acc[0] = ar * r - ai * i;
+    acc[1] = ar * i + ai * r;
+}
+
+void set_slot(TileOpDF& r, int f, const double* v) {
+    split_to_floats(v[0], r.c[4 * f], r.c[4 * f + 1]);
+    split_to_floats(v[1], r.c[4 * f + 2], r.c[4 * f + 3]);
+}
+template <class R> void set_slot(TileOp<R>& r, int f, const double* v) {
+    r.m[2 * f] = (R)v[0];
+    r.m[2 * f + 1] = (R)v[1];
+}
+template <class OpT> void set_slot_qubit(OpT& r, int f, int q) {
+    if (f == 0) r.tb = q;
+    else if (f == 1) r.tq = q;
+    else if (f == 2) r.cb = q;
+    else r.cq = q;
+}
+
+// Records of the run ops[i0, i1) around pivot qubit j (tile bit bit_of[j]).
+template <class OpT>
+void emit_phase_run(const std::vector<Op>& ops, size_t i0, size_t i1, int j, const int* bit_of, int b,
+                    std::vector<OpT>& out) {
+    double c0[2] = {1.0, 0.0};
+    std::vector<double> psi(2 * (size_t)b, 0.0);
+    for (int k = 0; k < b; ++k) psi[2 * k] = 1.0;
+    std::map<int, std::pair<double, double>> outside;  // qubit -> factor
+    for (size_t i = i0; i < i1; ++i) {
+        const Op& o = ops[i];
+        const double fr = o.m[6], fi = o.m[7];  // q22: the phase applied when every qubit of the gate is 1
+        const int k = o.kind == OP_1Q ? -1 : (o.t == j ? o.c : o.t);
+        if (k < 0) {
+            cmul_acc(c0, fr, fi);
+        } else if (bit_of[k] >= 0) {
+            cmul_acc(&psi[2 * bit_of[k]], fr, fi);
+        } else {
+            auto it = outside.emplace(k, std::make_pair(1.0, 0.0)).first;
+            double acc[2] = {it->second.first, it->second.second};
+            cmul_acc(acc, fr, fi);
+            it->second = {acc[0], acc[1]};
+        }
+    }
+    const int tile_rec = (b + 3) / 4, out_rec = ((int)outside.size() + 3) / 4;
+    OpT h{};
+    h.kind = OP_PRUN;
+    h.cls = tile_rec + out_rec;
+    h.tb = bit_of[j];
+    h.tq = j;
+    h.cb = (int)outside.size();
+    h.cq = prun_lo_bits(b);
+    set_slot(h, 0, c0);
+    out.push_back(h);
+    for (int r = 0; r < tile_rec; ++r) {
+        OpT d{};
+        d.kind = OP_PDATA;
+        const double one[2] = {1.0, 0.0};
+        for (int f = 0; f < 4; ++f) set_slot(d, f, 4 * r + f < b ? &psi[2 * (4 * r + f)] : one);
+        out.push_back(d);
+    }
+    auto it = outside.begin();
+    for (int r = 0; r < out_rec; ++r) {
+        OpT d{};
+        d.kind = OP_PDATA;
+        d.tb = d.tq = d.cb = d.cq = 0;
+        const double one[2] = {1.0, 0.0};
+        for (int f = 0; f < 4; ++f) {
+            if (it != outside.end()) {
+                const double v[2] = {it->second.first, it->second.second};
+                set_slot(d, f, v);
+                set_slot_qubit(d, f, it->first);
+                ++it;
+            } else {
+                set_slot(d, f, one);
+            }
+        }
+        out.push_back(d);
+    }
+}
+
+// Length of the longest run starting at ops[i] and its pivot (-1: none worth fusing).
+size_t find_phase_run(const std::vector<Op>& ops, size_t i, const int* bit_of, qs_dtype dt, int& pivot) {
+    pivot = -1;
+    if (!phase_gate(ops[i])) return 0;
+    size_t best = 0;
+    const int cand[2] = {ops[i].t, ops[i].c};
+    for (int q : cand) {
+        if (q < 0 || bit_of[q] < 0) continue;
+        size_t k = i;
+        int cost = 0;
+        while (k < ops.size() && phase_gate(ops[k]) && (ops[k].t == q || ops[k].c == q)) {
+            cost += phase_gate_cost(ops[k], dt);
+            ++k;
+        }
+        if (k - i > best && cost > phase_run_cost(dt)) {
+            best = k - i;
+            pivot = q;
+        }
+    }
+    return best;
+}
+
 template <class OpT>
 qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse, bool upload) {
     std::vector<PassDesc> descs;
@@ -211,15 +330,30 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
         pp.tp = d.tp;
         pp.tp.op0 = (int)tops.size();
         const std::vector<Op> fused = fuse_single_qubit(ops, d.members, p->s->dt, !(p->flags & QS_PLAN_NO_MERGE));
-        pp.tp.nops = (int)fused.size();
         pp.moves_only = true;
-        for (const Op& o : fused) {
+        const bool runs = !(p->flags & QS_PLAN_NO_PHASE_RUNS);
+        for (size_t i = 0; i < fused.size();) {
+            int pivot = -1;
+            const size_t len = runs ? find_phase_run(fused, i, d.bit_of, p->s->dt, pivot) : 0;
+            if (len > 0) {
+                const size_t before = tops.size();
+                emit_phase_run(fused, i, i + len, pivot, d.bit_of, d.tp.b, tops);
+                if (df) t64.resize(t64.size() + (tops.size() - before), TileOp<double>{});
+                // two complex products on half the tile: the arithmetic of one single-qubit diagonal gate
+                pp.op_counts[OP_1Q][GC_DIAG] += 1;
+                pp.moves_only = false;
+                p->device_ops += 1;
+                i += len;
+                continue;
+            }
+            const Op& o = fused[i++];
             pp.op_counts[o.kind][o.cls] += 1;
             tops.push_back(to_tile_op<OpT>(o, d.bit_of));
             if (df) t64.push_back(to_tile_op<TileOp<double>>(o, d.bit_of));
             if (!(o.kind == OP_SWAP || o.cls == GC_PERM)) pp.moves_only = false;
+            p->device_ops += 1;
         }
-        p->device_ops += (int)fused.size();
+        pp.tp.nops = (int)tops.size() - pp.tp.op0;
         p->passes.push_back(pp);
     }
     if (upload) {
@@ -374,7 +508,7 @@ qs_status qs_plan_create(qs_state* s, const qs_gate* gates, int n_gates, const d
     if (req_b0 > 0) b0 = req_b0;
     if (b0 > b) b0 = b;
     if (!(flags & QS_PLAN_DRY_RUN) &&  // a host-only plan is not bound by this device's shared memory
-        tile_smem_bytes(s->dt, std::min(b, s->n)) + ((size_t)8 << (std::min(b, s->n) - std::min(b0, s->n))) > smem_optin())
+        tile_pass_smem(s->dt, std::min(b, s->n), std::min(b0, s->n)) > smem_optin())
         return fail(QS_EINVAL, "tile shape too large for shared memory");
     qs_plan* p = new (std::nothrow) qs_plan();
     if (!p) return fail(QS_ENOMEM, "host allocation failed");
@@ -532,7 +666,7 @@ qs_status qs_autotune(qs_state* s, const qs_gate* gates, int n_gates, const doub
     qs_status out = QS_OK;
     for (int b = std::min(bmin, s->n); b <= std::min(kMaxTileBits, s->n) && out == QS_OK; ++b) {
         for (int b0 = 3; b0 <= 6 && b0 <= b - 2; ++b0) {
-            if (tile_smem_bytes(s->dt, b) + ((size_t)8 << (b - b0)) > smem_optin()) continue;
+            if (tile_pass_smem(s->dt, b, b0) > smem_optin()) continue;
             qs_plan* p = nullptr;
             out = qs_plan_create(s, gates, n_gates, theta, n_params, QS_PLAN_DEFAULT, b | (b0 << 8), &p);
             if (out != QS_OK) break;

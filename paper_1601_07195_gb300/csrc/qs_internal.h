@@ -22,8 +22,10 @@ enum GateClass : int {
     GC_PERM = 5       // exactly [[0,1],[1,0]] (X): a move
 };
 
-// Operation kinds after lowering the gate records.
-enum OpKind : int { OP_1Q = 0, OP_CU = 1, OP_SWAP = 2 };
+// Operation kinds after lowering the gate records.  OP_PRUN and OP_PDATA occur
+// only in tile-pass records: a fused run of phase gates around one qubit (a
+// header record followed by cls payload records of kind OP_PDATA).
+enum OpKind : int { OP_1Q = 0, OP_CU = 1, OP_SWAP = 2, OP_PRUN = 3, OP_PDATA = 4 };
 
 // A lowered gate (host side, FP64 matrix).
 struct Op {
@@ -59,6 +61,30 @@ struct TileOpDF {
 };
 
 constexpr int kMaxTileBits = 14;
+
+// Fused phase runs (plan.cu builds them, tile_ops.cuh / tile_df_ops.cuh apply
+// them).  A run is a sequence of gates diagonal with q11 = 1 (phase gates on
+// qubit j, controlled phases between j and other qubits k) that all involve
+// the pivot qubit j, a tile bit jb.  The run multiplies each amplitude whose
+// bit j is 1 by   C * T_lo[e & (2^lob - 1)] * T_hi[e >> lob]   where e is the
+// tile index, T_lo / T_hi are products of the per-tile-bit factors psi_k over
+// the set bits of the low / high part of e, and C is the product of the phase
+// gates on j alone and of the factors of qubits outside the tile that are 1 in
+// the tile's base index.  Records:
+//   header  kind OP_PRUN, cls = payload records, tb = jb, tq = j,
+//           cb = number of outside factors, cq = lob; factor slot 0 = the
+//           phase gates on j alone (product)
+//   payload ceil(b / 4) records of dense per-tile-bit factors psi_0..psi_{b-1}
+//           (identity where no gate couples j with that bit), then
+//           ceil(cb / 4) records of outside factors whose qubits are in the
+//           int fields tb, tq, cb, cq (factor slots 0..3)
+// A factor slot f of a record holds one complex number: m[2f], m[2f+1]
+// (native records) or c[4f..4f+3] = re.hi, re.lo, im.hi, im.lo (double-float).
+inline int prun_lo_bits(int b) { return b / 2; }
+// shared-memory entries (16 bytes each) for T_lo, T_hi and C
+inline size_t prun_table_entries(int b) {
+    return ((size_t)1 << prun_lo_bits(b)) + ((size_t)1 << (b - prun_lo_bits(b))) + 1;
+}
 
 // Kernel argument describing one tile pass (by value).
 struct TilePass {
@@ -146,6 +172,11 @@ qs_status launch_tile_pass_params(qs_state* s, const void* h_ops, const TilePass
 int tile_param_ops(bool f64);
 void split_to_floats(double x, float& hi, float& lo);
 size_t tile_smem_bytes(qs_dtype dt, int b);
+// dynamic shared memory of a tile pass: the tile, the phase-run tables, the
+// offsets of the 2^(b - b0) contiguous runs
+inline size_t tile_pass_smem(qs_dtype dt, int b, int b0) {
+    return tile_smem_bytes(dt, b) + 16 * prun_table_entries(b) + ((size_t)8 << (b - b0));
+}
 
 // Reductions (reduce.cu).
 qs_status ensure_scratch(qs_state* s, size_t partial_doubles, size_t result_doubles);

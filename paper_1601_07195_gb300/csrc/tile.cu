@@ -31,7 +31,9 @@ __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, 
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int b = P.b, b0 = P.b0, nh = b - b0;
     const uint32_t N = 1u << b;
-    uint64_t* hioff = reinterpret_cast<uint64_t*>(sm + N);
+    // tile, then the phase-run tables (16 bytes per entry, qs_internal.h), then the run offsets
+    unsigned char* tab = smem_raw + (sizeof(T) << b);
+    uint64_t* hioff = reinterpret_cast<uint64_t*>(tab + 16u * ((1u << (b / 2)) + (1u << (b - b / 2)) + 1u));
     const uint64_t base = deposit_bits((uint64_t)blockIdx.x, P.nontile_mask);
     for (uint32_t h = threadIdx.x; h < (1u << nh); h += kTileThreads) {
         uint64_t off = 0;
@@ -44,7 +46,14 @@ __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, 
     for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) sm[e] = psi[base + hioff[e >> b0] + (e & lomask)];
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
-        if (tile_apply<R, kTileThreads, B>(sm, N, op_at(g), base)) __syncthreads();
+        auto&& op = op_at(g);
+        if (op.kind == OP_PRUN) {
+            phase_run<R, kTileThreads, B>(sm, tab, N, b, op, op_at, g, base);
+            g += op.cls;  // the run's payload records
+            __syncthreads();
+        } else if (tile_apply<R, kTileThreads, B>(sm, N, op, base)) {
+            __syncthreads();
+        }
     }
     for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) psi[base + hioff[e >> b0] + (e & lomask)] = sm[e];
 }
@@ -55,7 +64,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(typename Amp<R>::T* __res
                                                        const TileOp<R>* __restrict__ ops, TilePass P) {
     psi += (uint64_t)blockIdx.y * P.inst_stride;
     ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride + P.op0;
-    tile_body<R>(psi, P, [&](int g) { return ops[g]; });
+    tile_body<R>(psi, P, [&](int g) -> const TileOp<R>& { return ops[g]; });
 }
 
 // ops in the kernel's parameter block (constant cache, no global load per op)
@@ -86,7 +95,7 @@ cudaError_t launch_p(qs_state* s, const TileParams<R>& L, size_t smem) {
 
 template <class R>
 cudaError_t launch_tile(qs_state* s, const void* d_ops, const TilePass& P, unsigned count) {
-    const size_t smem = tile_smem_bytes(s->dt, P.b) + ((size_t)8 << (P.b - P.b0));
+    const size_t smem = tile_pass_smem(s->dt, P.b, P.b0);
     static bool configured[2] = {false, false};
     const int which = sizeof(R) == 8 ? 1 : 0;
     if (!configured[which]) {
@@ -103,7 +112,7 @@ cudaError_t launch_tile(qs_state* s, const void* d_ops, const TilePass& P, unsig
 template <class R>
 cudaError_t launch_tile_p(qs_state* s, const void* h_ops, const TilePass& P) {
     if (P.nops > TileParams<R>::kOps) return cudaErrorInvalidValue;
-    const size_t smem = tile_smem_bytes(s->dt, P.b) + ((size_t)8 << (P.b - P.b0));
+    const size_t smem = tile_pass_smem(s->dt, P.b, P.b0);
     static thread_local TileParams<R> L;
     L.P = P;
     L.P.op0 = 0;
@@ -124,7 +133,7 @@ size_t tile_smem_bytes(qs_dtype dt, int b) { return amp_bytes(dt) << b; }
 int tile_param_ops(bool f64) { return f64 ? TileParams<double>::kOps : TileParams<float>::kOps; }
 
 qs_status launch_tile_pass_params(qs_state* s, const void* h_ops, const TilePass& pass, bool f64) {
-    if (tile_smem_bytes(s->dt, pass.b) + ((size_t)8 << (pass.b - pass.b0)) > smem_optin())
+    if (tile_pass_smem(s->dt, pass.b, pass.b0) > smem_optin())
         return fail(QS_EINVAL, "tile does not fit in shared memory");
     cudaError_t e = f64 ? launch_tile_p<double>(s, h_ops, pass) : launch_tile_p<float>(s, h_ops, pass);
     if (e != cudaSuccess) return cuda_fail(e, "tile kernel launch");
@@ -132,7 +141,7 @@ qs_status launch_tile_pass_params(qs_state* s, const void* h_ops, const TilePass
 }
 
 qs_status launch_tile_pass(qs_state* s, const void* d_ops, const TilePass& pass, bool arith_f64, unsigned count) {
-    if (tile_smem_bytes(s->dt, pass.b) + ((size_t)8 << (pass.b - pass.b0)) > smem_optin())
+    if (tile_pass_smem(s->dt, pass.b, pass.b0) > smem_optin())
         return fail(QS_EINVAL, "tile does not fit in shared memory");
     cudaError_t e;
     if (s->dt == QS_C64) e = launch_tile<float>(s, d_ops, pass, count);

@@ -28,7 +28,9 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
     float4* sm = reinterpret_cast<float4*>(smem_raw);
     const int b = P.b, b0 = P.b0, nh = b - b0;
     const uint32_t N = 1u << b;
-    uint64_t* hioff = reinterpret_cast<uint64_t*>(sm + N);
+    // tile, then the phase-run tables (qs_internal.h), then the run offsets
+    float4* tab = sm + N;
+    uint64_t* hioff = reinterpret_cast<uint64_t*>(tab + (1u << (b / 2)) + (1u << (b - b / 2)) + 1u);
     const uint64_t base = deposit_bits((uint64_t)blockIdx.x, P.nontile_mask);
     for (uint32_t h = threadIdx.x; h < (1u << nh); h += kThreads) {
         uint64_t off = 0;
@@ -41,7 +43,14 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
     for (uint32_t e = threadIdx.x; e < N; e += kThreads) sm[e] = df_load(psi[base + hioff[e >> b0] + (e & lomask)]);
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
-        if (df_tile_apply<kThreads, B>(sm, N, op_at(g), base)) __syncthreads();
+        auto&& op = op_at(g);
+        if (op.kind == OP_PRUN) {
+            df_phase_run<kThreads, B>(sm, tab, N, b, op, op_at, g, base);
+            g += op.cls;  // the run's payload records
+            __syncthreads();
+        } else if (df_tile_apply<kThreads, B>(sm, N, op, base)) {
+            __syncthreads();
+        }
     }
     for (uint32_t e = threadIdx.x; e < N; e += kThreads) psi[base + hioff[e >> b0] + (e & lomask)] = df_store(sm[e]);
 }
@@ -52,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_df(double2* __restrict__ psi,
                                                       TilePass P) {
     psi += (uint64_t)blockIdx.y * P.inst_stride;
     ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride + P.op0;
-    tile_df_body<B>(psi, P, [&](int g) { return ops[g]; });
+    tile_df_body<B>(psi, P, [&](int g) -> const TileOpDF& { return ops[g]; });
 }
 
 template <int B>
@@ -106,7 +115,7 @@ void split_to_floats(double x, float& hi, float& lo) {
 
 cudaError_t launch_tile_df_params(qs_state* s, const TileOpDF* h_ops, const TilePass& P) {
     if (P.nops > kParamOps) return cudaErrorInvalidValue;
-    const size_t smem = tile_smem_bytes(s->dt, P.b) + ((size_t)8 << (P.b - P.b0));
+    const size_t smem = tile_pass_smem(s->dt, P.b, P.b0);
     static thread_local TileParamsDF L;
     L.P = P;
     L.P.op0 = 0;
@@ -124,7 +133,7 @@ cudaError_t launch_tile_df_params(qs_state* s, const TileOpDF* h_ops, const Tile
 int tile_df_param_ops() { return kParamOps; }
 
 cudaError_t launch_tile_df(qs_state* s, const void* d_ops, const TilePass& P, unsigned count) {
-    const size_t smem = tile_smem_bytes(s->dt, P.b) + ((size_t)8 << (P.b - P.b0));
+    const size_t smem = tile_pass_smem(s->dt, P.b, P.b0);
     switch (P.b) {
     case 12: return launch_df_ptr<12>(s, d_ops, P, count, smem);
     case 13: return launch_df_ptr<13>(s, d_ops, P, count, smem);

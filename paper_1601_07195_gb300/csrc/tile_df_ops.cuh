@@ -207,6 +207,89 @@ __device__ __forceinline__ void df_tile_pairs(float4* sm, uint32_t N, int cls, i
     }
 }
 
+// ---- fused phase runs (record layout in qs_internal.h) ------------------------
+
+// q * x for two complex DF values
+__device__ __forceinline__ float4 df_cmul_v(float4 q, float4 x) {
+    const dfl re = df_dot2(df_mul(q.x, q.y, x.x, x.y), df_mul(-q.z, -q.w, x.z, x.w));
+    const dfl im = df_dot2(df_mul(q.x, q.y, x.z, x.w), df_mul(q.z, q.w, x.x, x.y));
+    return make_float4(re.h, re.l, im.h, im.l);
+}
+__device__ __forceinline__ float4 df_slot(const TileOpDF& r, int f) {
+    return make_float4(r.c[4 * f], r.c[4 * f + 1], r.c[4 * f + 2], r.c[4 * f + 3]);
+}
+__device__ __forceinline__ int slot_qubit(const TileOpDF& r, int f) {
+    return f == 0 ? r.tb : f == 1 ? r.tq : f == 2 ? r.cb : r.cq;
+}
+
+// Applies the run whose header is record g.  Three steps, each ended by a
+// barrier (the caller's barrier ends the last):
+//   1. threads [0, 2^lob) form T_lo without C, the next 2^hib threads T_hi;
+//      the last warp forms C (a butterfly product of its lanes' outside
+//      factors, taken from lane 0);
+//   2. T_lo *= C;
+//   3. every amplitude with bit jb = 1 is multiplied by T_lo * T_hi.
+template <int THREADS, int B, class OpAt>
+__device__ __forceinline__ void df_phase_run(float4* sm, float4* tab, uint32_t N, int b, const TileOpDF& h,
+                                             OpAt op_at, int g, uint64_t base) {
+    const int jb = h.tb, n_out = h.cb, lob = h.cq, hib = b - lob;
+    const int tile_rec = (b + 3) >> 2;
+    const uint32_t nlo = 1u << lob, nhi = 1u << hib;
+    float4* tlo = tab;
+    float4* thi = tab + nlo;
+    float4* tc = tab + nlo + nhi;
+    const uint32_t t = threadIdx.x;
+    const float4 one = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (t < nlo) {
+        float4 v = one;
+        for (int k = 0; k < lob; ++k)
+            if ((t >> k) & 1u) v = df_cmul_v(df_slot(op_at(g + 1 + (k >> 2)), k & 3), v);
+        tlo[t] = v;
+    } else if (t < nlo + nhi) {
+        const uint32_t u = t - nlo;
+        float4 v = one;
+        for (int k = 0; k < hib; ++k)
+            if ((u >> k) & 1u) v = df_cmul_v(df_slot(op_at(g + 1 + ((lob + k) >> 2)), (lob + k) & 3), v);
+        thi[u] = v;
+    }
+    if (t >= THREADS - 32) {
+        const int lane = (int)(t & 31u);
+        float4 v = one;
+        for (int i = lane; i < n_out; i += 32) {
+            const TileOpDF& r = op_at(g + 1 + tile_rec + (i >> 2));
+            if ((base >> slot_qubit(r, i & 3)) & 1ull) v = df_cmul_v(df_slot(r, i & 3), v);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            float4 o;
+            o.x = __shfl_xor_sync(0xffffffffu, v.x, off);
+            o.y = __shfl_xor_sync(0xffffffffu, v.y, off);
+            o.z = __shfl_xor_sync(0xffffffffu, v.z, off);
+            o.w = __shfl_xor_sync(0xffffffffu, v.w, off);
+            v = df_cmul_v(o, v);
+        }
+        if (lane == 0) *tc = df_cmul_v(df_slot(h, 0), v);
+    }
+    __syncthreads();
+    if (t < nlo) tlo[t] = df_cmul_v(*tc, tlo[t]);
+    __syncthreads();
+    const uint32_t lmask = nlo - 1u;
+    if constexpr (B > 0 && (1 << (B - 1)) / THREADS >= 1) {
+        constexpr int ITEMS = (1 << (B - 1)) / THREADS;
+        const uint32_t e0 = insert_zero32(t, jb) | (1u << jb);
+#pragma unroll
+        for (int m = 0; m < ITEMS; ++m) {
+            const uint32_t e = e0 + insert_zero32((uint32_t)(m * THREADS), jb);
+            sm[e] = df_cmul_v(df_cmul_v(tlo[e & lmask], thi[e >> lob]), sm[e]);
+        }
+    } else {
+        for (uint32_t p = t; p < (N >> 1); p += THREADS) {
+            const uint32_t e = insert_zero32(p, jb) | (1u << jb);
+            sm[e] = df_cmul_v(df_cmul_v(tlo[e & lmask], thi[e >> lob]), sm[e]);
+        }
+    }
+}
+
 template <int THREADS, int B = 0>
 __device__ __forceinline__ bool df_tile_apply(float4* sm, uint32_t N, const TileOpDF& op, uint64_t base) {
     if (op.kind == OP_SWAP) {

@@ -172,6 +172,89 @@ __device__ __forceinline__ void tile_pairs(typename Amp<R>::T* sm, uint32_t N, i
 // Apply one op to the tile whose non-tile qubits are fixed by `base`.  Every
 // branch depends only on the op and on base, so it is uniform over the CTA.
 // Returns false when the op leaves this tile unchanged (no barrier needed).
+// ---- fused phase runs (record layout in qs_internal.h) ------------------------
+template <class T, class R>
+__device__ __forceinline__ T slot_value(const TileOp<R>& r, int f) {
+    T v;
+    v.x = r.m[2 * f];
+    v.y = r.m[2 * f + 1];
+    return v;
+}
+template <class R>
+__device__ __forceinline__ int slot_qubit(const TileOp<R>& r, int f) {
+    return f == 0 ? r.tb : f == 1 ? r.tq : f == 2 ? r.cb : r.cq;
+}
+template <class T>
+__device__ __forceinline__ T cmul_v(T q, T a) {
+    return cmul(q.x, q.y, a);
+}
+
+// The run whose header is record g; steps and barriers as in df_phase_run
+// (tile_df_ops.cuh): tables T_lo and T_hi and the per-tile constant C, then
+// T_lo *= C, then every amplitude with bit jb = 1 times T_lo * T_hi.  The
+// tables live in `tab`, 16 bytes per entry whatever the amplitude type.
+template <class R, int THREADS, int B, class OpAt>
+__device__ __forceinline__ void phase_run(typename Amp<R>::T* sm, void* tab_raw, uint32_t N, int b,
+                                          const TileOp<R>& h, OpAt op_at, int g, uint64_t base) {
+    using T = typename Amp<R>::T;
+    const int jb = h.tb, n_out = h.cb, lob = h.cq, hib = b - lob;
+    const int tile_rec = (b + 3) >> 2;
+    const uint32_t nlo = 1u << lob, nhi = 1u << hib;
+    T* tlo = reinterpret_cast<T*>(tab_raw);
+    T* thi = tlo + nlo;
+    T* tc = tlo + nlo + nhi;
+    const uint32_t t = threadIdx.x;
+    T one;
+    one.x = (R)1;
+    one.y = (R)0;
+    if (t < nlo) {
+        T v = one;
+        for (int k = 0; k < lob; ++k)
+            if ((t >> k) & 1u) v = cmul_v(slot_value<T>(op_at(g + 1 + (k >> 2)), k & 3), v);
+        tlo[t] = v;
+    } else if (t < nlo + nhi) {
+        const uint32_t u = t - nlo;
+        T v = one;
+        for (int k = 0; k < hib; ++k)
+            if ((u >> k) & 1u) v = cmul_v(slot_value<T>(op_at(g + 1 + ((lob + k) >> 2)), (lob + k) & 3), v);
+        thi[u] = v;
+    }
+    if (t >= THREADS - 32) {
+        const int lane = (int)(t & 31u);
+        T v = one;
+        for (int i = lane; i < n_out; i += 32) {
+            const TileOp<R>& r = op_at(g + 1 + tile_rec + (i >> 2));
+            if ((base >> slot_qubit(r, i & 3)) & 1ull) v = cmul_v(slot_value<T>(r, i & 3), v);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            T o;
+            o.x = __shfl_xor_sync(0xffffffffu, v.x, off);
+            o.y = __shfl_xor_sync(0xffffffffu, v.y, off);
+            v = cmul_v(o, v);
+        }
+        if (lane == 0) *tc = cmul_v(slot_value<T>(h, 0), v);
+    }
+    __syncthreads();
+    if (t < nlo) tlo[t] = cmul_v(*tc, tlo[t]);
+    __syncthreads();
+    const uint32_t lmask = nlo - 1u;
+    if constexpr (B > 0 && (1 << (B - 1)) / THREADS >= 1) {
+        constexpr int ITEMS = (1 << (B - 1)) / THREADS;
+        const uint32_t e0 = insert_zero32(t, jb) | (1u << jb);
+#pragma unroll
+        for (int m = 0; m < ITEMS; ++m) {
+            const uint32_t e = e0 + insert_zero32((uint32_t)(m * THREADS), jb);
+            sm[e] = cmul_v(cmul_v(tlo[e & lmask], thi[e >> lob]), sm[e]);
+        }
+    } else {
+        for (uint32_t p = t; p < (N >> 1); p += THREADS) {
+            const uint32_t e = insert_zero32(p, jb) | (1u << jb);
+            sm[e] = cmul_v(cmul_v(tlo[e & lmask], thi[e >> lob]), sm[e]);
+        }
+    }
+}
+
 template <class R, int THREADS, int B = 0>
 __device__ __forceinline__ bool tile_apply(typename Amp<R>::T* sm, uint32_t N, const TileOp<R>& op, uint64_t base) {
     if (op.kind == OP_SWAP) {

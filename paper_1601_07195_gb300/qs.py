@@ -18,6 +18,7 @@ QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EDTYPE = range(6)
 QS_G_U1, QS_G_CU, QS_G_SWAP, QS_G_RX, QS_G_RY, QS_G_RZ = range(6)
 QS_P_Z, QS_P_ZZ, QS_P_X = range(3)
 PLAN_DEFAULT, PLAN_NO_FUSION, PLAN_GRAPH, PLAN_ARITH_F64, PLAN_DRY_RUN, PLAN_NO_MERGE = 0, 1, 2, 4, 8, 16
+PLAN_NO_PHASE_RUNS = 32
 
 _STATUS = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EDTYPE"}
 
@@ -294,7 +295,8 @@ class Plan:
         return np.array(out[:n], dtype=np.float64)
 
     def op_counts(self, i):
-        """3x6 array: ops of pass i by (single-qubit, controlled, swap) x gate class."""
+        """3x6 array: ops of pass i by (single-qubit, controlled, swap) x gate class; a fused run of
+        phase gates counts as one single-qubit diagonal op."""
         buf = (ctypes.c_int * 18)()
         _check(load().qs_plan_pass_op_counts(self._h, i, buf))
         return np.array(buf[:], dtype=np.int64).reshape(3, 6)

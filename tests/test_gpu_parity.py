@@ -409,14 +409,14 @@ def test_single_qubit_fusion_matches_unfused_and_oracle(qs, dt):
     psi = rand_state(n, 77)
     want = O.run(expected_input(psi, dt), gates)
     outs = {}
-    for flags in (qs.PLAN_DEFAULT, qs.PLAN_NO_MERGE):
+    for flags in (qs.PLAN_DEFAULT, qs.PLAN_NO_MERGE | qs.PLAN_NO_PHASE_RUNS):
         with upload(qs, n, dt, psi) as s:
             p = s.plan(gates, flags=flags)
             outs[flags] = (p.stats()["device_ops"], None)
             p.execute()
             outs[flags] = (outs[flags][0], s.to_numpy())
             p.close()
-    assert outs[qs.PLAN_DEFAULT][0] < outs[qs.PLAN_NO_MERGE][0] == len(gates)
+    assert outs[qs.PLAN_DEFAULT][0] < outs[qs.PLAN_NO_MERGE | qs.PLAN_NO_PHASE_RUNS][0] == len(gates)
     for flags, (_, got) in outs.items():
         assert np.max(np.abs(got - want)) < 5 * TOL[dt]
     xx = G.concat([G.gate_u1(2, G.MAT_X), G.gate_u1(2, G.MAT_X), G.gate_cu(0, 5, G.MAT_X), G.gate_u1(9, G.MAT_X)])
@@ -427,3 +427,94 @@ def test_single_qubit_fusion_matches_unfused_and_oracle(qs, dt):
         got = s.to_numpy()
         p.close()
     assert np.array_equal(got, O.run(expected_input(psi, dt), xx).astype(got.dtype))
+
+
+def _phase_runs_circuit(n, seed, rounds=12):
+    """Mixing gates on a pivot qubit j, each followed by a run of phase gates that
+    all involve j: phase gates on j, controlled phases with j as control and as
+    target, CZ; the other qubit anywhere (inside or outside the tile), repeated."""
+    rng = G.SplitMix64(seed)
+    out = []
+    for _ in range(rounds):
+        j = rng.randint(n)
+        out.append(G.gate_u1(j, G.haar_2x2(rng)))
+        for _ in range(4 + rng.randint(20)):
+            k = rng.randint(n)
+            phi = rng.uniform_range(0.0, 2.0 * np.pi)
+            w = rng.randint(4)
+            if k == j or w == 0:
+                out.append(G.gate_u1(j, G.mat_cphase(phi)))
+            elif w == 1:
+                out.append(G.gate_cu(j, k, G.mat_cphase(phi)))
+            elif w == 2:
+                out.append(G.gate_cu(k, j, G.mat_cphase(phi)))
+            else:
+                out.append(G.gate_cu(k, j, (1.0, 0.0, 0.0, -1.0)))
+    return G.concat(out)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("tile_bits", [0, 5, 8, 10, 11, 12])
+def test_phase_runs_match_oracle_and_unfused_runs(qs, dt, tile_bits):
+    """Runs of phase gates around one qubit are applied as one table update per
+    tile; the state matches the oracle and the plan that applies them one by one,
+    with fewer kernel updates."""
+    n = 16
+    gates = G.concat([_phase_runs_circuit(n, 4040 + tile_bits), G.random_circuit(n, 200, 4141)[0],
+                      G.qft_circuit(n)])
+    psi = rand_state(n, 21)
+    want = O.run(expected_input(psi, dt), gates)
+    ops = {}
+    for flags in (qs.PLAN_DEFAULT, qs.PLAN_NO_PHASE_RUNS):
+        with upload(qs, n, dt, psi) as s:
+            p = s.plan(gates, flags=flags, tile_bits=tile_bits)
+            ops[flags] = p.stats()["device_ops"]
+            p.execute()
+            got = s.to_numpy()
+            p.close()
+        assert np.max(np.abs(got - want)) < 5 * TOL[dt], flags
+    assert ops[qs.PLAN_DEFAULT] < ops[qs.PLAN_NO_PHASE_RUNS]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n", [1, 2, 6, 9])
+def test_phase_runs_whole_state_tile(qs, dt, n):
+    """Tiles that cover the whole state (T_lo / T_hi over 0..n bits), runs of
+    single-qubit phase gates kept apart (no matrix merge)."""
+    rng = G.SplitMix64(90 + n)
+    out = [G.gate_u1(0, G.MAT_H)]
+    for _ in range(40):
+        j = rng.randint(n)
+        out.append(G.gate_u1(j, G.haar_2x2(rng)))
+        for _ in range(6):
+            k = rng.randint(n)
+            phi = rng.uniform_range(0.0, 2.0 * np.pi)
+            out.append(G.gate_u1(j, G.mat_cphase(phi)) if k == j else G.gate_cu(k, j, G.mat_cphase(phi)))
+    gates = G.concat(out)
+    psi = rand_state(n, 5)
+    want = O.run(expected_input(psi, dt), gates)
+    with upload(qs, n, dt, psi) as s:
+        p = s.plan(gates, flags=qs.PLAN_NO_MERGE)
+        assert p.stats()["device_ops"] < len(gates)
+        p.execute()
+        got = s.to_numpy()
+        p.close()
+    assert np.max(np.abs(got - want)) < 5 * TOL[dt]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("tile_bits", [0, 9, 13])
+def test_qft_closed_form_n20_phase_runs(qs, dt, tile_bits):
+    """The QFT's controlled-phase chains are fused runs; the state is the closed form."""
+    n = 20
+    x = G.random_basis(n, 8)
+    with qs.State.create(n, dt) as s:
+        s.init_basis(x)
+        p = s.plan(G.qft_circuit(n), tile_bits=tile_bits)
+        counts = sum(p.op_counts(i) for i in range(p.stats()["passes"]))
+        p.execute()
+        got = s.to_numpy()
+        p.close()
+    assert counts[1][3] < n * (n - 1) // 2  # most controlled phases went into runs
+    want = O.qft_basis_amplitudes(n, x, np.arange(1 << n))
+    assert np.max(np.abs(got - want)) < TOL[dt]
