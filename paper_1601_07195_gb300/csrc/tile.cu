@@ -23,6 +23,10 @@ namespace {
 #define QS_TILE_THREADS 256
 #endif
 constexpr int kTileThreads = QS_TILE_THREADS;
+#ifndef QS_LOAD_BATCH
+#define QS_LOAD_BATCH 8
+#endif
+constexpr int kLoadBatch = QS_LOAD_BATCH;
 
 template <class R, int B = 0, class OpAt>
 __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, const TilePass& P, OpAt op_at) {
@@ -43,7 +47,24 @@ __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, 
     }
     __syncthreads();
     const uint32_t lomask = (1u << b0) - 1u;
-    for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) sm[e] = psi[base + hioff[e >> b0] + (e & lomask)];
+    if constexpr (B > 0 && kLoadBatch > 0 && (1 << B) >= kTileThreads) {
+        // fixed tile size: kLoadBatch global loads in flight per thread (tile_df.cu)
+        constexpr int PER = (1 << B) / kTileThreads;
+        constexpr int BATCH = PER < kLoadBatch ? PER : kLoadBatch;
+#pragma unroll
+        for (int u0 = 0; u0 < PER; u0 += BATCH) {
+            T v[BATCH];
+#pragma unroll
+            for (int k = 0; k < BATCH; ++k) {
+                const uint32_t e = threadIdx.x + (uint32_t)((u0 + k) * kTileThreads);
+                v[k] = psi[base + hioff[e >> b0] + (e & lomask)];
+            }
+#pragma unroll
+            for (int k = 0; k < BATCH; ++k) sm[threadIdx.x + (uint32_t)((u0 + k) * kTileThreads)] = v[k];
+        }
+    } else {
+        for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) sm[e] = psi[base + hioff[e >> b0] + (e & lomask)];
+    }
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
         auto&& op = op_at(g);

@@ -19,6 +19,10 @@ namespace {
 #define QS_TILE_DF_THREADS 256
 #endif
 constexpr int kThreads = QS_TILE_DF_THREADS;
+#ifndef QS_LOAD_BATCH
+#define QS_LOAD_BATCH 8
+#endif
+constexpr int kLoadBatch = QS_LOAD_BATCH;
 
 // The pass body; OpAt(g) yields op g of the pass.  B > 0: the tile has
 // exactly 2^B amplitudes and the fixed-size gate paths are used.
@@ -40,7 +44,25 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
     }
     __syncthreads();
     const uint32_t lomask = (1u << b0) - 1u;
-    for (uint32_t e = threadIdx.x; e < N; e += kThreads) sm[e] = df_load(psi[base + hioff[e >> b0] + (e & lomask)]);
+    if constexpr (B > 0 && kLoadBatch > 0 && (1 << B) >= kThreads) {
+        // fixed tile size: each thread issues kLoadBatch global loads before the
+        // first conversion, so one tile costs a few memory latencies, not 2^B / threads
+        constexpr int PER = (1 << B) / kThreads;
+        constexpr int BATCH = PER < kLoadBatch ? PER : kLoadBatch;
+#pragma unroll
+        for (int u0 = 0; u0 < PER; u0 += BATCH) {
+            double2 v[BATCH];
+#pragma unroll
+            for (int k = 0; k < BATCH; ++k) {
+                const uint32_t e = threadIdx.x + (uint32_t)((u0 + k) * kThreads);
+                v[k] = psi[base + hioff[e >> b0] + (e & lomask)];
+            }
+#pragma unroll
+            for (int k = 0; k < BATCH; ++k) sm[threadIdx.x + (uint32_t)((u0 + k) * kThreads)] = df_load(v[k]);
+        }
+    } else {
+        for (uint32_t e = threadIdx.x; e < N; e += kThreads) sm[e] = df_load(psi[base + hioff[e >> b0] + (e & lomask)]);
+    }
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
         auto&& op = op_at(g);
