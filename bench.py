@@ -84,15 +84,15 @@ def gate_class(g):
 # FP64 flops per amplitude the class's update touches (FMA = 2 flops)
 _FLOPS = {"general": 14.0, "real": 6.0, "diag": 6.0, "diag1": 6.0, "antidiag": 6.0, "perm": 0.0}
 # FP32 flops per touched amplitude of the double-float update (csrc/df.cuh):
-# df_mul = 1 FMUL + 3 FFMA = 7 flops; TwoSum = 6; dot2 = 2 df_mul + TwoSum + 2 adds + TwoSum = 28;
-# dot4 = 4 df_mul + 3 TwoSum + 6 adds + TwoSum = 58; a complex output = 2 dots.
-_DF_FLOPS = {"general": 116.0, "real": 56.0, "diag": 56.0, "diag1": 56.0, "antidiag": 56.0, "perm": 0.0}
+# df_mul = 1 FMUL + 3 FFMA = 7 flops; TwoSum = 6; dot2 = 2 df_mul + TwoSum + 2 adds = 22;
+# dot4 = 4 df_mul + 3 TwoSum + 6 adds = 52 (pairs stay unnormalised); a complex output = 2 dots.
+_DF_FLOPS = {"general": 104.0, "real": 44.0, "diag": 44.0, "diag1": 44.0, "antidiag": 44.0, "perm": 0.0}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 # DRAM bytes (read + write) of one double-float tile launch, from the ncu capture
 # of the n=26 case (profiles/k_tile_df_c128_n26_full.md); a tile pass reads and
 # writes the whole state once, so traffic scales with 2^n.  Update (or set to
 # None) whenever the kernel changes.
-DF_TILE_TRAFFIC_N26 = 1.074563e9 + 1.012196e9
+DF_TILE_TRAFFIC_N26 = 1.073861e9 + 1.012106e9
 
 
 def gate_cost(g, n, s, table=None):
@@ -388,8 +388,8 @@ def run_ours(args):
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; MEASURED_PEAKS.json "
                                "has no FP32 figure (an FFMA probe on this GPU measured 74.2 TFLOP/s)",
                 "flops_counted": ("FP32 flops of the double-float updates the kernel applies (after in-pass "
-                                  "fusion of same-qubit gates) per touched amplitude: general 116, "
-                                  "real/diagonal/anti-diagonal 56, permutation 0") if df else
+                                  "fusion of same-qubit gates) per touched amplitude: general 104, "
+                                  "real/diagonal/anti-diagonal 44, permutation 0; a fused phase run counts as one diagonal update") if df else
                                  "FP32 flops of the updates the kernel applies",
                 "fp64_equivalent_tflops": fp64_tf,
                 "fp64_equivalent_frac_of_fp64_peak": fp64_tf / FP64_PEAK_TFLOPS,

@@ -47,7 +47,7 @@ std::map<std::pair<int, int>, std::pair<int, int>> g_tune;
 
 void default_tile(qs_dtype dt, int n, int& b, int& b0) {
     if (dt == QS_C128) { b = 12; b0 = 4; }
-    else { b = 13; b0 = 5; }
+    else { b = 12; b0 = 4; }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find({(int)dt, n});
     if (it != g_tune.end()) { b = it->second.first; b0 = it->second.second; }

@@ -518,3 +518,81 @@ def test_qft_closed_form_n20_phase_runs(qs, dt, tile_bits):
     assert counts[1][3] < n * (n - 1) // 2  # most controlled phases went into runs
     want = O.qft_basis_amplitudes(n, x, np.arange(1 << n))
     assert np.max(np.abs(got - want)) < TOL[dt]
+
+
+def _hot_qubit_circuit(n, count, seed):
+    """Gates that stay on a few qubits for a while, mixed with swaps, controlled
+    gates whose control or target lies outside the tile, and diagonal gates on
+    qubits outside the tile."""
+    rng = G.SplitMix64(seed)
+    out = []
+    hot = [rng.randint(n) for _ in range(3)]
+    for i in range(count):
+        if i % 40 == 0:
+            hot = [rng.randint(n) for _ in range(3)]
+        a = hot[rng.randint(3)] if rng.randint(4) else rng.randint(n)
+        b = hot[rng.randint(3)] if rng.randint(4) else rng.randint(n)
+        w = rng.randint(7)
+        if w == 0:
+            out.append(G.gate_u1(a, G.haar_2x2(rng)))
+        elif w == 1:
+            out.append(G.gate_u1(a, G.MAT_H))
+        elif w == 2:
+            out.append(G.gate_u1(a, G.MAT_T if rng.randint(2) else G.MAT_X))
+        elif a != b and w == 3:
+            out.append(G.gate_cu(a, b, G.MAT_X))
+        elif a != b and w == 4:
+            out.append(G.gate_cu(a, b, G.mat_cphase(rng.uniform_range(0.0, 6.0))))
+        elif a != b and w == 5:
+            out.append(G.gate_swap(a, b))
+        elif a != b:
+            out.append(G.gate_cu(a, b, G.haar_2x2(rng)))
+        else:
+            out.append(G.gate_u1(a, (np.exp(0.4j), 0, 0, np.exp(-0.9j))))
+    return G.concat(out)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("tile_bits", [0, 3, 4, 7, 10, 12])
+def test_hot_qubit_circuits_match_oracle(qs, dt, tile_bits):
+    """Long stretches on three qubits with swaps, outside controls and outside
+    diagonal targets, planned with several tile shapes, with and without phase
+    runs, against the oracle."""
+    n = 15
+    gates = G.concat([_hot_qubit_circuit(n, 700, 1212 + tile_bits), G.random_circuit(n, 300, 1313)[0]])
+    psi = rand_state(n, 31)
+    want = O.run(expected_input(psi, dt), gates)
+    for flags in (qs.PLAN_DEFAULT, qs.PLAN_NO_PHASE_RUNS):
+        with upload(qs, n, dt, psi) as s:
+            p = s.plan(gates, flags=flags, tile_bits=tile_bits)
+            p.execute()
+            got = s.to_numpy()
+            p.close()
+        assert np.max(np.abs(got - want)) < 5 * TOL[dt], flags
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_hot_qubit_permutations_bit_exact(qs, dt):
+    """A moves-only circuit concentrated on few qubits (X, CNOT, SWAP) stays
+    bit-exact."""
+    n = 14
+    rng = G.SplitMix64(77)
+    out = []
+    for i in range(400):
+        hot = [(i // 50 + k) % n for k in (0, 3, 5)]
+        a, b = hot[rng.randint(3)], hot[rng.randint(3)]
+        r = rng.randint(3)
+        if r == 0 or a == b:
+            out.append(G.gate_u1(a, G.MAT_X))
+        elif r == 1:
+            out.append(G.gate_cu(a, b, G.MAT_X))
+        else:
+            out.append(G.gate_swap(a, b))
+    gates = G.concat(out)
+    rng2 = np.random.default_rng(3)
+    psi = rng2.uniform(0.5, 1, 1 << n) + 1j * rng2.uniform(0.5, 1, 1 << n)
+    want = O.run(expected_input(psi, dt), gates)
+    with upload(qs, n, dt, psi) as s:
+        s.run(gates)
+        got = s.to_numpy()
+    assert np.array_equal(got, want.astype(got.dtype))

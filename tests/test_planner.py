@@ -72,7 +72,7 @@ def test_plan_is_a_valid_reordering(case, dt, tile_bits):
     passes = p.passes()
     order = [g for ps in passes for g in ps["gates"]]
     assert sorted(order) == list(range(len(gates)))
-    b = tile_bits if tile_bits else (12 if dt == 1 else 13)
+    b = tile_bits if tile_bits else 12
     b = min(b, n)
     for ps in passes:
         if ps["kind"] == "tile":
@@ -123,13 +123,13 @@ def test_no_fusion_keeps_circuit_order():
 
 def test_tuning_table_roundtrip_and_planner_uses_it():
     from paper_1601_07195_gb300 import autotune as A
-    assert A.tune_get(qs.QS_C64, 17) == (13, 5)  # built-in default
+    assert A.tune_get(qs.QS_C64, 17) == (12, 4)  # built-in default
     A.tune_set(qs.QS_C64, 17, 9, 3)
     assert A.tune_get(qs.QS_C64, 17) == (9, 3)
     st = fake_state(17, qs.QS_C64)
     p = qs.Plan(st, G.random_circuit(17, 100, 2)[0], flags=qs.PLAN_DRY_RUN)
     assert all(bin(x["mask"]).count("1") == 9 for x in p.passes() if x["kind"] == "tile")
-    A.tune_set(qs.QS_C64, 17, 13, 5)
+    A.tune_set(qs.QS_C64, 17, 12, 4)
     with pytest.raises(qs.QSError):
         A.tune_set(qs.QS_C64, 17, 20, 3)
 
