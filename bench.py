@@ -429,16 +429,26 @@ def run_ours(args):
         state.copy_in_ptr(host.data_ptr(), 1 << n)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        parts = [0.0, 0.0, 0.0]  # each call below returns after its work is done
         for _ in range(e2e_steps):
+            ta = time.perf_counter()
             state.copy_in_ptr(host.data_ptr(), 1 << n)
+            tb = time.perf_counter()
             state.run(gates)
+            tc = time.perf_counter()
             res = state.marginals()
+            td = time.perf_counter()
+            parts[0] += tb - ta
+            parts[1] += tc - tb
+            parts[2] += td - tc
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         e2e_bytes = gate_bytes + 2 * N * s_bytes  # h2d of the state + marginals read (plus gates)
         e2e = {"value": world * e2e_bytes / e2e_s / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": int(N * s_bytes + gates.nbytes), "d2h_bytes_per_step": int(8 * n),
-               "ms_per_step": 1e3 * e2e_s, "steps": e2e_steps}
+               "ms_per_step": 1e3 * e2e_s, "steps": e2e_steps,
+               "breakdown_ms": {"h2d_state": 1e3 * parts[0] / e2e_steps, "qs_run": 1e3 * parts[1] / e2e_steps,
+                                "marginals_to_host": 1e3 * parts[2] / e2e_steps}}
         del host
 
     secondary = None
