@@ -596,3 +596,18 @@ def test_hot_qubit_permutations_bit_exact(qs, dt):
         s.run(gates)
         got = s.to_numpy()
     assert np.array_equal(got, want.astype(got.dtype))
+
+
+def test_small_tiles_many_waves_n22(qs):
+    """2^11-amplitude complex128 tiles at n = 22: 2048 tiles, several waves of
+    CTAs per pass, random circuit plus QFT against the oracle."""
+    n = 22
+    gates = G.concat([G.random_circuit(n, 400, 5150)[0], G.qft_circuit(n)])
+    psi = rand_state(n, 41)
+    want = O.run(psi.copy(), gates)
+    with upload(qs, n, 1, psi) as s:
+        p = s.plan(gates, tile_bits=11 | (4 << 8))
+        p.execute()
+        got = s.to_numpy()
+        p.close()
+    assert np.max(np.abs(got - want)) < TOL[1]
