@@ -33,7 +33,7 @@ struct PlanPass {
     TilePass tp;     // tile pass
     uint64_t mask;   // tile qubits (tile pass) or the gate's qubits
     int n_gates;
-    bool moves_only; // every gate is a permutation (X, CNOT, SWAP): run bit-exact on doubles
+    bool moves_only; // every gate is a permutation (X, CNOT, SWAP): exact moves of 16-byte values
     std::vector<int> members;  // circuit positions of the pass's gates, in execution order
     int op_counts[3][6];       // ops the kernel applies, by kind (1q, controlled, swap) and class
 };
@@ -355,6 +355,28 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
         }
         pp.tp.nops = (int)tops.size() - pp.tp.op0;
         p->passes.push_back(pp);
+    }
+    if (df) {
+        // Consecutive tile passes hand the state to each other as float pairs: in
+        // each run of tile passes, the first double-float pass splits the doubles
+        // it loads and the last one joins what it stores.  Moves-only passes in
+        // between move 16-byte values whatever they hold; single-gate passes
+        // need doubles and end a run.
+        size_t i = 0;
+        while (i < p->passes.size()) {
+            if (p->passes[i].kind != 1) { ++i; continue; }
+            size_t j = i;
+            std::vector<size_t> dfp;
+            for (; j < p->passes.size() && p->passes[j].kind == 1; ++j)
+                if (!p->passes[j].moves_only) dfp.push_back(j);
+            for (size_t k = 0; k < dfp.size(); ++k) {
+                int io = 0;
+                if (k > 0) io |= kIoPairsIn;
+                if (k + 1 < dfp.size()) io |= kIoPairsOut;
+                p->passes[dfp[k]].tp.io = io;
+            }
+            i = j;
+        }
     }
     if (upload) {
         if (qs_status st = upload_ops(tops, &p->d_ops)) return st;

@@ -96,8 +96,15 @@ struct TilePass {
     int32_t nops;
     uint64_t inst_stride;      // batched launches: amplitudes between instances (blockIdx.y)
     int32_t ops_stride;        // batched launches: op records between instances
-    int32_t pad;
+    int32_t io;                // double-float passes: kIoPairsIn / kIoPairsOut (state held as float pairs)
 };
+
+// Double-float tile passes of one plan may hand the state to each other as
+// float pairs (hi, lo) instead of rounded doubles: 16 bytes per amplitude
+// either way, so no extra HBM traffic, and the split at load and the join at
+// store happen once per run of such passes instead of once per pass.
+constexpr int kIoPairsIn = 1;   // the pass reads float pairs (no split)
+constexpr int kIoPairsOut = 2;  // the pass writes float pairs (no join)
 
 // One pass of a plan, before its ops are converted to device records.
 struct PassDesc {

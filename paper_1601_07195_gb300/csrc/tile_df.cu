@@ -44,6 +44,20 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
     }
     __syncthreads();
     const uint32_t lomask = (1u << b0) - 1u;
+    // kIoPairsIn: the previous pass left float pairs in place of the doubles
+    // (the same 16 bytes per amplitude), so the tile is taken without a split
+    const bool pairs_in = (P.io & kIoPairsIn) != 0;
+    auto to_tile = [&](double2 raw) -> float4 {
+        if (pairs_in) {
+            float4 v;
+            v.x = __int_as_float((int)(unsigned)__double_as_longlong(raw.x));
+            v.y = __int_as_float((int)(unsigned)((unsigned long long)__double_as_longlong(raw.x) >> 32));
+            v.z = __int_as_float((int)(unsigned)__double_as_longlong(raw.y));
+            v.w = __int_as_float((int)(unsigned)((unsigned long long)__double_as_longlong(raw.y) >> 32));
+            return v;
+        }
+        return df_load(raw);
+    };
     if constexpr (B > 0 && kLoadBatch > 0 && (1 << B) >= kThreads) {
         // fixed tile size: each thread issues kLoadBatch global loads before the
         // first conversion, so one tile costs a few memory latencies, not 2^B / threads
@@ -58,10 +72,10 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
                 v[k] = psi[base + hioff[e >> b0] + (e & lomask)];
             }
 #pragma unroll
-            for (int k = 0; k < BATCH; ++k) sm[threadIdx.x + (uint32_t)((u0 + k) * kThreads)] = df_load(v[k]);
+            for (int k = 0; k < BATCH; ++k) sm[threadIdx.x + (uint32_t)((u0 + k) * kThreads)] = to_tile(v[k]);
         }
     } else {
-        for (uint32_t e = threadIdx.x; e < N; e += kThreads) sm[e] = df_load(psi[base + hioff[e >> b0] + (e & lomask)]);
+        for (uint32_t e = threadIdx.x; e < N; e += kThreads) sm[e] = to_tile(psi[base + hioff[e >> b0] + (e & lomask)]);
     }
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
@@ -74,7 +88,19 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
             __syncthreads();
         }
     }
-    for (uint32_t e = threadIdx.x; e < N; e += kThreads) psi[base + hioff[e >> b0] + (e & lomask)] = df_store(sm[e]);
+    if (P.io & kIoPairsOut) {
+        // the next pass reads float pairs: renormalised here by TwoSum (exact),
+        // as the rounding to a double and the split would do, so that the low
+        // parts do not grow relative to the high parts over many passes
+        float4* dst = reinterpret_cast<float4*>(psi);
+        for (uint32_t e = threadIdx.x; e < N; e += kThreads) {
+            const float4 v = sm[e];
+            const dfl r = two_sum(v.x, v.y), i = two_sum(v.z, v.w);
+            dst[base + hioff[e >> b0] + (e & lomask)] = make_float4(r.h, r.l, i.h, i.l);
+        }
+    } else {
+        for (uint32_t e = threadIdx.x; e < N; e += kThreads) psi[base + hioff[e >> b0] + (e & lomask)] = df_store(sm[e]);
+    }
 }
 
 // ops in device memory (batched launches: one op array per instance)

@@ -611,3 +611,25 @@ def test_small_tiles_many_waves_n22(qs):
         got = s.to_numpy()
         p.close()
     assert np.max(np.abs(got - want)) < TOL[1]
+
+
+def test_c128_norm_drift_over_many_passes(qs):
+    """QFT, 3000 random gates and their inverse at n = 22: 110 tile passes that
+    hand the state to each other as float pairs.  A unitary circuit keeps the
+    norm at 1; the drift stays at the level of the double-float rounding
+    (about 1e-12), which an unrenormalised hand-off exceeds 100-fold."""
+    n = 22
+    x = G.random_basis(n, G.SEEDS["qft30"])
+    r, _ = G.random_circuit(n, 3000, G.SEEDS["qft30"])
+    gates = G.concat([G.qft_circuit(n), r, G.inverse_circuit(r)])
+    with qs.State.create(n, 1) as s:
+        s.init_basis(x)
+        p = s.plan(gates)
+        assert p.stats()["passes"] > 100
+        p.execute()
+        nrm = s.norm()
+        got = s.to_numpy()
+        p.close()
+    assert abs(nrm - 1.0) < 1e-11
+    want = O.qft_basis_amplitudes(n, x, np.arange(1 << n))
+    assert np.max(np.abs(got - want)) < TOL[1]
