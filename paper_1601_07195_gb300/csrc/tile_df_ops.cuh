@@ -65,25 +65,36 @@ __device__ __forceinline__ void df_tile_1q_body(float4* sm, uint32_t half, int t
 // per-thread base index per op plus per-step offsets that are uniform over the
 // CTA (compile-time m, per-op tb) leave almost no integer work per pair, and
 // the fully unrolled steps expose independent pairs to the scheduler.
+#ifndef QS_DF_ILP
+#define QS_DF_ILP 2
+#endif
+// independent pairs loaded before any is computed, per step of the fixed paths
+constexpr int kDfIlp = QS_DF_ILP;
+
 template <int CLS, int THREADS, int B>
 __device__ __forceinline__ void df_tile_1q_fixed(float4* sm, int tb, const float* c) {
     constexpr int PAIRS = (1 << (B - 1)) / THREADS;
     static_assert(PAIRS >= 2 && PAIRS % 2 == 0, "tile too small for the fixed path");
+    constexpr int STEP = (PAIRS % kDfIlp == 0) ? kDfIlp : 2;
     float4* s0 = sm + insert_zero32(threadIdx.x, tb);
     float4* s1 = s0 + (1u << tb);
 #pragma unroll
-    for (int m = 0; m < PAIRS; m += 2) {
-        const uint32_t d0 = insert_zero32((uint32_t)(m * THREADS), tb);
-        const uint32_t d1 = insert_zero32((uint32_t)((m + 1) * THREADS), tb);
-        float4 a, b, x, y;
-        if (CLS != GC_DIAG1) { a = s0[d0]; x = s0[d1]; }
-        b = s1[d0];
-        y = s1[d1];
-        df_pair_update<CLS>(c, a, b);
-        df_pair_update<CLS>(c, x, y);
-        if (CLS != GC_DIAG1) { s0[d0] = a; s0[d1] = x; }
-        s1[d0] = b;
-        s1[d1] = y;
+    for (int m = 0; m < PAIRS; m += STEP) {
+        uint32_t d[STEP];
+        float4 a[STEP], b[STEP];
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) {
+            d[u] = insert_zero32((uint32_t)((m + u) * THREADS), tb);
+            if (CLS != GC_DIAG1) a[u] = s0[d[u]];
+            b[u] = s1[d[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) df_pair_update<CLS>(c, a[u], b[u]);
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) {
+            if (CLS != GC_DIAG1) s0[d[u]] = a[u];
+            s1[d[u]] = b[u];
+        }
     }
 }
 
@@ -91,22 +102,27 @@ template <int CLS, int THREADS, int B>
 __device__ __forceinline__ void df_tile_cu_fixed(float4* sm, int cb, int tb, const float* c) {
     constexpr int ITEMS = (1 << (B - 2)) / THREADS;
     static_assert(ITEMS >= 2 && ITEMS % 2 == 0, "tile too small for the fixed path");
+    constexpr int STEP = (ITEMS % kDfIlp == 0) ? kDfIlp : 2;
     const int lo = min(cb, tb), hi = max(cb, tb);
     float4* s0 = sm + (insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb));
     float4* s1 = s0 + (1u << tb);
 #pragma unroll
-    for (int m = 0; m < ITEMS; m += 2) {
-        const uint32_t d0 = insert_two_zeros32((uint32_t)(m * THREADS), lo, hi);
-        const uint32_t d1 = insert_two_zeros32((uint32_t)((m + 1) * THREADS), lo, hi);
-        float4 a, b, x, y;
-        if (CLS != GC_DIAG1) { a = s0[d0]; x = s0[d1]; }
-        b = s1[d0];
-        y = s1[d1];
-        df_pair_update<CLS>(c, a, b);
-        df_pair_update<CLS>(c, x, y);
-        if (CLS != GC_DIAG1) { s0[d0] = a; s0[d1] = x; }
-        s1[d0] = b;
-        s1[d1] = y;
+    for (int m = 0; m < ITEMS; m += STEP) {
+        uint32_t d[STEP];
+        float4 a[STEP], b[STEP];
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) {
+            d[u] = insert_two_zeros32((uint32_t)((m + u) * THREADS), lo, hi);
+            if (CLS != GC_DIAG1) a[u] = s0[d[u]];
+            b[u] = s1[d[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) df_pair_update<CLS>(c, a[u], b[u]);
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) {
+            if (CLS != GC_DIAG1) s0[d[u]] = a[u];
+            s1[d[u]] = b[u];
+        }
     }
 }
 
