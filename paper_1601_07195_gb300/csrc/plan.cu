@@ -15,6 +15,7 @@
 // circuit order, so the plan computes the same ordered product (up to
 // rounding) as applying the gates one at a time.
 #include <algorithm>
+#include <utility>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -25,7 +26,8 @@
 namespace qs {
 namespace {
 
-constexpr int kWindow = 512;  // gates scanned ahead when filling a pass
+constexpr int kWindow = 512;     // gates scanned ahead when filling a pass
+constexpr int kSearchRounds = 4; // local-search rounds over the tile set of a pass
 
 struct PlanPass {
     int kind;        // 0 = single gate, 1 = tile pass
@@ -449,28 +451,61 @@ qs_status plan_passes(int n, const std::vector<Op>& ops, int b, int b0, bool fus
             }
         }
         if (fuse && mem.empty()) {
-            uint64_t blocked_all = 0, blocked_nd = 0;
-            int scanned = 0;
-            for (size_t j = first; j < ops.size() && scanned < kWindow; ++j) {
-                if (taken[j]) continue;
-                ++scanned;
-                const Op& o = ops[j];
-                const uint64_t sup = (1ull << o.t) | (o.c >= 0 ? (1ull << o.c) : 0ull);
-                const bool diag = op_is_diagonal(o);
-                const bool movable = diag ? !(sup & blocked_nd) : !(sup & blocked_all);
-                if (movable) {
-                    const uint64_t need = o.kind == OP_SWAP ? sup : (diag ? 0ull : (1ull << o.t));
-                    if (popc(T | need) <= b) {
-                        T |= need;
-                        mem.push_back((int)j);
-                        taken[j] = 1;
-                        continue;
+            // One greedy scan from tile set T0: gates join while their mixing
+            // qubits fit b tile bits, pulled ahead only over gates they commute with.
+            auto scan = [&](uint64_t T0, std::vector<int>& m) -> uint64_t {
+                uint64_t Ts = T0, blocked_all = 0, blocked_nd = 0;
+                int scanned = 0;
+                m.clear();
+                for (size_t j = first; j < ops.size() && scanned < kWindow; ++j) {
+                    if (taken[j]) continue;
+                    ++scanned;
+                    const Op& o = ops[j];
+                    const uint64_t sup = (1ull << o.t) | (o.c >= 0 ? (1ull << o.c) : 0ull);
+                    const bool diag = op_is_diagonal(o);
+                    const bool movable = diag ? !(sup & blocked_nd) : !(sup & blocked_all);
+                    if (movable) {
+                        const uint64_t need = o.kind == OP_SWAP ? sup : (diag ? 0ull : (1ull << o.t));
+                        if (popc(Ts | need) <= b) {
+                            Ts |= need;
+                            m.push_back((int)j);
+                            continue;
+                        }
+                    }
+                    blocked_all |= sup;
+                    if (!diag) blocked_nd |= sup;
+                    if ((blocked_nd & all) == all) break;
+                }
+                return Ts;
+            };
+            T = scan(T, mem);
+            // Local search over tile sets: exchanging one chosen qubit for one
+            // left out can let more gates into the pass (the greedy takes
+            // qubits in first-come order).  Each round keeps the best exchange;
+            // fewer passes mean fewer HBM round trips for the same gates.
+            const uint64_t low = (1ull << b0) - 1ull;
+            std::vector<int> cand_mem;
+            for (int round = 0; round < kSearchRounds && n > b; ++round) {
+                const uint64_t base_T = T;
+                uint64_t best_T = T;
+                std::vector<int> best_mem;
+                for (int q_out = b0; q_out < n; ++q_out) {
+                    if (!((base_T >> q_out) & 1ull)) continue;
+                    for (int q_in = b0; q_in < n; ++q_in) {
+                        if ((base_T >> q_in) & 1ull) continue;
+                        const uint64_t Tc = ((base_T & ~(1ull << q_out)) | (1ull << q_in)) | low;
+                        const uint64_t Tr = scan(Tc, cand_mem);
+                        if (cand_mem.size() > std::max(mem.size(), best_mem.size())) {
+                            best_mem.swap(cand_mem);
+                            best_T = Tr;
+                        }
                     }
                 }
-                blocked_all |= sup;
-                if (!diag) blocked_nd |= sup;
-                if ((blocked_nd & all) == all) break;
+                if (best_mem.empty()) break;
+                mem.swap(best_mem);
+                T = best_T;
             }
+            for (int j : mem) taken[j] = 1;
         }
         if (mem.empty()) return fail(QS_EINVAL, "planner made no progress");  // unreachable: the first gate always fits
         while (first < ops.size() && taken[first]) ++first;
