@@ -144,6 +144,18 @@ __device__ __forceinline__ float4 df_rmul2(const float* c, int p, float4 a, int 
     return make_float4(re.h, re.l, im.h, im.l);
 }
 
+// balanced real gate: q * (a + s b) for real DF constant q = double j and s = +-1
+// (a and b complex DF values): the sum is exact (TwoSum), then one product
+__device__ __forceinline__ dfl df_addsig(float ah, float al, float s, float bh, float bl) {
+    const dfl t = two_sum(ah, s * bh);  // s * bh is exact
+    return {t.h, t.l + fmaf(s, bl, al)};
+}
+__device__ __forceinline__ float4 df_bal(const float* c, int j, float s, float4 a, float4 b) {
+    const dfl tr = df_addsig(a.x, a.y, s, b.x, b.y), ti = df_addsig(a.z, a.w, s, b.z, b.w);
+    const dfl re = df_mul(QH(j), QL(j), tr.h, tr.l), im = df_mul(QH(j), QL(j), ti.h, ti.l);
+    return make_float4(re.h, re.l, im.h, im.l);
+}
+
 #undef QH
 #undef QL
 

@@ -15,6 +15,7 @@
 // circuit order, so the plan computes the same ordered product (up to
 // rounding) as applying the gates one at a time.
 #include <algorithm>
+#include <cmath>
 #include <utility>
 #include <cstring>
 #include <map>
@@ -107,6 +108,14 @@ template <> TileOpDF to_tile_op<TileOpDF>(const Op& o, const int* bit_of) {
     TileOpDF t{};
     fill_common(t, o, bit_of);
     for (int j = 0; j < 8; ++j) split_to_floats(o.m[j], t.c[2 * j], t.c[2 * j + 1]);
+    // a real gate whose entries share one magnitude (H, HX, XH, ZH, ...):
+    // a' = q11 (a + s1 b), b' = q21 (a + s3 b) with s1 = q12/q11, s3 = q22/q21 = +-1
+    if (o.kind != OP_SWAP && o.cls == GC_REAL && o.m[0] != 0.0 && o.m[4] != 0.0 &&
+        std::fabs(o.m[0]) == std::fabs(o.m[2]) && std::fabs(o.m[4]) == std::fabs(o.m[6])) {
+        t.cls = GC_REAL_BAL;
+        t.c[2] = (o.m[2] == o.m[0]) ? 1.0f : -1.0f;
+        t.c[10] = (o.m[6] == o.m[4]) ? 1.0f : -1.0f;
+    }
     return t;
 }
 

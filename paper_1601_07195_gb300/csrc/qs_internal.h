@@ -19,7 +19,11 @@ enum GateClass : int {
     GC_DIAG = 2,      // q12 = q21 = 0 (RZ)
     GC_DIAG1 = 3,     // q12 = q21 = 0 and q11 = 1 exactly (T, phase): only |1> amplitudes change
     GC_ANTIDIAG = 4,  // q11 = q22 = 0
-    GC_PERM = 5       // exactly [[0,1],[1,0]] (X): a move
+    GC_PERM = 5,      // exactly [[0,1],[1,0]] (X): a move
+    // internal to double-float tile records (counted as GC_REAL): a real gate
+    // whose four entries have one magnitude (H and its products with X and Z);
+    // the record holds q11 and q21 and the signs s1 = q12/q11, s3 = q22/q21
+    GC_REAL_BAL = 6
 };
 
 // Operation kinds after lowering the gate records.  OP_PRUN and OP_PDATA occur

@@ -19,6 +19,10 @@ __device__ __forceinline__ void df_pair_update(const float* c, float4& a, float4
         const float4 a2 = df_rmul2(c, 0, a, 2, b);
         const float4 b2 = df_rmul2(c, 4, a, 6, b);
         a = a2; b = b2;
+    } else if constexpr (CLS == GC_REAL_BAL) {  // signs in the unused imaginary slots c[2], c[10]
+        const float4 a2 = df_bal(c, 0, c[2], a, b);
+        const float4 b2 = df_bal(c, 4, c[10], a, b);
+        a = a2; b = b2;
     } else if constexpr (CLS == GC_DIAG) {
         a = df_cmul(c, 0, 1, a);
         b = df_cmul(c, 6, 7, b);
@@ -206,6 +210,7 @@ __device__ __forceinline__ void df_tile_pairs(float4* sm, uint32_t N, int cls, i
         switch (cls) {
         case GC_GENERAL: df_tile_1q_any<GC_GENERAL, THREADS, B>(sm, N, tb, c); break;
         case GC_REAL: df_tile_1q_any<GC_REAL, THREADS, B>(sm, N, tb, c); break;
+        case GC_REAL_BAL: df_tile_1q_any<GC_REAL_BAL, THREADS, B>(sm, N, tb, c); break;
         case GC_DIAG: df_tile_1q_any<GC_DIAG, THREADS, B>(sm, N, tb, c); break;
         case GC_DIAG1: df_tile_1q_any<GC_DIAG1, THREADS, B>(sm, N, tb, c); break;
         case GC_ANTIDIAG: df_tile_1q_any<GC_ANTIDIAG, THREADS, B>(sm, N, tb, c); break;
@@ -215,6 +220,7 @@ __device__ __forceinline__ void df_tile_pairs(float4* sm, uint32_t N, int cls, i
         switch (cls) {
         case GC_GENERAL: df_tile_cu_any<GC_GENERAL, THREADS, B>(sm, N, cb, tb, c); break;
         case GC_REAL: df_tile_cu_any<GC_REAL, THREADS, B>(sm, N, cb, tb, c); break;
+        case GC_REAL_BAL: df_tile_cu_any<GC_REAL_BAL, THREADS, B>(sm, N, cb, tb, c); break;
         case GC_DIAG: df_tile_cu_any<GC_DIAG, THREADS, B>(sm, N, cb, tb, c); break;
         case GC_DIAG1: df_tile_cu_any<GC_DIAG1, THREADS, B>(sm, N, cb, tb, c); break;
         case GC_ANTIDIAG: df_tile_cu_any<GC_ANTIDIAG, THREADS, B>(sm, N, cb, tb, c); break;
