@@ -633,3 +633,41 @@ def test_c128_norm_drift_over_many_passes(qs):
     assert abs(nrm - 1.0) < 1e-11
     want = O.qft_basis_amplitudes(n, x, np.arange(1 << n))
     assert np.max(np.abs(got - want)) < TOL[1]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_special_phase_and_balanced_gates_in_tiles(qs, dt):
+    """Real gates with entries of one magnitude (H, HX, XH, ZH) take a dedicated
+    path in the double-float tile kernel; with phases that are multiples of
+    pi/4 (S, S^dagger, Z, T, T^dagger, T^3, CZ, controlled S and T) kept apart
+    (no merge, no phase runs), on tile bits and with controls inside and
+    outside the tile, they match the oracle."""
+    n = 14
+    w = np.exp(1j * np.pi / 4)
+    phases = [1j, -1j, -1.0, w, np.conj(w), w ** 3, -w, w ** 5]
+    r2 = 1 / np.sqrt(2)
+    bal = [(r2, r2, r2, -r2), (r2, r2, -r2, r2), (r2, -r2, r2, r2), (-r2, r2, r2, r2)]
+    rng = G.SplitMix64(4242)
+    out = []
+    for _ in range(300):
+        a = rng.randint(n)
+        b = (a + 1 + rng.randint(n - 1)) % n
+        k = rng.randint(4)
+        if k == 0:
+            out.append(G.gate_u1(a, (1, 0, 0, phases[rng.randint(len(phases))])))
+        elif k == 1:
+            out.append(G.gate_cu(b, a, (1, 0, 0, phases[rng.randint(len(phases))])))
+        elif k == 2:
+            out.append(G.gate_u1(a, bal[rng.randint(len(bal))]))
+        else:
+            out.append(G.gate_u1(a, G.haar_2x2(rng)))
+    gates = G.concat(out)
+    psi = rand_state(n, 17)
+    want = O.run(expected_input(psi, dt), gates)
+    for tile_bits in (0, 9):
+        with upload(qs, n, dt, psi) as s:
+            p = s.plan(gates, flags=qs.PLAN_NO_MERGE | qs.PLAN_NO_PHASE_RUNS, tile_bits=tile_bits)
+            p.execute()
+            got = s.to_numpy()
+            p.close()
+        assert np.max(np.abs(got - want)) < 5 * TOL[dt], tile_bits
