@@ -22,6 +22,7 @@
 // All launches (and the upload of the gate matrices for the current angles)
 // are captured once into a CUDA graph and replayed by qs_batch_execute.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -321,10 +322,43 @@ __global__ void __launch_bounds__(kAdjThreads) k_tile_adj(typename Tr::G* __rest
     }
     __syncthreads();
     const uint32_t lomask = (1u << b0) - 1u;
-    for (uint32_t e = threadIdx.x; e < N; e += kAdjThreads) {
-        const uint64_t g = base + hioff[e >> b0] + (e & lomask);
-        f[e] = Tr::load(phi[g]);
-        l[e] = Tr::load(lam[g]);
+    constexpr bool kDF = std::is_same<E, float4>::value;
+    // double-float: consecutive reverse passes hand phi and lambda over as float
+    // pairs (kIoPairsIn / kIoPairsOut), the last one does not store them at all
+    const bool pairs_in = kDF && (P.io & kIoPairsIn);
+    auto take = [&](typename Tr::G raw) -> E {
+        if constexpr (kDF) {
+            if (pairs_in) return *reinterpret_cast<const E*>(&raw);
+        }
+        return Tr::load(raw);
+    };
+    if constexpr (B > 0 && (1 << B) >= kAdjThreads) {
+        // fixed tile size: four amplitudes of each state in flight per thread
+        constexpr int PER = (1 << B) / kAdjThreads;
+        constexpr int BATCH = PER < 4 ? PER : 4;
+#pragma unroll
+        for (int u0 = 0; u0 < PER; u0 += BATCH) {
+            typename Tr::G vf[BATCH], vl[BATCH];
+#pragma unroll
+            for (int k = 0; k < BATCH; ++k) {
+                const uint32_t e = threadIdx.x + (uint32_t)((u0 + k) * kAdjThreads);
+                const uint64_t g = base + hioff[e >> b0] + (e & lomask);
+                vf[k] = phi[g];
+                vl[k] = lam[g];
+            }
+#pragma unroll
+            for (int k = 0; k < BATCH; ++k) {
+                const uint32_t e = threadIdx.x + (uint32_t)((u0 + k) * kAdjThreads);
+                f[e] = take(vf[k]);
+                l[e] = take(vl[k]);
+            }
+        }
+    } else {
+        for (uint32_t e = threadIdx.x; e < N; e += kAdjThreads) {
+            const uint64_t g = base + hioff[e >> b0] + (e & lomask);
+            f[e] = take(phi[g]);
+            l[e] = take(lam[g]);
+        }
     }
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
@@ -332,10 +366,22 @@ __global__ void __launch_bounds__(kAdjThreads) k_tile_adj(typename Tr::G* __rest
         adj_apply<Tr, kAdjThreads, B, true>(f, l, N, op, base, red, wslots);
         __syncthreads();
     }
-    for (uint32_t e = threadIdx.x; e < N; e += kAdjThreads) {
-        const uint64_t g = base + hioff[e >> b0] + (e & lomask);
-        phi[g] = Tr::store(f[e]);
-        lam[g] = Tr::store(l[e]);
+    if (!(P.io & kIoDiscard)) {
+        for (uint32_t e = threadIdx.x; e < N; e += kAdjThreads) {
+            const uint64_t g = base + hioff[e >> b0] + (e & lomask);
+            if constexpr (kDF) {
+                if (P.io & kIoPairsOut) {  // renormalised by TwoSum, as in the forward passes
+                    const E a = f[e], c = l[e];
+                    const dfl ar = two_sum(a.x, a.y), ai = two_sum(a.z, a.w);
+                    const dfl cr = two_sum(c.x, c.y), ci = two_sum(c.z, c.w);
+                    reinterpret_cast<E*>(phi)[g] = make_float4(ar.h, ar.l, ai.h, ai.l);
+                    reinterpret_cast<E*>(lam)[g] = make_float4(cr.h, cr.l, ci.h, ci.l);
+                    continue;
+                }
+            }
+            phi[g] = Tr::store(f[e]);
+            lam[g] = Tr::store(l[e]);
+        }
     }
     // rotation partials: the warps' sums in fixed order (slots this pass does not use are never read)
     for (int sl = threadIdx.x; sl < n_slots; sl += kAdjThreads) {
@@ -745,12 +791,17 @@ qs_status record(qs_batch* bt) {
         sv.data = g.phi;
         sv.stream = st;
         size_t op0 = 0;
-        for (const PassDesc& d : g.fwd) {
+        const bool df = std::is_same<OpT, TileOpDF>::value;
+        for (size_t fi = 0; fi < g.fwd.size(); ++fi) {
+            const PassDesc& d = g.fwd[fi];
             TilePass tp = d.tp;
             tp.op0 = (int)op0;
             tp.nops = (int)d.members.size();
             tp.inst_stride = N;
             tp.ops_stride = (int)g.fwd_per;
+            // double-float forward passes hand the state over as float pairs;
+            // the last one leaves doubles for lambda = H psi and the reverse sweep
+            tp.io = df ? ((fi > 0 ? kIoPairsIn : 0) | (fi + 1 < g.fwd.size() ? kIoPairsOut : 0)) : 0;
             if (qs_status s = launch_tile_pass(&sv, bt->d_stage + g.st_fwd.off, tp, false, count)) return s;
             op0 += d.members.size();
         }
@@ -773,6 +824,9 @@ qs_status record(qs_batch* bt) {
             tp.nops = (int)d.members.size();
             tp.inst_stride = N;
             tp.ops_stride = (int)g.rev_per;
+            // phi and lambda pass from one reverse pass to the next as float pairs
+            // (double-float); after the last pass nothing reads them
+            tp.io = (df && pi > 0 ? kIoPairsIn : 0) | (pi + 1 < g.rev.size() ? (df ? kIoPairsOut : 0) : kIoDiscard);
             const unsigned tiles = (unsigned)(1ull << (g.n - tp.b));
             const OpT* rops = reinterpret_cast<const OpT*>(bt->d_stage + g.st_rev.off);
             const dim3 grid(tiles, count);

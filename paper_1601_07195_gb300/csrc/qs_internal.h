@@ -109,6 +109,7 @@ struct TilePass {
 // store happen once per run of such passes instead of once per pass.
 constexpr int kIoPairsIn = 1;   // the pass reads float pairs (no split)
 constexpr int kIoPairsOut = 2;  // the pass writes float pairs (no join)
+constexpr int kIoDiscard = 4;   // reverse adjoint passes: the states are not read again, no store
 
 // One pass of a plan, before its ops are converted to device records.
 struct PassDesc {
