@@ -92,7 +92,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x F
 # of the n=26 case (profiles/k_tile_df_c128_n26_full.md); a tile pass reads and
 # writes the whole state once, so traffic scales with 2^n.  Update (or set to
 # None) whenever the kernel changes.
-DF_TILE_TRAFFIC_N26 = 1.073906e9 + 1.012158e9
+DF_TILE_TRAFFIC_N26 = 1.074417e9 + 1.012082e9
 
 
 def gate_cost(g, n, s, table=None):
