@@ -29,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -140,7 +141,9 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples go to a temporary file (QS_CLOCK_DIR overrides the directory);
+        # the JSON line carries their summary
+        self.path = os.path.join(os.environ.get("QS_CLOCK_DIR", tempfile.gettempdir()), f"qs_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
