@@ -64,25 +64,36 @@ __device__ __forceinline__ void tile_cu(typename Amp<R>::T* sm, uint32_t N, int 
 // Fixed-size tiles (2^B amplitudes): one per-thread base index per op plus
 // offsets uniform over the CTA (insert_zero is additive over the disjoint bits
 // of t < THREADS and m * THREADS), fully unrolled.
+#ifndef QS_TILE_ILP
+#define QS_TILE_ILP 2
+#endif
+// independent pairs loaded before any is computed, per step of the fixed paths
+constexpr int kTileIlp = QS_TILE_ILP;
+
 template <class R, int CLS, int THREADS, int B>
 __device__ __forceinline__ void tile_1q_fixed(typename Amp<R>::T* sm, int tb, const R* m) {
     using T = typename Amp<R>::T;
     constexpr int PAIRS = (1 << (B - 1)) / THREADS;
+    constexpr int STEP = (PAIRS % kTileIlp == 0) ? kTileIlp : 2;
     T* s0 = sm + insert_zero32(threadIdx.x, tb);
     T* s1 = s0 + (1u << tb);
 #pragma unroll
-    for (int k = 0; k < PAIRS; k += 2) {
-        const uint32_t d0 = insert_zero32((uint32_t)(k * THREADS), tb);
-        const uint32_t d1 = insert_zero32((uint32_t)((k + 1) * THREADS), tb);
-        T a, b, x, y;
-        if (CLS != GC_DIAG1) { a = s0[d0]; x = s0[d1]; }
-        b = s1[d0];
-        y = s1[d1];
-        pair_update<CLS>(m, a, b);
-        pair_update<CLS>(m, x, y);
-        if (CLS != GC_DIAG1) { s0[d0] = a; s0[d1] = x; }
-        s1[d0] = b;
-        s1[d1] = y;
+    for (int k = 0; k < PAIRS; k += STEP) {
+        uint32_t d[STEP];
+        T a[STEP], b[STEP];
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) {
+            d[u] = insert_zero32((uint32_t)((k + u) * THREADS), tb);
+            if (CLS != GC_DIAG1) a[u] = s0[d[u]];
+            b[u] = s1[d[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) pair_update<CLS>(m, a[u], b[u]);
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) {
+            if (CLS != GC_DIAG1) s0[d[u]] = a[u];
+            s1[d[u]] = b[u];
+        }
     }
 }
 
@@ -90,22 +101,27 @@ template <class R, int CLS, int THREADS, int B>
 __device__ __forceinline__ void tile_cu_fixed(typename Amp<R>::T* sm, int cb, int tb, const R* m) {
     using T = typename Amp<R>::T;
     constexpr int ITEMS = (1 << (B - 2)) / THREADS;
+    constexpr int STEP = (ITEMS % kTileIlp == 0) ? kTileIlp : 2;
     const int lo = min(cb, tb), hi = max(cb, tb);
     T* s0 = sm + (insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb));
     T* s1 = s0 + (1u << tb);
 #pragma unroll
-    for (int k = 0; k < ITEMS; k += 2) {
-        const uint32_t d0 = insert_two_zeros32((uint32_t)(k * THREADS), lo, hi);
-        const uint32_t d1 = insert_two_zeros32((uint32_t)((k + 1) * THREADS), lo, hi);
-        T a, b, x, y;
-        if (CLS != GC_DIAG1) { a = s0[d0]; x = s0[d1]; }
-        b = s1[d0];
-        y = s1[d1];
-        pair_update<CLS>(m, a, b);
-        pair_update<CLS>(m, x, y);
-        if (CLS != GC_DIAG1) { s0[d0] = a; s0[d1] = x; }
-        s1[d0] = b;
-        s1[d1] = y;
+    for (int k = 0; k < ITEMS; k += STEP) {
+        uint32_t d[STEP];
+        T a[STEP], b[STEP];
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) {
+            d[u] = insert_two_zeros32((uint32_t)((k + u) * THREADS), lo, hi);
+            if (CLS != GC_DIAG1) a[u] = s0[d[u]];
+            b[u] = s1[d[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) pair_update<CLS>(m, a[u], b[u]);
+#pragma unroll
+        for (int u = 0; u < STEP; ++u) {
+            if (CLS != GC_DIAG1) s0[d[u]] = a[u];
+            s1[d[u]] = b[u];
+        }
     }
 }
 
