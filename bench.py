@@ -94,6 +94,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x F
 # writes the whole state once, so traffic scales with 2^n.  Update (or set to
 # None) whenever the kernel changes.
 DF_TILE_TRAFFIC_N26 = 1.074417e9 + 1.012082e9
+# the same for the complex64 tile kernel, one n=27 launch (profiles/k_tile_c64_n27_full.md)
+C64_TILE_TRAFFIC_N27 = 1.073863e9 + 1.012055e9
 
 
 def gate_cost(g, n, s, table=None):
@@ -382,12 +384,15 @@ def run_ours(args):
     table = _DF_FLOPS if df else _FLOPS
     fp32_flops = sum(kernel_flops(plan.op_counts(i), n, table) for i in tile_idx)
     achieved_tf = fp32_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
-    roofline = {"bound": "alu", "kernel": "k_tile_df (fused tile pass, double-float)" if df else "k_tile<float>",
+    roofline = {"bound": "alu", "kernel": "k_tile_df (fused tile pass, double-float)" if df else "k_tile_p<float, 12> (fused tile pass, FP32)",
                 "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / FP32_PEAK_TFLOPS,
-                "traffic": (DF_TILE_TRAFFIC_N26 * 2.0 ** (n - 26)) if (df and DF_TILE_TRAFFIC_N26) else None,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one n=26 launch, "
-                                  "scaled by 2^(n-26)" if df else None,
+                "traffic": (DF_TILE_TRAFFIC_N26 * 2.0 ** (n - 26)) if (df and DF_TILE_TRAFFIC_N26) else
+                           ((C64_TILE_TRAFFIC_N27 * 2.0 ** (n - 27)) if (not df and C64_TILE_TRAFFIC_N27) else None),
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one n=26 launch, "
+                                   "scaled by 2^(n-26)") if df else
+                                  ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one n=27 launch, "
+                                   "scaled by 2^(n-27)"),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; MEASURED_PEAKS.json "
                                "has no FP32 figure (an FFMA probe on this GPU measured 74.2 TFLOP/s)",
                 "flops_counted": ("FP32 flops of the double-float updates the kernel applies (after in-pass "
