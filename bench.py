@@ -401,6 +401,10 @@ def run_ours(args):
                                  "FP32 flops of the updates the kernel applies",
                 "fp64_equivalent_tflops": fp64_tf,
                 "fp64_equivalent_frac_of_fp64_peak": fp64_tf / FP64_PEAK_TFLOPS,
+                "limiter": ("instruction issue: double-float FP32 arithmetic plus SMEM sweeps and index work "
+                            "(profiles/k_tile_df_c128_n26_full.md)") if df else
+                           ("shared-memory bandwidth: 92% of peak SMEM wavefronts "
+                            "(profiles/k_tile_c64_n27_full.md)"),
                 "launches_per_step": len(tile_idx), "avg_launch_ms": tile_launch_ms,
                 "hbm_frac_of_measured": (2 * N * s_bytes / (tile_launch_ms / 1e3)) / 6794.8e9 if tile_idx else None}
 
