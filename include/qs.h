@@ -164,7 +164,12 @@ enum {
 QS_API qs_status qs_plan_create(qs_state* s, const qs_gate* gates, int n_gates, const double* theta, int n_params,
                          int flags, int tile_bits, qs_plan** out);
 
-/* Launch the plan on the state's stream (asynchronous). */
+/* Launch the plan on the state's stream (asynchronous).  For complex128 in
+ * double-float arithmetic, consecutive tile passes hand the state to each
+ * other as float pairs (hi, lo), the same 16 bytes per amplitude, so while the
+ * plan runs the state's memory may hold that form; it holds IEEE complex128
+ * again when the plan's last pass has completed.  Work on other streams must
+ * not read the state in between. */
 QS_API qs_status qs_plan_execute(qs_plan* p);
 
 /* Plan statistics: number of passes over the state, of which tile passes,
