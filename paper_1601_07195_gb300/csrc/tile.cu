@@ -11,6 +11,7 @@
 // and controls outside the tile are a per-tile predicate.  One pass therefore
 // reads and writes the state once for the whole run of gates.
 #include <cstring>
+#include <type_traits>
 
 #include "device.cuh"
 #include "tile_ops.cuh"
@@ -31,6 +32,8 @@ constexpr int kLoadBatch = QS_LOAD_BATCH;
 template <class R, int B = 0, class OpAt>
 __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, const TilePass& P, OpAt op_at) {
     using T = typename Amp<R>::T;
+    // complex64 tiles use the bank-spreading layout (tile_ops.cuh)
+    using L = typename std::conditional<std::is_same<R, float>::value, SwizzledLayout, FlatLayout>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     const int b = P.b, b0 = P.b0, nh = b - b0;
@@ -60,23 +63,23 @@ __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, 
                 v[k] = psi[base + hioff[e >> b0] + (e & lomask)];
             }
 #pragma unroll
-            for (int k = 0; k < BATCH; ++k) sm[threadIdx.x + (uint32_t)((u0 + k) * kTileThreads)] = v[k];
+            for (int k = 0; k < BATCH; ++k) sm[L::at(threadIdx.x + (uint32_t)((u0 + k) * kTileThreads))] = v[k];
         }
     } else {
-        for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) sm[e] = psi[base + hioff[e >> b0] + (e & lomask)];
+        for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) sm[L::at(e)] = psi[base + hioff[e >> b0] + (e & lomask)];
     }
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
         auto&& op = op_at(g);
         if (op.kind == OP_PRUN) {
-            phase_run<R, kTileThreads, B>(sm, tab, N, b, op, op_at, g, base);
+            phase_run<R, kTileThreads, B, L>(sm, tab, N, b, op, op_at, g, base);
             g += op.cls;  // the run's payload records
             __syncthreads();
-        } else if (tile_apply<R, kTileThreads, B>(sm, N, op, base)) {
+        } else if (tile_apply<R, kTileThreads, B, L>(sm, N, op, base)) {
             __syncthreads();
         }
     }
-    for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) psi[base + hioff[e >> b0] + (e & lomask)] = sm[e];
+    for (uint32_t e = threadIdx.x; e < N; e += kTileThreads) psi[base + hioff[e >> b0] + (e & lomask)] = sm[L::at(e)];
 }
 
 // ops in device memory (batched launches: one op array per instance)

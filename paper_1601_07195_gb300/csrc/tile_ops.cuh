@@ -10,9 +10,25 @@
 
 namespace qs {
 
+// Shared-memory layout of a tile: amplitude e of the tile sits at L::at(e).
+struct FlatLayout {
+    static __device__ __forceinline__ uint32_t at(uint32_t e) { return e; }
+};
+// complex64 tiles (8-byte amplitudes, 32 four-byte banks): the partners of a
+// gate on tile bit t <= 3 are 1..8 elements apart, so a warp's 32 lanes would
+// hit half of the banks and a 64-bit access would take four wavefronts instead
+// of two.  Storing amplitude e at e ^ (15 * bit4(e)) spreads them over all
+// banks (every single-qubit gate and most controlled ones back to two).  The
+// per-step offsets of the fixed-size loops (multiples of the CTA size with
+// zeros inserted) leave bits 0..4 alone, so there L::at(base + d) =
+// L::at(base) + d and the swizzle costs nothing per access.
+struct SwizzledLayout {
+    static __device__ __forceinline__ uint32_t at(uint32_t e) { return e ^ ((0u - ((e >> 4) & 1u)) & 15u); }
+};
+
 // Two pairs per step (p and p + THREADS), both loaded before either is
 // updated, so the two updates are independent instruction chains.
-template <class R, int CLS, int THREADS>
+template <class R, int CLS, int THREADS, class L = FlatLayout>
 __device__ __forceinline__ void tile_1q(typename Amp<R>::T* sm, uint32_t N, int tb, const R* m) {
     using T = typename Amp<R>::T;
     const uint32_t half = N >> 1;
@@ -22,21 +38,21 @@ __device__ __forceinline__ void tile_1q(typename Amp<R>::T* sm, uint32_t N, int 
         const uint32_t i0 = insert_zero32(p, tb), i1 = i0 | (1u << tb);
         const uint32_t j0 = insert_zero32(two ? q : p, tb), j1 = j0 | (1u << tb);
         T a, b, x, y;
-        if (CLS != GC_DIAG1) { a = sm[i0]; x = sm[j0]; }
-        b = sm[i1];
-        y = sm[j1];
+        if (CLS != GC_DIAG1) { a = sm[L::at(i0)]; x = sm[L::at(j0)]; }
+        b = sm[L::at(i1)];
+        y = sm[L::at(j1)];
         pair_update<CLS>(m, a, b);
         pair_update<CLS>(m, x, y);
-        if (CLS != GC_DIAG1) sm[i0] = a;
-        sm[i1] = b;
+        if (CLS != GC_DIAG1) sm[L::at(i0)] = a;
+        sm[L::at(i1)] = b;
         if (two) {
-            if (CLS != GC_DIAG1) sm[j0] = x;
-            sm[j1] = y;
+            if (CLS != GC_DIAG1) sm[L::at(j0)] = x;
+            sm[L::at(j1)] = y;
         }
     }
 }
 
-template <class R, int CLS, int THREADS>
+template <class R, int CLS, int THREADS, class L = FlatLayout>
 __device__ __forceinline__ void tile_cu(typename Amp<R>::T* sm, uint32_t N, int cb, int tb, const R* m) {
     using T = typename Amp<R>::T;
     const int lo = min(cb, tb), hi = max(cb, tb);
@@ -47,16 +63,16 @@ __device__ __forceinline__ void tile_cu(typename Amp<R>::T* sm, uint32_t N, int 
         const uint32_t i0 = insert_two_zeros32(p, lo, hi) | (1u << cb), i1 = i0 | (1u << tb);
         const uint32_t j0 = insert_two_zeros32(two ? q : p, lo, hi) | (1u << cb), j1 = j0 | (1u << tb);
         T a, b, x, y;
-        if (CLS != GC_DIAG1) { a = sm[i0]; x = sm[j0]; }
-        b = sm[i1];
-        y = sm[j1];
+        if (CLS != GC_DIAG1) { a = sm[L::at(i0)]; x = sm[L::at(j0)]; }
+        b = sm[L::at(i1)];
+        y = sm[L::at(j1)];
         pair_update<CLS>(m, a, b);
         pair_update<CLS>(m, x, y);
-        if (CLS != GC_DIAG1) sm[i0] = a;
-        sm[i1] = b;
+        if (CLS != GC_DIAG1) sm[L::at(i0)] = a;
+        sm[L::at(i1)] = b;
         if (two) {
-            if (CLS != GC_DIAG1) sm[j0] = x;
-            sm[j1] = y;
+            if (CLS != GC_DIAG1) sm[L::at(j0)] = x;
+            sm[L::at(j1)] = y;
         }
     }
 }
@@ -70,13 +86,15 @@ __device__ __forceinline__ void tile_cu(typename Amp<R>::T* sm, uint32_t N, int 
 // independent pairs loaded before any is computed, per step of the fixed paths
 constexpr int kTileIlp = QS_TILE_ILP;
 
-template <class R, int CLS, int THREADS, int B>
+template <class R, int CLS, int THREADS, int B, class L = FlatLayout>
 __device__ __forceinline__ void tile_1q_fixed(typename Amp<R>::T* sm, int tb, const R* m) {
     using T = typename Amp<R>::T;
+    static_assert(THREADS % 32 == 0, "step offsets must leave bits 0..4 alone");
     constexpr int PAIRS = (1 << (B - 1)) / THREADS;
     constexpr int STEP = (PAIRS % kTileIlp == 0) ? kTileIlp : 2;
-    T* s0 = sm + insert_zero32(threadIdx.x, tb);
-    T* s1 = s0 + (1u << tb);
+    const uint32_t e0 = insert_zero32(threadIdx.x, tb);
+    T* s0 = sm + L::at(e0);
+    T* s1 = sm + L::at(e0 | (1u << tb));
 #pragma unroll
     for (int k = 0; k < PAIRS; k += STEP) {
         uint32_t d[STEP];
@@ -97,14 +115,16 @@ __device__ __forceinline__ void tile_1q_fixed(typename Amp<R>::T* sm, int tb, co
     }
 }
 
-template <class R, int CLS, int THREADS, int B>
+template <class R, int CLS, int THREADS, int B, class L = FlatLayout>
 __device__ __forceinline__ void tile_cu_fixed(typename Amp<R>::T* sm, int cb, int tb, const R* m) {
     using T = typename Amp<R>::T;
+    static_assert(THREADS % 32 == 0, "step offsets must leave bits 0..4 alone");
     constexpr int ITEMS = (1 << (B - 2)) / THREADS;
     constexpr int STEP = (ITEMS % kTileIlp == 0) ? kTileIlp : 2;
     const int lo = min(cb, tb), hi = max(cb, tb);
-    T* s0 = sm + (insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb));
-    T* s1 = s0 + (1u << tb);
+    const uint32_t e0 = insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb);
+    T* s0 = sm + L::at(e0);
+    T* s1 = sm + L::at(e0 | (1u << tb));
 #pragma unroll
     for (int k = 0; k < ITEMS; k += STEP) {
         uint32_t d[STEP];
@@ -125,62 +145,63 @@ __device__ __forceinline__ void tile_cu_fixed(typename Amp<R>::T* sm, int cb, in
     }
 }
 
-template <class R, int CLS, int THREADS, int B>
+template <class R, int CLS, int THREADS, int B, class L = FlatLayout>
 __device__ __forceinline__ void tile_1q_any(typename Amp<R>::T* sm, uint32_t N, int tb, const R* m) {
-    if constexpr (B > 0 && (1 << (B - 1)) / THREADS >= 2) tile_1q_fixed<R, CLS, THREADS, B>(sm, tb, m);
-    else tile_1q<R, CLS, THREADS>(sm, N, tb, m);
+    if constexpr (B > 0 && (1 << (B - 1)) / THREADS >= 2) tile_1q_fixed<R, CLS, THREADS, B, L>(sm, tb, m);
+    else tile_1q<R, CLS, THREADS, L>(sm, N, tb, m);
 }
-template <class R, int CLS, int THREADS, int B>
+template <class R, int CLS, int THREADS, int B, class L = FlatLayout>
 __device__ __forceinline__ void tile_cu_any(typename Amp<R>::T* sm, uint32_t N, int cb, int tb, const R* m) {
-    if constexpr (B > 0 && (1 << (B - 2)) / THREADS >= 2) tile_cu_fixed<R, CLS, THREADS, B>(sm, cb, tb, m);
-    else tile_cu<R, CLS, THREADS>(sm, N, cb, tb, m);
+    if constexpr (B > 0 && (1 << (B - 2)) / THREADS >= 2) tile_cu_fixed<R, CLS, THREADS, B, L>(sm, cb, tb, m);
+    else tile_cu<R, CLS, THREADS, L>(sm, N, cb, tb, m);
 }
 
 // Multiply the tile (or, with cb >= 0, the half whose tile bit cb is 1) by f.
-template <class R, int THREADS>
+template <class R, int THREADS, class L = FlatLayout>
 __device__ __forceinline__ void tile_scale(typename Amp<R>::T* sm, uint32_t N, R fr, R fi, int cb) {
     if (cb < 0) {
-        for (uint32_t e = threadIdx.x; e < N; e += THREADS) sm[e] = cmul(fr, fi, sm[e]);
+        for (uint32_t e = threadIdx.x; e < N; e += THREADS) sm[L::at(e)] = cmul(fr, fi, sm[L::at(e)]);
     } else {
         for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
-            const uint32_t e = insert_zero32(p, cb) | (1u << cb);
+            const uint32_t e = L::at(insert_zero32(p, cb) | (1u << cb));
             sm[e] = cmul(fr, fi, sm[e]);
         }
     }
 }
 
-template <class R, int THREADS>
+template <class R, int THREADS, class L = FlatLayout>
 __device__ __forceinline__ void tile_swap(typename Amp<R>::T* sm, uint32_t N, int ab, int bb) {
     using T = typename Amp<R>::T;
     const int lo = min(ab, bb), hi = max(ab, bb);
     for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
         const uint32_t i = insert_two_zeros32(p, lo, hi);
-        const T x = sm[i | (1u << ab)];
-        sm[i | (1u << ab)] = sm[i | (1u << bb)];
-        sm[i | (1u << bb)] = x;
+        const uint32_t ia = L::at(i | (1u << ab)), ib = L::at(i | (1u << bb));
+        const T x = sm[ia];
+        sm[ia] = sm[ib];
+        sm[ib] = x;
     }
 }
 
 // B > 0: the tile has exactly 2^B amplitudes (fixed-size paths); B = 0: any size.
-template <class R, int THREADS, int B = 0>
+template <class R, int THREADS, int B = 0, class L = FlatLayout>
 __device__ __forceinline__ void tile_pairs(typename Amp<R>::T* sm, uint32_t N, int cls, int cb, int tb, const R* m) {
     if (cb < 0) {
         switch (cls) {
-        case GC_GENERAL: tile_1q_any<R, GC_GENERAL, THREADS, B>(sm, N, tb, m); break;
-        case GC_REAL: tile_1q_any<R, GC_REAL, THREADS, B>(sm, N, tb, m); break;
-        case GC_DIAG: tile_1q_any<R, GC_DIAG, THREADS, B>(sm, N, tb, m); break;
-        case GC_DIAG1: tile_1q_any<R, GC_DIAG1, THREADS, B>(sm, N, tb, m); break;
-        case GC_ANTIDIAG: tile_1q_any<R, GC_ANTIDIAG, THREADS, B>(sm, N, tb, m); break;
-        default: tile_1q_any<R, GC_PERM, THREADS, B>(sm, N, tb, m); break;
+        case GC_GENERAL: tile_1q_any<R, GC_GENERAL, THREADS, B, L>(sm, N, tb, m); break;
+        case GC_REAL: tile_1q_any<R, GC_REAL, THREADS, B, L>(sm, N, tb, m); break;
+        case GC_DIAG: tile_1q_any<R, GC_DIAG, THREADS, B, L>(sm, N, tb, m); break;
+        case GC_DIAG1: tile_1q_any<R, GC_DIAG1, THREADS, B, L>(sm, N, tb, m); break;
+        case GC_ANTIDIAG: tile_1q_any<R, GC_ANTIDIAG, THREADS, B, L>(sm, N, tb, m); break;
+        default: tile_1q_any<R, GC_PERM, THREADS, B, L>(sm, N, tb, m); break;
         }
     } else {
         switch (cls) {
-        case GC_GENERAL: tile_cu_any<R, GC_GENERAL, THREADS, B>(sm, N, cb, tb, m); break;
-        case GC_REAL: tile_cu_any<R, GC_REAL, THREADS, B>(sm, N, cb, tb, m); break;
-        case GC_DIAG: tile_cu_any<R, GC_DIAG, THREADS, B>(sm, N, cb, tb, m); break;
-        case GC_DIAG1: tile_cu_any<R, GC_DIAG1, THREADS, B>(sm, N, cb, tb, m); break;
-        case GC_ANTIDIAG: tile_cu_any<R, GC_ANTIDIAG, THREADS, B>(sm, N, cb, tb, m); break;
-        default: tile_cu_any<R, GC_PERM, THREADS, B>(sm, N, cb, tb, m); break;
+        case GC_GENERAL: tile_cu_any<R, GC_GENERAL, THREADS, B, L>(sm, N, cb, tb, m); break;
+        case GC_REAL: tile_cu_any<R, GC_REAL, THREADS, B, L>(sm, N, cb, tb, m); break;
+        case GC_DIAG: tile_cu_any<R, GC_DIAG, THREADS, B, L>(sm, N, cb, tb, m); break;
+        case GC_DIAG1: tile_cu_any<R, GC_DIAG1, THREADS, B, L>(sm, N, cb, tb, m); break;
+        case GC_ANTIDIAG: tile_cu_any<R, GC_ANTIDIAG, THREADS, B, L>(sm, N, cb, tb, m); break;
+        default: tile_cu_any<R, GC_PERM, THREADS, B, L>(sm, N, cb, tb, m); break;
         }
     }
 }
@@ -209,7 +230,7 @@ __device__ __forceinline__ T cmul_v(T q, T a) {
 // (tile_df_ops.cuh): tables T_lo and T_hi and the per-tile constant C, then
 // T_lo *= C, then every amplitude with bit jb = 1 times T_lo * T_hi.  The
 // tables live in `tab`, 16 bytes per entry whatever the amplitude type.
-template <class R, int THREADS, int B, class OpAt>
+template <class R, int THREADS, int B, class L, class OpAt>
 __device__ __forceinline__ void phase_run(typename Amp<R>::T* sm, void* tab_raw, uint32_t N, int b,
                                           const TileOp<R>& h, OpAt op_at, int g, uint64_t base) {
     using T = typename Amp<R>::T;
@@ -257,24 +278,25 @@ __device__ __forceinline__ void phase_run(typename Amp<R>::T* sm, void* tab_raw,
     const uint32_t lmask = nlo - 1u;
     if constexpr (B > 0 && (1 << (B - 1)) / THREADS >= 1) {
         constexpr int ITEMS = (1 << (B - 1)) / THREADS;
-        const uint32_t e0 = insert_zero32(t, jb) | (1u << jb);
+        const uint32_t e0 = insert_zero32(t, jb) | (1u << jb), s0 = L::at(e0);
 #pragma unroll
         for (int m = 0; m < ITEMS; ++m) {
-            const uint32_t e = e0 + insert_zero32((uint32_t)(m * THREADS), jb);
-            sm[e] = cmul_v(cmul_v(tlo[e & lmask], thi[e >> lob]), sm[e]);
+            const uint32_t d = insert_zero32((uint32_t)(m * THREADS), jb);
+            const uint32_t e = e0 + d;  // tables by tile index, the amplitude by its SMEM place
+            sm[s0 + d] = cmul_v(cmul_v(tlo[e & lmask], thi[e >> lob]), sm[s0 + d]);
         }
     } else {
         for (uint32_t p = t; p < (N >> 1); p += THREADS) {
-            const uint32_t e = insert_zero32(p, jb) | (1u << jb);
-            sm[e] = cmul_v(cmul_v(tlo[e & lmask], thi[e >> lob]), sm[e]);
+            const uint32_t e = insert_zero32(p, jb) | (1u << jb), se = L::at(e);
+            sm[se] = cmul_v(cmul_v(tlo[e & lmask], thi[e >> lob]), sm[se]);
         }
     }
 }
 
-template <class R, int THREADS, int B = 0>
+template <class R, int THREADS, int B = 0, class L = FlatLayout>
 __device__ __forceinline__ bool tile_apply(typename Amp<R>::T* sm, uint32_t N, const TileOp<R>& op, uint64_t base) {
     if (op.kind == OP_SWAP) {
-        tile_swap<R, THREADS>(sm, N, op.tb, op.cb);
+        tile_swap<R, THREADS, L>(sm, N, op.tb, op.cb);
         return true;
     }
     int cb = -1;
@@ -288,10 +310,10 @@ __device__ __forceinline__ bool tile_apply(typename Amp<R>::T* sm, uint32_t N, c
     if (op.tb < 0) {  // diagonal gate whose target is not a tile bit: one factor for the (half-)tile
         const bool bit = (base >> op.tq) & 1ull;
         if (op.cls == GC_DIAG1 && !bit) return false;
-        tile_scale<R, THREADS>(sm, N, bit ? op.m[6] : op.m[0], bit ? op.m[7] : op.m[1], cb);
+        tile_scale<R, THREADS, L>(sm, N, bit ? op.m[6] : op.m[0], bit ? op.m[7] : op.m[1], cb);
         return true;
     }
-    tile_pairs<R, THREADS, B>(sm, N, op.cls, cb, op.tb, op.m);
+    tile_pairs<R, THREADS, B, L>(sm, N, op.cls, cb, op.tb, op.m);
     return true;
 }
 
