@@ -47,6 +47,28 @@ __device__ __forceinline__ uint64_t deposit_bits(uint64_t v, uint64_t mask) {
     return out;
 }
 
+// Shared-memory layout of a tile: amplitude e of the tile sits at L::at(e).
+struct FlatLayout {
+    static __device__ __forceinline__ uint32_t at(uint32_t e) { return e; }
+};
+// complex64 tiles (8-byte amplitudes, 32 four-byte banks): the partners of a
+// gate on tile bit t <= 3 are 1..8 elements apart, so a warp's 32 lanes would
+// hit half of the banks and a 64-bit access would take four wavefronts instead
+// of two.  Storing amplitude e at e ^ (15 * bit4(e)) spreads them over all
+// banks (every single-qubit gate and most controlled ones back to two).  The
+// per-step offsets of the fixed-size loops (multiples of the CTA size with
+// zeros inserted) leave bits 0..4 alone, so there L::at(base + d) =
+// L::at(base) + d and the swizzle costs nothing per access.
+struct SwizzledLayout {
+    static __device__ __forceinline__ uint32_t at(uint32_t e) { return e ^ ((0u - ((e >> 4) & 1u)) & 15u); }
+};
+// The same for 16-byte amplitudes (complex128 as float pairs or doubles): the
+// bank period is 8 amplitudes, and e ^ (7 * bit3(e)) spreads the partners of
+// gates on tile bits 0..2; the fixed-size loops' offsets leave bits 0..3 alone.
+struct Swizzled16Layout {
+    static __device__ __forceinline__ uint32_t at(uint32_t e) { return e ^ ((0u - ((e >> 3) & 1u)) & 7u); }
+};
+
 // ---- complex products, written as FMA chains --------------------------------
 // q * a with q = (qr, qi)
 template <class T, class R>

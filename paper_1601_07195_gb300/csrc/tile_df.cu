@@ -7,6 +7,7 @@
 // contract and control/diagonal handling are those of tile.cu (Section 4.4,
 // Fig. 5, on a shared-memory tile over any qubit set).
 #include <cstring>
+#include <type_traits>
 
 #include "device.cuh"
 #include "df.cuh"
@@ -23,11 +24,17 @@ constexpr int kThreads = QS_TILE_DF_THREADS;
 #define QS_LOAD_BATCH 8
 #endif
 constexpr int kLoadBatch = QS_LOAD_BATCH;
+// shared-memory layout of the tile (device.cuh): bank-spreading for gates on tile bits 0..2
+#ifndef QS_DF_SWIZZLE
+#define QS_DF_SWIZZLE 1
+#endif
+using kDfLayout = std::conditional<QS_DF_SWIZZLE != 0, Swizzled16Layout, FlatLayout>::type;
 
 // The pass body; OpAt(g) yields op g of the pass.  B > 0: the tile has
 // exactly 2^B amplitudes and the fixed-size gate paths are used.
 template <int B = 0, class OpAt>
 __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const TilePass& P, OpAt op_at) {
+    using L = kDfLayout;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* sm = reinterpret_cast<float4*>(smem_raw);
     const int b = P.b, b0 = P.b0, nh = b - b0;
@@ -72,19 +79,19 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
                 v[k] = psi[base + hioff[e >> b0] + (e & lomask)];
             }
 #pragma unroll
-            for (int k = 0; k < BATCH; ++k) sm[threadIdx.x + (uint32_t)((u0 + k) * kThreads)] = to_tile(v[k]);
+            for (int k = 0; k < BATCH; ++k) sm[L::at(threadIdx.x + (uint32_t)((u0 + k) * kThreads))] = to_tile(v[k]);
         }
     } else {
-        for (uint32_t e = threadIdx.x; e < N; e += kThreads) sm[e] = to_tile(psi[base + hioff[e >> b0] + (e & lomask)]);
+        for (uint32_t e = threadIdx.x; e < N; e += kThreads) sm[L::at(e)] = to_tile(psi[base + hioff[e >> b0] + (e & lomask)]);
     }
     __syncthreads();
     for (int g = 0; g < P.nops; ++g) {
         auto&& op = op_at(g);
         if (op.kind == OP_PRUN) {
-            df_phase_run<kThreads, B>(sm, tab, N, b, op, op_at, g, base);
+            df_phase_run<kThreads, B, L>(sm, tab, N, b, op, op_at, g, base);
             g += op.cls;  // the run's payload records
             __syncthreads();
-        } else if (df_tile_apply<kThreads, B>(sm, N, op, base)) {
+        } else if (df_tile_apply<kThreads, B, L>(sm, N, op, base)) {
             __syncthreads();
         }
     }
@@ -94,12 +101,12 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
         // parts do not grow relative to the high parts over many passes
         float4* dst = reinterpret_cast<float4*>(psi);
         for (uint32_t e = threadIdx.x; e < N; e += kThreads) {
-            const float4 v = sm[e];
+            const float4 v = sm[L::at(e)];
             const dfl r = two_sum(v.x, v.y), i = two_sum(v.z, v.w);
             dst[base + hioff[e >> b0] + (e & lomask)] = make_float4(r.h, r.l, i.h, i.l);
         }
     } else {
-        for (uint32_t e = threadIdx.x; e < N; e += kThreads) psi[base + hioff[e >> b0] + (e & lomask)] = df_store(sm[e]);
+        for (uint32_t e = threadIdx.x; e < N; e += kThreads) psi[base + hioff[e >> b0] + (e & lomask)] = df_store(sm[L::at(e)]);
     }
 }
 

@@ -41,7 +41,7 @@ __device__ __forceinline__ void df_pair_update(const float* c, float4& a, float4
 // computing: the two double-float updates are independent chains the
 // scheduler can interleave.  GUARD is needed only when the pair count is not
 // a multiple of 2 * THREADS (tiles smaller than 4 * THREADS amplitudes).
-template <int CLS, int THREADS, bool GUARD>
+template <int CLS, int THREADS, bool GUARD, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_1q_body(float4* sm, uint32_t half, int tb, const float* c) {
     for (uint32_t p = threadIdx.x; p < half; p += 2 * THREADS) {
         const uint32_t q = p + THREADS;
@@ -49,16 +49,16 @@ __device__ __forceinline__ void df_tile_1q_body(float4* sm, uint32_t half, int t
         const uint32_t i0 = insert_zero32(p, tb), i1 = i0 | (1u << tb);
         const uint32_t j0 = insert_zero32(two ? q : p, tb), j1 = j0 | (1u << tb);
         float4 a, b, x, y;
-        if (CLS != GC_DIAG1) { a = sm[i0]; x = sm[j0]; }
-        b = sm[i1];
-        y = sm[j1];
+        if (CLS != GC_DIAG1) { a = sm[L::at(i0)]; x = sm[L::at(j0)]; }
+        b = sm[L::at(i1)];
+        y = sm[L::at(j1)];
         df_pair_update<CLS>(c, a, b);
         df_pair_update<CLS>(c, x, y);
-        if (CLS != GC_DIAG1) sm[i0] = a;
-        sm[i1] = b;
+        if (CLS != GC_DIAG1) sm[L::at(i0)] = a;
+        sm[L::at(i1)] = b;
         if (two) {
-            if (CLS != GC_DIAG1) sm[j0] = x;
-            sm[j1] = y;
+            if (CLS != GC_DIAG1) sm[L::at(j0)] = x;
+            sm[L::at(j1)] = y;
         }
     }
 }
@@ -75,13 +75,15 @@ __device__ __forceinline__ void df_tile_1q_body(float4* sm, uint32_t half, int t
 // independent pairs loaded before any is computed, per step of the fixed paths
 constexpr int kDfIlp = QS_DF_ILP;
 
-template <int CLS, int THREADS, int B>
+template <int CLS, int THREADS, int B, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_1q_fixed(float4* sm, int tb, const float* c) {
     constexpr int PAIRS = (1 << (B - 1)) / THREADS;
     static_assert(PAIRS >= 2 && PAIRS % 2 == 0, "tile too small for the fixed path");
+    static_assert(THREADS % 32 == 0, "step offsets must leave bits 0..4 alone");
     constexpr int STEP = (PAIRS % kDfIlp == 0) ? kDfIlp : 2;
-    float4* s0 = sm + insert_zero32(threadIdx.x, tb);
-    float4* s1 = s0 + (1u << tb);
+    const uint32_t e0 = insert_zero32(threadIdx.x, tb);
+    float4* s0 = sm + L::at(e0);
+    float4* s1 = sm + L::at(e0 | (1u << tb));
 #pragma unroll
     for (int m = 0; m < PAIRS; m += STEP) {
         uint32_t d[STEP];
@@ -102,14 +104,16 @@ __device__ __forceinline__ void df_tile_1q_fixed(float4* sm, int tb, const float
     }
 }
 
-template <int CLS, int THREADS, int B>
+template <int CLS, int THREADS, int B, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_cu_fixed(float4* sm, int cb, int tb, const float* c) {
     constexpr int ITEMS = (1 << (B - 2)) / THREADS;
     static_assert(ITEMS >= 2 && ITEMS % 2 == 0, "tile too small for the fixed path");
+    static_assert(THREADS % 32 == 0, "step offsets must leave bits 0..4 alone");
     constexpr int STEP = (ITEMS % kDfIlp == 0) ? kDfIlp : 2;
     const int lo = min(cb, tb), hi = max(cb, tb);
-    float4* s0 = sm + (insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb));
-    float4* s1 = s0 + (1u << tb);
+    const uint32_t e0 = insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb);
+    float4* s0 = sm + L::at(e0);
+    float4* s1 = sm + L::at(e0 | (1u << tb));
 #pragma unroll
     for (int m = 0; m < ITEMS; m += STEP) {
         uint32_t d[STEP];
@@ -130,14 +134,14 @@ __device__ __forceinline__ void df_tile_cu_fixed(float4* sm, int cb, int tb, con
     }
 }
 
-template <int CLS, int THREADS>
+template <int CLS, int THREADS, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_1q(float4* sm, uint32_t N, int tb, const float* c) {
     const uint32_t half = N >> 1;
-    if ((half & (2 * THREADS - 1)) == 0) df_tile_1q_body<CLS, THREADS, false>(sm, half, tb, c);
-    else df_tile_1q_body<CLS, THREADS, true>(sm, half, tb, c);
+    if ((half & (2 * THREADS - 1)) == 0) df_tile_1q_body<CLS, THREADS, false, L>(sm, half, tb, c);
+    else df_tile_1q_body<CLS, THREADS, true, L>(sm, half, tb, c);
 }
 
-template <int CLS, int THREADS, bool GUARD>
+template <int CLS, int THREADS, bool GUARD, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_cu_body(float4* sm, uint32_t quarter, int cb, int tb, const float* c) {
     const int lo = min(cb, tb), hi = max(cb, tb);
     for (uint32_t p = threadIdx.x; p < quarter; p += 2 * THREADS) {
@@ -146,85 +150,89 @@ __device__ __forceinline__ void df_tile_cu_body(float4* sm, uint32_t quarter, in
         const uint32_t i0 = insert_two_zeros32(p, lo, hi) | (1u << cb), i1 = i0 | (1u << tb);
         const uint32_t j0 = insert_two_zeros32(two ? q : p, lo, hi) | (1u << cb), j1 = j0 | (1u << tb);
         float4 a, b, x, y;
-        if (CLS != GC_DIAG1) { a = sm[i0]; x = sm[j0]; }
-        b = sm[i1];
-        y = sm[j1];
+        if (CLS != GC_DIAG1) { a = sm[L::at(i0)]; x = sm[L::at(j0)]; }
+        b = sm[L::at(i1)];
+        y = sm[L::at(j1)];
         df_pair_update<CLS>(c, a, b);
         df_pair_update<CLS>(c, x, y);
-        if (CLS != GC_DIAG1) sm[i0] = a;
-        sm[i1] = b;
+        if (CLS != GC_DIAG1) sm[L::at(i0)] = a;
+        sm[L::at(i1)] = b;
         if (two) {
-            if (CLS != GC_DIAG1) sm[j0] = x;
-            sm[j1] = y;
+            if (CLS != GC_DIAG1) sm[L::at(j0)] = x;
+            sm[L::at(j1)] = y;
         }
     }
 }
 
-template <int CLS, int THREADS>
+template <int CLS, int THREADS, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_cu(float4* sm, uint32_t N, int cb, int tb, const float* c) {
     const uint32_t quarter = N >> 2;
-    if ((quarter & (2 * THREADS - 1)) == 0) df_tile_cu_body<CLS, THREADS, false>(sm, quarter, cb, tb, c);
-    else df_tile_cu_body<CLS, THREADS, true>(sm, quarter, cb, tb, c);
+    if ((quarter & (2 * THREADS - 1)) == 0) df_tile_cu_body<CLS, THREADS, false, L>(sm, quarter, cb, tb, c);
+    else df_tile_cu_body<CLS, THREADS, true, L>(sm, quarter, cb, tb, c);
 }
 
-template <bool USE22, int THREADS>
+template <bool USE22, int THREADS, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_scale(float4* sm, uint32_t N, const float* c, int cb) {
     if (cb < 0) {
 #pragma unroll 2
-        for (uint32_t e = threadIdx.x; e < N; e += THREADS) sm[e] = USE22 ? df_cmul(c, 6, 7, sm[e]) : df_cmul(c, 0, 1, sm[e]);
+        for (uint32_t e = threadIdx.x; e < N; e += THREADS) {
+            const uint32_t se = L::at(e);
+            sm[se] = USE22 ? df_cmul(c, 6, 7, sm[se]) : df_cmul(c, 0, 1, sm[se]);
+        }
     } else {
 #pragma unroll 2
         for (uint32_t p = threadIdx.x; p < (N >> 1); p += THREADS) {
-            const uint32_t e = insert_zero32(p, cb) | (1u << cb);
+            const uint32_t e = L::at(insert_zero32(p, cb) | (1u << cb));
             sm[e] = USE22 ? df_cmul(c, 6, 7, sm[e]) : df_cmul(c, 0, 1, sm[e]);
         }
     }
 }
 
-template <int THREADS>
+template <int THREADS, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_swap(float4* sm, uint32_t N, int ab, int bb) {
     const int lo = min(ab, bb), hi = max(ab, bb);
     for (uint32_t p = threadIdx.x; p < (N >> 2); p += THREADS) {
         const uint32_t i = insert_two_zeros32(p, lo, hi);
-        const float4 x = sm[i | (1u << ab)];
-        sm[i | (1u << ab)] = sm[i | (1u << bb)];
-        sm[i | (1u << bb)] = x;
+        const uint32_t ia = L::at(i | (1u << ab)), ib = L::at(i | (1u << bb));
+        const float4 x = sm[ia];
+        sm[ia] = sm[ib];
+        sm[ib] = x;
     }
 }
 
-template <int CLS, int THREADS, int B>
+template <int CLS, int THREADS, int B, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_1q_any(float4* sm, uint32_t N, int tb, const float* c) {
-    if constexpr (B > 0 && (1 << (B - 1)) / THREADS >= 2) df_tile_1q_fixed<CLS, THREADS, B>(sm, tb, c);
-    else df_tile_1q<CLS, THREADS>(sm, N, tb, c);
+    if constexpr (B > 0 && (1 << (B - 1)) / THREADS >= 2) df_tile_1q_fixed<CLS, THREADS, B, L>(sm, tb, c);
+    else df_tile_1q<CLS, THREADS, L>(sm, N, tb, c);
 }
-template <int CLS, int THREADS, int B>
+template <int CLS, int THREADS, int B, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_cu_any(float4* sm, uint32_t N, int cb, int tb, const float* c) {
-    if constexpr (B > 0 && (1 << (B - 2)) / THREADS >= 2) df_tile_cu_fixed<CLS, THREADS, B>(sm, cb, tb, c);
-    else df_tile_cu<CLS, THREADS>(sm, N, cb, tb, c);
+    if constexpr (B > 0 && (1 << (B - 2)) / THREADS >= 2) df_tile_cu_fixed<CLS, THREADS, B, L>(sm, cb, tb, c);
+    else df_tile_cu<CLS, THREADS, L>(sm, N, cb, tb, c);
 }
 
 // B > 0: the tile has exactly 2^B amplitudes (fixed-size paths); B = 0: any size.
-template <int THREADS, int B = 0>
+template <int THREADS, int B = 0, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_pairs(float4* sm, uint32_t N, int cls, int cb, int tb, const float* c) {
     if (cb < 0) {
         switch (cls) {
-        case GC_GENERAL: df_tile_1q_any<GC_GENERAL, THREADS, B>(sm, N, tb, c); break;
-        case GC_REAL: df_tile_1q_any<GC_REAL, THREADS, B>(sm, N, tb, c); break;
-        case GC_REAL_BAL: df_tile_1q_any<GC_REAL_BAL, THREADS, B>(sm, N, tb, c); break;
-        case GC_DIAG: df_tile_1q_any<GC_DIAG, THREADS, B>(sm, N, tb, c); break;
-        case GC_DIAG1: df_tile_1q_any<GC_DIAG1, THREADS, B>(sm, N, tb, c); break;
-        case GC_ANTIDIAG: df_tile_1q_any<GC_ANTIDIAG, THREADS, B>(sm, N, tb, c); break;
-        default: df_tile_1q_any<GC_PERM, THREADS, B>(sm, N, tb, c); break;
+        case GC_GENERAL: df_tile_1q_any<GC_GENERAL, THREADS, B, L>(sm, N, tb, c); break;
+        case GC_REAL: df_tile_1q_any<GC_REAL, THREADS, B, L>(sm, N, tb, c); break;
+        case GC_REAL_BAL: df_tile_1q_any<GC_REAL_BAL, THREADS, B, L>(sm, N, tb, c); break;
+        case GC_DIAG: df_tile_1q_any<GC_DIAG, THREADS, B, L>(sm, N, tb, c); break;
+        case GC_DIAG1: df_tile_1q_any<GC_DIAG1, THREADS, B, L>(sm, N, tb, c); break;
+        case GC_ANTIDIAG: df_tile_1q_any<GC_ANTIDIAG, THREADS, B, L>(sm, N, tb, c); break;
+        default: df_tile_1q_any<GC_PERM, THREADS, B, L>(sm, N, tb, c); break;
         }
     } else {
         switch (cls) {
-        case GC_GENERAL: df_tile_cu_any<GC_GENERAL, THREADS, B>(sm, N, cb, tb, c); break;
-        case GC_REAL: df_tile_cu_any<GC_REAL, THREADS, B>(sm, N, cb, tb, c); break;
-        case GC_REAL_BAL: df_tile_cu_any<GC_REAL_BAL, THREADS, B>(sm, N, cb, tb, c); break;
-        case GC_DIAG: df_tile_cu_any<GC_DIAG, THREADS, B>(sm, N, cb, tb, c); break;
-        case GC_DIAG1: df_tile_cu_any<GC_DIAG1, THREADS, B>(sm, N, cb, tb, c); break;
-        case GC_ANTIDIAG: df_tile_cu_any<GC_ANTIDIAG, THREADS, B>(sm, N, cb, tb, c); break;
-        default: df_tile_cu_any<GC_PERM, THREADS, B>(sm, N, cb, tb, c); break;
+        case GC_GENERAL: df_tile_cu_any<GC_GENERAL, THREADS, B, L>(sm, N, cb, tb, c); break;
+        case GC_REAL: df_tile_cu_any<GC_REAL, THREADS, B, L>(sm, N, cb, tb, c); break;
+        case GC_REAL_BAL: df_tile_cu_any<GC_REAL_BAL, THREADS, B, L>(sm, N, cb, tb, c); break;
+        case GC_DIAG: df_tile_cu_any<GC_DIAG, THREADS, B, L>(sm, N, cb, tb, c); break;
+        case GC_DIAG1: df_tile_cu_any<GC_DIAG1, THREADS, B, L>(sm, N, cb, tb, c); break;
+        case GC_ANTIDIAG: df_tile_cu_any<GC_ANTIDIAG, THREADS, B, L>(sm, N, cb, tb, c); break;
+        default: df_tile_cu_any<GC_PERM, THREADS, B, L>(sm, N, cb, tb, c); break;
         }
     }
 }
@@ -251,7 +259,7 @@ __device__ __forceinline__ int slot_qubit(const TileOpDF& r, int f) {
 //      factors, taken from lane 0);
 //   2. T_lo *= C;
 //   3. every amplitude with bit jb = 1 is multiplied by T_lo * T_hi.
-template <int THREADS, int B, class OpAt>
+template <int THREADS, int B, class L, class OpAt>
 __device__ __forceinline__ void df_phase_run(float4* sm, float4* tab, uint32_t N, int b, const TileOpDF& h,
                                              OpAt op_at, int g, uint64_t base) {
     const int jb = h.tb, n_out = h.cb, lob = h.cq, hib = b - lob;
@@ -298,24 +306,25 @@ __device__ __forceinline__ void df_phase_run(float4* sm, float4* tab, uint32_t N
     const uint32_t lmask = nlo - 1u;
     if constexpr (B > 0 && (1 << (B - 1)) / THREADS >= 1) {
         constexpr int ITEMS = (1 << (B - 1)) / THREADS;
-        const uint32_t e0 = insert_zero32(t, jb) | (1u << jb);
+        const uint32_t e0 = insert_zero32(t, jb) | (1u << jb), s0 = L::at(e0);
 #pragma unroll
         for (int m = 0; m < ITEMS; ++m) {
-            const uint32_t e = e0 + insert_zero32((uint32_t)(m * THREADS), jb);
-            sm[e] = df_cmul_v(df_cmul_v(tlo[e & lmask], thi[e >> lob]), sm[e]);
+            const uint32_t d = insert_zero32((uint32_t)(m * THREADS), jb);
+            const uint32_t e = e0 + d;  // tables by tile index, the amplitude by its SMEM place
+            sm[s0 + d] = df_cmul_v(df_cmul_v(tlo[e & lmask], thi[e >> lob]), sm[s0 + d]);
         }
     } else {
         for (uint32_t p = t; p < (N >> 1); p += THREADS) {
-            const uint32_t e = insert_zero32(p, jb) | (1u << jb);
-            sm[e] = df_cmul_v(df_cmul_v(tlo[e & lmask], thi[e >> lob]), sm[e]);
+            const uint32_t e = insert_zero32(p, jb) | (1u << jb), se = L::at(e);
+            sm[se] = df_cmul_v(df_cmul_v(tlo[e & lmask], thi[e >> lob]), sm[se]);
         }
     }
 }
 
-template <int THREADS, int B = 0>
+template <int THREADS, int B = 0, class L = FlatLayout>
 __device__ __forceinline__ bool df_tile_apply(float4* sm, uint32_t N, const TileOpDF& op, uint64_t base) {
     if (op.kind == OP_SWAP) {
-        df_tile_swap<THREADS>(sm, N, op.tb, op.cb);
+        df_tile_swap<THREADS, L>(sm, N, op.tb, op.cb);
         return true;
     }
     int cb = -1;
@@ -329,11 +338,11 @@ __device__ __forceinline__ bool df_tile_apply(float4* sm, uint32_t N, const Tile
     if (op.tb < 0) {
         const bool bit = (base >> op.tq) & 1ull;
         if (op.cls == GC_DIAG1 && !bit) return false;
-        if (bit) df_tile_scale<true, THREADS>(sm, N, op.c, cb);
-        else df_tile_scale<false, THREADS>(sm, N, op.c, cb);
+        if (bit) df_tile_scale<true, THREADS, L>(sm, N, op.c, cb);
+        else df_tile_scale<false, THREADS, L>(sm, N, op.c, cb);
         return true;
     }
-    df_tile_pairs<THREADS, B>(sm, N, op.cls, cb, op.tb, op.c);
+    df_tile_pairs<THREADS, B, L>(sm, N, op.cls, cb, op.tb, op.c);
     return true;
 }
 

@@ -10,22 +10,6 @@
 
 namespace qs {
 
-// Shared-memory layout of a tile: amplitude e of the tile sits at L::at(e).
-struct FlatLayout {
-    static __device__ __forceinline__ uint32_t at(uint32_t e) { return e; }
-};
-// complex64 tiles (8-byte amplitudes, 32 four-byte banks): the partners of a
-// gate on tile bit t <= 3 are 1..8 elements apart, so a warp's 32 lanes would
-// hit half of the banks and a 64-bit access would take four wavefronts instead
-// of two.  Storing amplitude e at e ^ (15 * bit4(e)) spreads them over all
-// banks (every single-qubit gate and most controlled ones back to two).  The
-// per-step offsets of the fixed-size loops (multiples of the CTA size with
-// zeros inserted) leave bits 0..4 alone, so there L::at(base + d) =
-// L::at(base) + d and the swizzle costs nothing per access.
-struct SwizzledLayout {
-    static __device__ __forceinline__ uint32_t at(uint32_t e) { return e ^ ((0u - ((e >> 4) & 1u)) & 15u); }
-};
-
 // Two pairs per step (p and p + THREADS), both loaded before either is
 // updated, so the two updates are independent instruction chains.
 template <class R, int CLS, int THREADS, class L = FlatLayout>
