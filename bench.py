@@ -93,9 +93,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x F
 # of the n=26 case (profiles/k_tile_df_c128_n26_full.md); a tile pass reads and
 # writes the whole state once, so traffic scales with 2^n.  Update (or set to
 # None) whenever the kernel changes.
-DF_TILE_TRAFFIC_N26 = 1.074417e9 + 1.012082e9
+DF_TILE_TRAFFIC_N26 = 1.073894e9 + 1.012251e9
 # the same for the complex64 tile kernel, one n=27 launch (profiles/k_tile_c64_n27_full.md)
-C64_TILE_TRAFFIC_N27 = 1.073863e9 + 1.012055e9
+C64_TILE_TRAFFIC_N27 = 1.074006e9 + 1.012051e9
 
 
 def gate_cost(g, n, s, table=None):
@@ -403,7 +403,7 @@ def run_ours(args):
                 "fp64_equivalent_frac_of_fp64_peak": fp64_tf / FP64_PEAK_TFLOPS,
                 "limiter": ("instruction issue: double-float FP32 arithmetic plus SMEM sweeps and index work "
                             "(profiles/k_tile_df_c128_n26_full.md)") if df else
-                           ("shared-memory bandwidth: 92% of peak SMEM wavefronts "
+                           ("shared-memory bandwidth: 83% of peak SMEM wavefronts, 86% issue "
                             "(profiles/k_tile_c64_n27_full.md)"),
                 "launches_per_step": len(tile_idx), "avg_launch_ms": tile_launch_ms,
                 "hbm_frac_of_measured": (2 * N * s_bytes / (tile_launch_ms / 1e3)) / 6794.8e9 if tile_idx else None}
