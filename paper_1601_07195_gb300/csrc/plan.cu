@@ -10,10 +10,15 @@
 //   * a later gate may be pulled into the pass ahead of gates left behind when
 //     it commutes with each of them: disjoint qubits, or both diagonal;
 //   * a pass holding a single gate runs as a strided single-gate kernel
-//     (gates.cu), which moves only the amplitudes the gate changes.
+//     (gates.cu), which moves only the amplitudes the gate changes;
+//   * after the greedy scan, a local search exchanges one tile qubit for one
+//     left out while that admits more gates into the pass.
 // The order of the gates within a pass and among the gates left behind is the
 // circuit order, so the plan computes the same ordered product (up to
-// rounding) as applying the gates one at a time.
+// rounding) as applying the gates one at a time.  Within a pass, adjacent
+// same-qubit gates are multiplied into one matrix and runs of phase gates
+// around one qubit become one table update; consecutive double-float passes
+// hand the state over as float pairs (qs_internal.h).
 #include <algorithm>
 #include <cmath>
 #include <utility>

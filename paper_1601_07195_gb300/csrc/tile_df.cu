@@ -1,11 +1,14 @@
 // tile_df.cu -- the fused tile pass of tile.cu for complex128 states with the
 // gate arithmetic in double-float form (df.cuh) on the FP32 pipes.
 //
-// The tile is split into (hi, lo) float pairs once when it is loaded, every
-// gate of the pass is applied to the pairs in shared memory, and the pairs are
-// rounded back to doubles once when the tile is stored.  Layout, planner
-// contract and control/diagonal handling are those of tile.cu (Section 4.4,
-// Fig. 5, on a shared-memory tile over any qubit set).
+// The tile is split into (hi, lo) float pairs when it is loaded, every gate of
+// the pass is applied to the pairs in shared memory, and the pairs are rounded
+// back to doubles when the tile is stored; between consecutive passes of a
+// plan the state stays in HBM as float pairs instead (TilePass::io), so the
+// split and the join run once per run of passes.  Planner contract and
+// control/diagonal handling are those of tile.cu (Section 4.4, Fig. 5, on a
+// shared-memory tile over any qubit set); the tile's shared-memory layout
+// spreads the partners of gates on the lowest tile bits over all banks.
 #include <cstring>
 #include <type_traits>
 
