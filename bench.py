@@ -88,6 +88,9 @@ _FLOPS = {"general": 14.0, "real": 6.0, "diag": 6.0, "diag1": 6.0, "antidiag": 6
 # df_mul = 1 FMUL + 3 FFMA = 7 flops; TwoSum = 6; dot2 = 2 df_mul + TwoSum + 2 adds = 22;
 # dot4 = 4 df_mul + 3 TwoSum + 6 adds = 52 (pairs stay unnormalised); a complex output = 2 dots.
 _DF_FLOPS = {"general": 104.0, "real": 44.0, "diag": 44.0, "diag1": 44.0, "antidiag": 44.0, "perm": 0.0}
+# a balanced real gate (H-like, qs_plan_pass_balanced): per component an exact
+# sum (1 FMUL + TwoSum + 1 FFMA + 1 add = 10) and one product (7): 34 per amplitude
+_DF_FLOPS_BALANCED = 34.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 # DRAM bytes (read + write) of one double-float tile launch, from the ncu capture
 # of the n=26 case (profiles/k_tile_df_c128_n26_full.md); a tile pass reads and
@@ -383,6 +386,10 @@ def run_ours(args):
     # FP32 flops of the kernel's own algorithm: double-float update for complex128, plain FP32 for complex64
     table = _DF_FLOPS if df else _FLOPS
     fp32_flops = sum(kernel_flops(plan.op_counts(i), n, table) for i in tile_idx)
+    if df:  # balanced real updates were counted as general real ones above
+        for i in tile_idx:
+            b1, bc = plan.balanced(i)
+            fp32_flops -= (_DF_FLOPS["real"] - _DF_FLOPS_BALANCED) * N * (b1 + 0.5 * bc)
     achieved_tf = fp32_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
     roofline = {"bound": "alu", "kernel": "k_tile_df (fused tile pass, double-float)" if df else "k_tile_p<float, 12> (fused tile pass, FP32)",
                 "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -397,7 +404,8 @@ def run_ours(args):
                                "has no FP32 figure (an FFMA probe on this GPU measured 74.2 TFLOP/s)",
                 "flops_counted": ("FP32 flops of the double-float updates the kernel applies (after in-pass "
                                   "fusion of same-qubit gates) per touched amplitude: general 104, "
-                                  "real/diagonal/anti-diagonal 44, permutation 0; a fused phase run counts as one diagonal update") if df else
+                                  "real/diagonal/anti-diagonal 44, balanced real (H-like) 34, permutation 0; a fused phase "
+                                  "run counts as one diagonal update") if df else
                                  "FP32 flops of the updates the kernel applies",
                 "fp64_equivalent_tflops": fp64_tf,
                 "fp64_equivalent_frac_of_fp64_peak": fp64_tf / FP64_PEAK_TFLOPS,

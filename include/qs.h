@@ -190,6 +190,14 @@ QS_API qs_status qs_plan_device_ops(const qs_plan* p, int* n_ops);
  * arithmetic. */
 QS_API qs_status qs_plan_pass_op_counts(const qs_plan* p, int i, int* counts);
 
+/* Of pass i's real gate updates (class 1 above), how many the complex128
+ * double-float kernel applies in balanced form: counts[0] single-qubit,
+ * counts[1] controlled.  A real gate whose four entries share one magnitude
+ * (H and its products with X and Z) updates a pair as q11 (a + s1 b) and
+ * q21 (a + s3 b): an exact sum and one product per component.  Zero for
+ * other plans. */
+QS_API qs_status qs_plan_pass_balanced(const qs_plan* p, int i, int* counts);
+
 /* Per-pass description: for pass i, its kind (0 = single gate, 1 = tile),
  * first gate and gate count in plan order, and the tile's qubit mask. */
 QS_API qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* n_gates, uint64_t* tile_mask);

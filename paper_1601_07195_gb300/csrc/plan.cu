@@ -44,6 +44,7 @@ struct PlanPass {
     bool moves_only; // every gate is a permutation (X, CNOT, SWAP): exact moves of 16-byte values
     std::vector<int> members;  // circuit positions of the pass's gates, in execution order
     int op_counts[3][6];       // ops the kernel applies, by kind (1q, controlled, swap) and class
+    int balanced[2];           // of the real ones: balanced (H-like) single-qubit / controlled records
 };
 
 inline int popc(uint64_t x) { return __builtin_popcountll(x); }
@@ -365,6 +366,7 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
             const Op& o = fused[i++];
             pp.op_counts[o.kind][o.cls] += 1;
             tops.push_back(to_tile_op<OpT>(o, d.bit_of));
+            if (tops.back().cls == GC_REAL_BAL) pp.balanced[o.kind == OP_CU ? 1 : 0] += 1;
             if (df) t64.push_back(to_tile_op<TileOp<double>>(o, d.bit_of));
             if (!(o.kind == OP_SWAP || o.cls == GC_PERM)) pp.moves_only = false;
             p->device_ops += 1;
@@ -629,6 +631,14 @@ qs_status qs_plan_pass_op_counts(const qs_plan* p, int i, int* counts) {
     if (!p || !counts) return fail(QS_EINVAL, "NULL argument");
     if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
     std::memcpy(counts, p->passes[i].op_counts, sizeof(p->passes[i].op_counts));
+    return QS_OK;
+}
+
+qs_status qs_plan_pass_balanced(const qs_plan* p, int i, int* counts) {
+    if (!p || !counts) return fail(QS_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
+    counts[0] = p->passes[i].balanced[0];
+    counts[1] = p->passes[i].balanced[1];
     return QS_OK;
 }
 

@@ -61,6 +61,7 @@ _SIGS = {
     "qs_plan_pass_gates": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "qs_plan_device_ops": [_vp, ctypes.POINTER(ctypes.c_int)],
     "qs_plan_pass_op_counts": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "qs_plan_pass_balanced": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "qs_plan_set_timing": [_vp, ctypes.c_int],
     "qs_plan_pass_times": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)],
     "qs_plan_destroy": [_vp],
@@ -300,6 +301,13 @@ class Plan:
         buf = (ctypes.c_int * 18)()
         _check(load().qs_plan_pass_op_counts(self._h, i, buf))
         return np.array(buf[:], dtype=np.int64).reshape(3, 6)
+
+    def balanced(self, i):
+        """(single-qubit, controlled) real updates of pass i applied in balanced form
+        (complex128 double-float plans; see qs_plan_pass_balanced)."""
+        buf = (ctypes.c_int * 2)()
+        _check(load().qs_plan_pass_balanced(self._h, i, buf))
+        return int(buf[0]), int(buf[1])
 
     def close(self):
         if self._h is not None and self._h.value:
