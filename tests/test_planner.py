@@ -142,3 +142,24 @@ def test_autotune_cache_file_roundtrip(tmp_path, monkeypatch):
     assert A.apply_cache(str(cache), device="FAKE GPU") == 1
     assert A.tune_get(qs.QS_C128, 21) == (11, 4)
     assert A.apply_cache(str(cache), device="OTHER") == 0
+
+
+def test_balanced_real_counts():
+    """qs_plan_pass_balanced: complex128 double-float plans apply real gates whose
+    entries share one magnitude (H, HX, XH, ZH) in balanced form; RY-type real
+    gates, complex64 and native-FP64 plans report none."""
+    n = 14
+    r2 = 1 / np.sqrt(2)
+    gates = G.concat([G.gate_u1(3, G.MAT_H), G.gate_u1(5, (r2, r2, -r2, r2)), G.gate_u1(6, G.MAT_H),
+                      G.gate_rot(G.G_RY, 7, 0), G.gate_cu(1, 8, G.MAT_H), G.gate_u1(9, G.MAT_X)])
+    theta = np.array([0.3])
+
+    def totals(dt, flags=0):
+        p = qs.Plan(fake_state(n, dt), gates, theta, flags=qs.PLAN_DRY_RUN | qs.PLAN_NO_MERGE | flags)
+        bal = np.sum([p.balanced(i) for i in range(p.stats()["passes"])], axis=0)
+        real = sum(int(p.op_counts(i)[0][1]) + int(p.op_counts(i)[1][1]) for i in range(p.stats()["passes"]))
+        return tuple(int(v) for v in bal), real
+
+    assert totals(qs.QS_C128) == ((3, 1), 5)  # 3 single-qubit + 1 controlled H-like, plus RY
+    assert totals(qs.QS_C64)[0] == (0, 0)
+    assert totals(qs.QS_C128, qs.PLAN_ARITH_F64)[0] == (0, 0)
