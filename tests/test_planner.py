@@ -163,3 +163,71 @@ def test_balanced_real_counts():
     assert totals(qs.QS_C128) == ((3, 1), 5)  # 3 single-qubit + 1 controlled H-like, plus RY
     assert totals(qs.QS_C64)[0] == (0, 0)
     assert totals(qs.QS_C128, qs.PLAN_ARITH_F64)[0] == (0, 0)
+
+
+def _random_mixed_circuit(n, count, seed):
+    """Single-qubit gates of every class, controlled gates, swaps and rotations."""
+    rng = G.SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        a = rng.randint(n)
+        b = (a + 1 + rng.randint(n - 1)) % n
+        k = rng.randint(9)
+        if k == 0:
+            out.append(G.gate_u1(a, G.haar_2x2(rng)))
+        elif k == 1:
+            out.append(G.gate_u1(a, G.MAT_H))
+        elif k == 2:
+            out.append(G.gate_u1(a, G.MAT_T))
+        elif k == 3:
+            out.append(G.gate_u1(a, G.MAT_X))
+        elif k == 4:
+            out.append(G.gate_cu(a, b, G.MAT_X))
+        elif k == 5:
+            out.append(G.gate_cu(a, b, G.mat_cphase(rng.uniform_range(0.0, 6.0))))
+        elif k == 6:
+            out.append(G.gate_swap(a, b))
+        elif k == 7:
+            out.append(G.gate_rot(G.G_RZ, a, 0))
+        else:
+            out.append(G.gate_cu(a, b, G.haar_2x2(rng)))
+    return G.concat(out)
+
+
+def test_random_plans_are_valid_reorderings():
+    """Property test over random circuits, qubit counts and tile shapes: every
+    gate is planned once, each tile pass holds its gates' mixing qubits, a gate
+    only moves ahead of gates it commutes with, and the oracle applying the
+    gates in execution order reproduces the circuit-order state."""
+    hyp = pytest.importorskip("hypothesis")
+    st_ = hyp.strategies
+
+    @hyp.settings(max_examples=200, deadline=None, derandomize=True)
+    @hyp.given(n=st_.integers(2, 10), count=st_.integers(1, 160), seed=st_.integers(0, 10 ** 6),
+               b=st_.integers(2, 12), b0=st_.integers(0, 6), dt=st_.sampled_from([0, 1]))
+    def check(n, count, seed, b, b0, dt):
+        gates = _random_mixed_circuit(n, count, seed)
+        theta = np.array([0.7])
+        st = fake_state(n, dt)
+        p = qs.Plan(st, gates, theta, flags=qs.PLAN_DRY_RUN, tile_bits=b | (min(b0, b) << 8))
+        passes = p.passes()
+        order = [g for ps in passes for g in ps["gates"]]
+        assert sorted(order) == list(range(len(gates)))
+        for ps in passes:
+            if ps["kind"] == "tile":
+                assert bin(ps["mask"]).count("1") == min(b, n)
+                for j in ps["gates"]:
+                    assert all((ps["mask"] >> q) & 1 for q in mixing(gates[j]))
+        pos = {g: i for i, g in enumerate(order)}
+        for a in range(len(gates)):
+            for c in range(a + 1, len(gates)):
+                if pos[c] < pos[a]:
+                    assert commute(gates[a], gates[c]), (a, c)
+        x = seed % (1 << n)
+        want = O.simulate(n, gates, theta=theta, x=x)
+        got = O.simulate(n, gates[order], theta=theta, x=x)
+        assert np.max(np.abs(want - got)) < 1e-12
+        p.close()
+        st.close()
+
+    check()
