@@ -671,3 +671,31 @@ def test_special_phase_and_balanced_gates_in_tiles(qs, dt):
             got = s.to_numpy()
             p.close()
         assert np.max(np.abs(got - want)) < 5 * TOL[dt], tile_bits
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_random_shapes_against_oracle(qs, dt):
+    """Seeded random circuits (every gate class, controlled gates, swaps,
+    rotations, QFT chains) on random qubit counts and tile shapes, planned with
+    all fusions and run on the GPU, against the oracle."""
+    rng = G.SplitMix64(31337 + dt)
+    for case in range(24):
+        n = 4 + rng.randint(11)
+        b = 2 + rng.randint(min(n, 13) - 1)
+        b0 = rng.randint(min(b, 6) + 1)
+        r, _ = G.random_circuit(n, 20 + rng.randint(200), 9000 + case)
+        parts = [r]
+        if rng.randint(2):
+            parts.append(G.qft_circuit(n))
+        if rng.randint(2):
+            parts.append(G.concat([G.gate_swap(k, (k + 1 + rng.randint(n - 1)) % n) for k in range(n - 1)]))
+        gates = G.concat(parts)
+        psi = rand_state(n, 100 + case)
+        want = O.run(expected_input(psi, dt), gates)
+        with upload(qs, n, dt, psi) as s:
+            p = s.plan(gates, tile_bits=b | (b0 << 8))
+            p.execute()
+            got = s.to_numpy()
+            p.close()
+        err = float(np.max(np.abs(got - want)))
+        assert err < 5 * TOL[dt], (case, n, b, b0, err)
