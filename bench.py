@@ -91,12 +91,16 @@ _DF_FLOPS = {"general": 104.0, "real": 44.0, "diag": 44.0, "diag1": 44.0, "antid
 # a balanced real gate (H-like, qs_plan_pass_balanced): per component an exact
 # sum (1 FMUL + TwoSum + 1 FFMA + 1 add = 10) and one product (7): 34 per amplitude
 _DF_FLOPS_BALANCED = 34.0
+# a general single-qubit unitary in phase-shear-phase form (qs_plan_pass_prp): two
+# complex products on the |1> amplitude (2 x 22 flops each) and a shear, per
+# component one product and one sum (15): 148 per pair, 74 per amplitude
+_DF_FLOPS_PRP = 74.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 # DRAM bytes (read + write) of one double-float tile launch, from the ncu capture
 # of the n=26 case (profiles/k_tile_df_c128_n26_full.md); a tile pass reads and
 # writes the whole state once, so traffic scales with 2^n.  Update (or set to
 # None) whenever the kernel changes.
-DF_TILE_TRAFFIC_N26 = 1.073894e9 + 1.012251e9
+DF_TILE_TRAFFIC_N26 = 1.073891e9 + 1.012328e9
 # the same for the complex64 tile kernel, one n=27 launch (profiles/k_tile_c64_n27_full.md)
 C64_TILE_TRAFFIC_N27 = 1.074006e9 + 1.012051e9
 
@@ -386,10 +390,11 @@ def run_ours(args):
     # FP32 flops of the kernel's own algorithm: double-float update for complex128, plain FP32 for complex64
     table = _DF_FLOPS if df else _FLOPS
     fp32_flops = sum(kernel_flops(plan.op_counts(i), n, table) for i in tile_idx)
-    if df:  # balanced real updates were counted as general real ones above
+    if df:  # balanced real and phase-shear-phase updates were counted as real / general ones above
         for i in tile_idx:
             b1, bc = plan.balanced(i)
             fp32_flops -= (_DF_FLOPS["real"] - _DF_FLOPS_BALANCED) * N * (b1 + 0.5 * bc)
+            fp32_flops -= (_DF_FLOPS["general"] - _DF_FLOPS_PRP) * N * plan.prp(i)
     achieved_tf = fp32_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
     roofline = {"bound": "alu", "kernel": "k_tile_df (fused tile pass, double-float)" if df else "k_tile_p<float, 12> (fused tile pass, FP32)",
                 "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -404,7 +409,8 @@ def run_ours(args):
                                "has no FP32 figure (an FFMA probe on this GPU measured 74.2 TFLOP/s)",
                 "flops_counted": ("FP32 flops of the double-float updates the kernel applies (after in-pass "
                                   "fusion of same-qubit gates) per touched amplitude: general 104, "
-                                  "real/diagonal/anti-diagonal 44, balanced real (H-like) 34, permutation 0; a fused phase "
+                                  "real/diagonal/anti-diagonal 44, balanced real (H-like) 34, general single-qubit in "
+                                  "phase-shear-phase form 74, permutation 0; a fused phase "
                                   "run counts as one diagonal update") if df else
                                  "FP32 flops of the updates the kernel applies",
                 "fp64_equivalent_tflops": fp64_tf,

@@ -144,13 +144,24 @@ enum {
     QS_PLAN_DRY_RUN = 8,    /* plan on the host only (no device memory); cannot execute */
     QS_PLAN_NO_MERGE = 16,  /* keep every gate separate: no product of adjacent single-qubit
                                gates on the same qubit inside a tile pass */
-    QS_PLAN_NO_PHASE_RUNS = 32  /* apply runs of phase gates one by one.  Without it, a run of
+    QS_PLAN_NO_PHASE_RUNS = 32, /* apply runs of phase gates one by one.  Without it, a run of
                                consecutive gates inside a tile pass that are diagonal with
                                q11 = 1 (T, S, phase, CZ, controlled phase) and all involve one
                                tile qubit j (the controlled-phase chains of the QFT, Section 5)
                                is applied as one update: per tile, a table of phase products
                                over the low and the high half of the tile bits, and two complex
                                products per amplitude whose bit j is 1. */
+    QS_PLAN_NO_PRP = 64     /* complex128 double-float plans: apply every general single-qubit
+                               unitary with its full complex 2x2 product.  Without it, inside a
+                               tile pass, such a unitary U is applied as
+                               U = K diag(1, z) [[1, t], [-t, 1]] diag(1, y)  (|t| <= 1; when
+                               |q12| > |q11|, the same form times X): two complex products on
+                               the |1> amplitude and one real shear, about 70% of the
+                               arithmetic.  The complex scalars K of a pass are multiplied
+                               into one other single-qubit update of the pass (a diagonal,
+                               anti-diagonal or general one, whose cost does not change), so
+                               the pass applies the same product.  Taken only where the form
+                               reproduces U to 4e-15 in every entry (unitary U). */
 };
 
 /* Build an execution plan for `gates` (copied in) on state s: gate classes,
@@ -197,6 +208,11 @@ QS_API qs_status qs_plan_pass_op_counts(const qs_plan* p, int i, int* counts);
  * q21 (a + s3 b): an exact sum and one product per component.  Zero for
  * other plans. */
 QS_API qs_status qs_plan_pass_balanced(const qs_plan* p, int i, int* counts);
+
+/* Of pass i's general single-qubit updates (class 0 above), how many the
+ * complex128 double-float kernel applies in the phase-shear-phase form of
+ * QS_PLAN_NO_PRP: *count.  Zero for other plans. */
+QS_API qs_status qs_plan_pass_prp(const qs_plan* p, int i, int* count);
 
 /* Per-pass description: for pass i, its kind (0 = single gate, 1 = tile),
  * first gate and gate count in plan order, and the tile's qubit mask. */

@@ -156,6 +156,18 @@ __device__ __forceinline__ float4 df_bal(const float* c, int j, float s, float4 
     return make_float4(re.h, re.l, im.h, im.l);
 }
 
+// phase, shear, phase (GC_PRP): bt = y b; a' = a + t bt; b' = z (bt - t a),
+// with y = doubles (0, 1), the real t = double 2, z = doubles (4, 5)
+__device__ __forceinline__ void df_prp(const float* c, float4& a, float4& b) {
+    const float4 bt = df_cmul(c, 0, 1, b);
+    const dfl ar = df_dot2({a.x, a.y}, df_mul(QH(2), QL(2), bt.x, bt.y));
+    const dfl ai = df_dot2({a.z, a.w}, df_mul(QH(2), QL(2), bt.z, bt.w));
+    const dfl br = df_dot2({bt.x, bt.y}, df_mul(-QH(2), -QL(2), a.x, a.y));
+    const dfl bi = df_dot2({bt.z, bt.w}, df_mul(-QH(2), -QL(2), a.z, a.w));
+    a = make_float4(ar.h, ar.l, ai.h, ai.l);
+    b = df_cmul(c, 4, 5, make_float4(br.h, br.l, bi.h, bi.l));
+}
+
 #undef QH
 #undef QL
 

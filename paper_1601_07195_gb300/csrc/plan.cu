@@ -45,6 +45,7 @@ struct PlanPass {
     std::vector<int> members;  // circuit positions of the pass's gates, in execution order
     int op_counts[3][6];       // ops the kernel applies, by kind (1q, controlled, swap) and class
     int balanced[2];           // of the real ones: balanced (H-like) single-qubit / controlled records
+    int prp;                   // of the general single-qubit ones: phase-shear-phase records
 };
 
 inline int popc(uint64_t x) { return __builtin_popcountll(x); }
@@ -123,6 +124,139 @@ template <> TileOpDF to_tile_op<TileOpDF>(const Op& o, const int* bit_of) {
         t.c[10] = (o.m[6] == o.m[4]) ? 1.0f : -1.0f;
     }
     return t;
+}
+
+// acc *= (r + i I)
+void cmul_acc(double* acc, double r, double i) {
+    const double ar = acc[0], ai = acc[1];
+    acc[0] = ar * r - ai * i;
+    acc[1] = ar * i + ai * r;
+}
+
+// ---- general single-qubit unitaries in phase-shear-phase form ------------------
+// For a unitary V with |v11| >= |v12| (else V = U X, the columns swapped):
+//   V = K diag(1, z) [[1, t], [-t, 1]] diag(1, y),
+//   K = v11,  t = |v21| / |v11|,  z = -(v21 / v11) / t,  y = (v22 / v11) / z,
+// which reproduces v11, v21 and v22 to rounding and gives v12 = K t y, equal to
+// the given v12 up to the departure of V from unitarity.  The double-float
+// kernel then applies two complex products to the |1> amplitude and a shear
+// (one product and one sum per component) instead of the full 2x2 product.
+struct PrpForm {
+    bool swap;
+    double K[2], t, y[2], z[2];
+};
+
+constexpr double kPrpTol = 4e-15;          // largest entry error of the form accepted
+constexpr double kPrpMinScale = 0x1p-24;   // smallest product of left-out scalars K in one pass
+
+void cdiv(double ar, double ai, double br, double bi, double& r, double& i) {
+    const double d = br * br + bi * bi;
+    r = (ar * br + ai * bi) / d;
+    i = (ai * br - ar * bi) / d;
+}
+
+bool prp_form(const Op& o, PrpForm& f) {
+    if (o.kind != OP_1Q || o.cls != GC_GENERAL) return false;
+    const double* m = o.m;
+    f.swap = std::hypot(m[2], m[3]) > std::hypot(m[0], m[1]);
+    double v[8];
+    const int col[2] = {f.swap ? 1 : 0, f.swap ? 0 : 1};
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) {
+            v[2 * (2 * r + c)] = m[2 * (2 * r + col[c])];
+            v[2 * (2 * r + c) + 1] = m[2 * (2 * r + col[c]) + 1];
+        }
+    const double a11 = std::hypot(v[0], v[1]), a21 = std::hypot(v[4], v[5]);
+    if (!(a11 >= 0.5 && a11 <= 1.0 + 1e-12 && a21 > 0.0)) return false;
+    f.K[0] = v[0];
+    f.K[1] = v[1];
+    f.t = a21 / a11;
+    if (!(f.t <= 1.0 + 1e-12)) return false;
+    double q[2];
+    cdiv(v[4], v[5], v[0], v[1], q[0], q[1]);
+    f.z[0] = -q[0] / f.t;
+    f.z[1] = -q[1] / f.t;
+    cdiv(v[6], v[7], v[0], v[1], q[0], q[1]);
+    cdiv(q[0], q[1], f.z[0], f.z[1], f.y[0], f.y[1]);
+    // the entries the form gives, against V
+    auto cm = [](const double* a, const double* b, double* out) {
+        const double r = a[0] * b[0] - a[1] * b[1], i = a[0] * b[1] + a[1] * b[0];
+        out[0] = r;
+        out[1] = i;
+    };
+    double e12[2], e21[2], e22[2], zy[2];
+    cm(f.K, f.y, e12);
+    e12[0] *= f.t;
+    e12[1] *= f.t;
+    cm(f.K, f.z, e21);
+    e21[0] *= -f.t;
+    e21[1] *= -f.t;
+    cm(f.z, f.y, zy);
+    cm(f.K, zy, e22);
+    double err = 0.0;
+    for (int j = 0; j < 2; ++j) {
+        err = std::max(err, std::fabs(e12[j] - v[2 + j]));
+        err = std::max(err, std::fabs(e21[j] - v[4 + j]));
+        err = std::max(err, std::fabs(e22[j] - v[6 + j]));
+    }
+    return err <= kPrpTol;  // false for NaN
+}
+
+TileOpDF prp_record(const Op& o, const PrpForm& f, const int* bit_of) {
+    TileOpDF r{};
+    fill_common(r, o, bit_of);
+    r.cls = f.swap ? GC_PRP_X : GC_PRP;
+    split_to_floats(f.y[0], r.c[0], r.c[1]);
+    split_to_floats(f.y[1], r.c[2], r.c[3]);
+    split_to_floats(f.t, r.c[4], r.c[5]);
+    split_to_floats(f.z[0], r.c[8], r.c[9]);
+    split_to_floats(f.z[1], r.c[10], r.c[11]);
+    return r;
+}
+
+// Which single-qubit ops of one pass (after fusion) become phase-shear-phase
+// records, and the op (keeper) that takes the product of their scalars K: a
+// diagonal, anti-diagonal or general update whose class and cost a complex
+// scale leaves unchanged, else the last candidate, which then stays general.
+// Candidates whose K would bring the product below kPrpMinScale stay general,
+// so the amplitudes inside the pass grow by less than 2^24.
+int choose_prp(const std::vector<Op>& ops, std::vector<PrpForm>& forms, std::vector<char>& as_prp,
+               double* Kpass) {
+    forms.assign(ops.size(), PrpForm{});
+    as_prp.assign(ops.size(), 0);
+    Kpass[0] = 1.0;
+    Kpass[1] = 0.0;
+    int keeper = -1, last = -1;
+    for (size_t i = 0; i < ops.size(); ++i) {
+        if (prp_form(ops[i], forms[i])) {
+            as_prp[i] = 1;
+            last = (int)i;
+        }
+    }
+    if (last < 0) return -1;
+    for (size_t i = 0; i < ops.size() && keeper < 0; ++i) {
+        const Op& o = ops[i];
+        if (o.kind == OP_1Q && !as_prp[i] && (o.cls == GC_DIAG || o.cls == GC_ANTIDIAG || o.cls == GC_GENERAL))
+            keeper = (int)i;
+    }
+    if (keeper < 0) {
+        keeper = last;
+        as_prp[last] = 0;
+    }
+    double mag = 1.0;
+    int used = 0;
+    for (size_t i = 0; i < ops.size(); ++i) {
+        if (!as_prp[i]) continue;
+        const double k = std::hypot(forms[i].K[0], forms[i].K[1]);
+        if (mag * k < kPrpMinScale) {
+            as_prp[i] = 0;
+            continue;
+        }
+        mag *= k;
+        cmul_acc(Kpass, forms[i].K[0], forms[i].K[1]);
+        ++used;
+    }
+    return used > 0 ? keeper : -1;
 }
 
 template <class OpT>
@@ -219,12 +353,6 @@ int phase_gate_cost(const Op& o, qs_dtype dt) {
     return (o.kind == OP_1Q ? c : c / 2) + 12;
 }
 int phase_run_cost(qs_dtype dt) { return 2 * class_cost(GC_DIAG1, dt) + 5 * 12; }
-
-void cmul_acc(double* acc, double r, double i) {
-    const double ar = acc[0], ai = acc[1];
-    acc[0] = ar * r - ai * i;
-    acc[1] = ar * i + ai * r;
-}
 
 void set_slot(TileOpDF& r, int f, const double* v) {
     split_to_floats(v[0], r.c[4 * f], r.c[4 * f + 1]);
@@ -349,6 +477,11 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
         const std::vector<Op> fused = fuse_single_qubit(ops, d.members, p->s->dt, !(p->flags & QS_PLAN_NO_MERGE));
         pp.moves_only = true;
         const bool runs = !(p->flags & QS_PLAN_NO_PHASE_RUNS);
+        std::vector<PrpForm> forms;
+        std::vector<char> as_prp;
+        double Kpass[2] = {1.0, 0.0};
+        const int keeper = (df && !(p->flags & QS_PLAN_NO_PRP)) ? choose_prp(fused, forms, as_prp, Kpass) : -1;
+        if (keeper < 0) as_prp.assign(fused.size(), 0);
         for (size_t i = 0; i < fused.size();) {
             int pivot = -1;
             const size_t len = runs ? find_phase_run(fused, i, d.bit_of, p->s->dt, pivot) : 0;
@@ -363,8 +496,21 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
                 i += len;
                 continue;
             }
-            const Op& o = fused[i++];
+            const size_t at = i++;
+            Op o = fused[at];
             pp.op_counts[o.kind][o.cls] += 1;
+            if constexpr (std::is_same<OpT, TileOpDF>::value) {
+                if (as_prp[at]) {
+                    tops.push_back(prp_record(o, forms[at], d.bit_of));
+                    t64.push_back(to_tile_op<TileOp<double>>(o, d.bit_of));
+                    pp.prp += 1;
+                    pp.moves_only = false;
+                    p->device_ops += 1;
+                    continue;
+                }
+                if ((int)at == keeper)  // the pass's scalars K, multiplied into every entry
+                    for (int j = 0; j < 4; ++j) cmul_acc(&o.m[2 * j], Kpass[0], Kpass[1]);
+            }
             tops.push_back(to_tile_op<OpT>(o, d.bit_of));
             if (tops.back().cls == GC_REAL_BAL) pp.balanced[o.kind == OP_CU ? 1 : 0] += 1;
             if (df) t64.push_back(to_tile_op<TileOp<double>>(o, d.bit_of));
@@ -639,6 +785,13 @@ qs_status qs_plan_pass_balanced(const qs_plan* p, int i, int* counts) {
     if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
     counts[0] = p->passes[i].balanced[0];
     counts[1] = p->passes[i].balanced[1];
+    return QS_OK;
+}
+
+qs_status qs_plan_pass_prp(const qs_plan* p, int i, int* count) {
+    if (!p || !count) return fail(QS_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
+    *count = p->passes[i].prp;
     return QS_OK;
 }
 

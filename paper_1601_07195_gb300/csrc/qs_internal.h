@@ -23,7 +23,15 @@ enum GateClass : int {
     // internal to double-float tile records (counted as GC_REAL): a real gate
     // whose four entries have one magnitude (H and its products with X and Z);
     // the record holds q11 and q21 and the signs s1 = q12/q11, s3 = q22/q21
-    GC_REAL_BAL = 6
+    GC_REAL_BAL = 6,
+    // internal to double-float tile records (counted as GC_GENERAL): a
+    // single-qubit unitary written as  U = K diag(1, z) [[1, t], [-t, 1]] diag(1, y)
+    // (GC_PRP) or, when |q12| > |q11|, as that form times X (GC_PRP_X: the pair
+    // is swapped first).  The record holds y (doubles 0, 1), the real t
+    // (double 2, 0 <= t <= 1) and z (doubles 4, 5); the complex scalar K is
+    // left out and multiplied into another update of the same pass (plan.cu).
+    GC_PRP = 7,
+    GC_PRP_X = 8
 };
 
 // Operation kinds after lowering the gate records.  OP_PRUN and OP_PDATA occur

@@ -23,6 +23,11 @@ __device__ __forceinline__ void df_pair_update(const float* c, float4& a, float4
         const float4 a2 = df_bal(c, 0, c[2], a, b);
         const float4 b2 = df_bal(c, 4, c[10], a, b);
         a = a2; b = b2;
+    } else if constexpr (CLS == GC_PRP) {
+        df_prp(c, a, b);
+    } else if constexpr (CLS == GC_PRP_X) {
+        df_prp(c, b, a);  // U = U' X: the pair enters swapped, U' = PRP
+        const float4 t = a; a = b; b = t;
     } else if constexpr (CLS == GC_DIAG) {
         a = df_cmul(c, 0, 1, a);
         b = df_cmul(c, 6, 7, b);
@@ -219,6 +224,8 @@ __device__ __forceinline__ void df_tile_pairs(float4* sm, uint32_t N, int cls, i
         case GC_GENERAL: df_tile_1q_any<GC_GENERAL, THREADS, B, L>(sm, N, tb, c); break;
         case GC_REAL: df_tile_1q_any<GC_REAL, THREADS, B, L>(sm, N, tb, c); break;
         case GC_REAL_BAL: df_tile_1q_any<GC_REAL_BAL, THREADS, B, L>(sm, N, tb, c); break;
+        case GC_PRP: df_tile_1q_any<GC_PRP, THREADS, B, L>(sm, N, tb, c); break;
+        case GC_PRP_X: df_tile_1q_any<GC_PRP_X, THREADS, B, L>(sm, N, tb, c); break;
         case GC_DIAG: df_tile_1q_any<GC_DIAG, THREADS, B, L>(sm, N, tb, c); break;
         case GC_DIAG1: df_tile_1q_any<GC_DIAG1, THREADS, B, L>(sm, N, tb, c); break;
         case GC_ANTIDIAG: df_tile_1q_any<GC_ANTIDIAG, THREADS, B, L>(sm, N, tb, c); break;

@@ -19,6 +19,7 @@ QS_G_U1, QS_G_CU, QS_G_SWAP, QS_G_RX, QS_G_RY, QS_G_RZ = range(6)
 QS_P_Z, QS_P_ZZ, QS_P_X = range(3)
 PLAN_DEFAULT, PLAN_NO_FUSION, PLAN_GRAPH, PLAN_ARITH_F64, PLAN_DRY_RUN, PLAN_NO_MERGE = 0, 1, 2, 4, 8, 16
 PLAN_NO_PHASE_RUNS = 32
+PLAN_NO_PRP = 64
 
 _STATUS = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EDTYPE"}
 
@@ -62,6 +63,7 @@ _SIGS = {
     "qs_plan_device_ops": [_vp, ctypes.POINTER(ctypes.c_int)],
     "qs_plan_pass_op_counts": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "qs_plan_pass_balanced": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "qs_plan_pass_prp": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "qs_plan_set_timing": [_vp, ctypes.c_int],
     "qs_plan_pass_times": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)],
     "qs_plan_destroy": [_vp],
@@ -308,6 +310,13 @@ class Plan:
         buf = (ctypes.c_int * 2)()
         _check(load().qs_plan_pass_balanced(self._h, i, buf))
         return int(buf[0]), int(buf[1])
+
+    def prp(self, i):
+        """General single-qubit updates of pass i applied in phase-shear-phase form
+        (complex128 double-float plans; see QS_PLAN_NO_PRP)."""
+        out = ctypes.c_int()
+        _check(load().qs_plan_pass_prp(self._h, i, ctypes.byref(out)))
+        return int(out.value)
 
     def close(self):
         if self._h is not None and self._h.value:

@@ -699,3 +699,87 @@ def test_random_shapes_against_oracle(qs, dt):
             p.close()
         err = float(np.max(np.abs(got - want)))
         assert err < 5 * TOL[dt], (case, n, b, b0, err)
+
+
+def _general_heavy_circuit(n, seed, count=300):
+    """General single-qubit gates of every shape the phase-shear-phase form meets:
+    Haar unitaries (|q11| >= |q12| and the swapped case), nearly diagonal and nearly
+    anti-diagonal unitaries, general matrices that are not unitary (kept as full
+    products), diagonal gates (which take a pass's scalar), controlled gates, and a
+    long block of unitaries on the lowest qubits (one pass whose scalars would
+    multiply below 2^-24)."""
+    rng = G.SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        q = rng.randint(n)
+        w = rng.randint(9)
+        u = G.haar_2x2(rng)
+        if w <= 2:
+            out.append(G.gate_u1(q, u))
+        elif w == 3:  # nearly diagonal: Haar phases around a tiny rotation
+            e = 10.0 ** -(3 + rng.randint(9))
+            c, s = np.cos(e), np.sin(e)
+            p, r = np.exp(1j * rng.uniform_range(0, 6.28)), np.exp(1j * rng.uniform_range(0, 6.28))
+            out.append(G.gate_u1(q, (p * c, -p * s * r, s, c * r)))
+        elif w == 4:  # nearly anti-diagonal
+            e = 10.0 ** -(3 + rng.randint(9))
+            c, s = np.cos(e), np.sin(e)
+            p = np.exp(1j * rng.uniform_range(0, 6.28))
+            out.append(G.gate_u1(q, (s * p, c, -c * p, s)))
+        elif w == 5:  # not unitary
+            out.append(G.gate_u1(q, tuple(0.8 * z for z in u[:3]) + (u[3],)))
+        elif w == 6:
+            out.append(G.gate_u1(q, (np.exp(-0.3j * (1 + q)), 0.0, 0.0, np.exp(0.7j))))
+        elif n > 1:
+            c = (q + 1 + rng.randint(n - 1)) % n
+            out.append(G.gate_cu(c, q, u))
+    m = min(n, 4)
+    lows = []
+    for k in range(160):  # a controlled X on the same qubit keeps neighbours from merging
+        lows.append(G.gate_u1(k % m, G.haar_2x2(rng)))
+        if m > 1:
+            lows.append(G.gate_cu((k + 1) % m, k % m, G.MAT_X))
+    return G.concat(out[: count // 2] + lows + out[count // 2:])
+
+
+@pytest.mark.parametrize("n,tile_bits", [(3, 0), (8, 5), (14, 0), (14, 10 | (2 << 8)), (18, 0)])
+def test_prp_form_matches_full_products_and_oracle(qs, n, tile_bits):
+    """complex128 tile passes apply general single-qubit unitaries as phase, shear,
+    phase with the pass's scalars multiplied into one other update: the state
+    matches the oracle and the plan with full complex products (PLAN_NO_PRP)."""
+    dt = qs.QS_C128
+    gates = G.concat([_general_heavy_circuit(n, 7070 + n), G.random_circuit(n, 200, 7171 + n)[0]])
+    psi = rand_state(n, 23)
+    want = O.run(expected_input(psi, dt), gates)
+    got, prp = {}, {}
+    for flags in (qs.PLAN_DEFAULT, qs.PLAN_NO_PRP):
+        with upload(qs, n, dt, psi) as s:
+            p = s.plan(gates, flags=flags, tile_bits=tile_bits)
+            prp[flags] = sum(p.prp(i) for i in range(p.stats()["passes"]))
+            p.execute()
+            got[flags] = s.to_numpy()
+            p.close()
+        assert np.max(np.abs(got[flags] - want)) < 5 * TOL[dt], flags
+    assert prp[qs.PLAN_DEFAULT] > 0 and prp[qs.PLAN_NO_PRP] == 0
+    assert np.max(np.abs(got[qs.PLAN_DEFAULT] - got[qs.PLAN_NO_PRP])) < 5 * TOL[dt]
+
+
+@pytest.mark.parametrize("n", [10, 20])
+def test_prp_form_norm_and_closed_form(qs, n):
+    """A circuit of general unitaries followed by its inverse returns the input
+    (complex128, phase-shear-phase form), and the norm stays 1."""
+    dt = qs.QS_C128
+    fwd = _general_heavy_circuit(n, 7272 + n, count=400)
+    col0 = fwd["m"][:, 0] ** 2 + fwd["m"][:, 1] ** 2 + fwd["m"][:, 4] ** 2 + fwd["m"][:, 5] ** 2
+    fwd = fwd[(fwd["kind"] != G.G_U1) | (np.abs(col0 - 1.0) < 1e-9)]  # unitary gates only
+    gates = G.concat([fwd, G.inverse_circuit(fwd)])
+    psi = rand_state(n, 29)
+    with upload(qs, n, dt, psi) as s:
+        p = s.plan(gates)
+        assert sum(p.prp(i) for i in range(p.stats()["passes"])) > 0
+        p.execute()
+        got = s.to_numpy()
+        nrm = s.norm()
+        p.close()
+    assert np.max(np.abs(got - expected_input(psi, dt))) < 5 * TOL[dt]
+    assert abs(nrm - 1.0) < 1e-12

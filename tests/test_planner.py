@@ -231,3 +231,37 @@ def test_random_plans_are_valid_reorderings():
         st.close()
 
     check()
+
+
+def test_prp_counts_keeper_and_scale_bound():
+    """complex128 plans apply general single-qubit unitaries in phase-shear-phase
+    form except one per pass that takes the pass's scalars (when no diagonal,
+    anti-diagonal or non-unitary general update can); non-unitary matrices keep
+    the full product; the scalars' product stays above 2^-24; complex64 plans and
+    PLAN_NO_PRP apply none."""
+    rng = G.SplitMix64(5)
+    st = fake_state(10, qs.QS_C128)
+    haar = [G.gate_u1(q, G.haar_2x2(rng)) for q in range(5)]
+
+    def counts(gates, flags=0, state=st):
+        p = qs.Plan(state, G.concat(gates), flags=qs.PLAN_DRY_RUN | flags)
+        n = p.stats()["passes"]
+        out = (n, sum(p.prp(i) for i in range(n)), sum(int(p.op_counts(i)[0][0]) for i in range(n)))
+        p.close()
+        return out
+
+    assert counts(haar) == (1, 4, 5)
+    diag = G.gate_u1(7, (np.exp(0.3j), 0.0, 0.0, np.exp(-0.2j)))
+    assert counts(haar + [diag]) == (1, 5, 5)
+    bad = G.gate_u1(6, (0.5, 0.5j, 0.5, 0.4))  # not unitary: keeps the full product and takes the scalars
+    assert counts(haar + [bad]) == (1, 5, 6)
+    assert counts(haar + [diag], flags=qs.PLAN_NO_PRP)[1] == 0
+    assert counts(haar + [diag], state=fake_state(10, qs.QS_C64))[1] == 0
+    # 160 unitaries on qubits 0..3 that cannot merge (a controlled X between
+    # neighbours on the same qubit): one pass, some kept general by the bound
+    long = []
+    for k in range(160):
+        long.append(G.gate_u1(k % 4, G.haar_2x2(rng)))
+        long.append(G.gate_cu((k + 1) % 4, k % 4, G.MAT_X))
+    n, prp, general = counts(long + [diag])
+    assert n == 1 and general == 160 and 40 <= prp < 159
