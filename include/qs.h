@@ -161,7 +161,12 @@ enum {
                                into one other single-qubit update of the pass (a diagonal,
                                anti-diagonal or general one, whose cost does not change), so
                                the pass applies the same product.  Taken only where the form
-                               reproduces U to 4e-15 in every entry (unitary U). */
+                               reproduces U to 4e-15 in every entry (unitary U).  Likewise a
+                               real single-qubit gate whose four entries share one magnitude
+                               (H, HX, XH, ZH, ...), q11 [[1, s1], [r, r s3]] with signs s1,
+                               r, s3, is applied as the bracket (two exact sums and no product
+                               per component) with q11 left out.  The scalars left out of one
+                               pass multiply to at least 2^-24. */
 };
 
 /* Build an execution plan for `gates` (copied in) on state s: gate classes,
@@ -209,10 +214,12 @@ QS_API qs_status qs_plan_pass_op_counts(const qs_plan* p, int i, int* counts);
  * other plans. */
 QS_API qs_status qs_plan_pass_balanced(const qs_plan* p, int i, int* counts);
 
-/* Of pass i's general single-qubit updates (class 0 above), how many the
- * complex128 double-float kernel applies in the phase-shear-phase form of
- * QS_PLAN_NO_PRP: *count.  Zero for other plans. */
-QS_API qs_status qs_plan_pass_prp(const qs_plan* p, int i, int* count);
+/* Single-qubit updates of pass i that the complex128 double-float kernel
+ * applies with a scalar left out (QS_PLAN_NO_PRP): counts[0] general ones
+ * (class 0 above) in phase-shear-phase form, counts[1] real ones (class 1,
+ * not counted by qs_plan_pass_balanced) as a signed sum without q11.  Zero
+ * for other plans. */
+QS_API qs_status qs_plan_pass_prp(const qs_plan* p, int i, int* counts);
 
 /* Per-pass description: for pass i, its kind (0 = single gate, 1 = tile),
  * first gate and gate count in plan order, and the tile's qubit mask. */

@@ -45,7 +45,7 @@ struct PlanPass {
     std::vector<int> members;  // circuit positions of the pass's gates, in execution order
     int op_counts[3][6];       // ops the kernel applies, by kind (1q, controlled, swap) and class
     int balanced[2];           // of the real ones: balanced (H-like) single-qubit / controlled records
-    int prp;                   // of the general single-qubit ones: phase-shear-phase records
+    int forms[2];              // single-qubit records that leave a scalar out: phase-shear-phase, balanced real
 };
 
 inline int popc(uint64_t x) { return __builtin_popcountll(x); }
@@ -214,46 +214,72 @@ TileOpDF prp_record(const Op& o, const PrpForm& f, const int* bit_of) {
     return r;
 }
 
-// Which single-qubit ops of one pass (after fusion) become phase-shear-phase
-// records, and the op (keeper) that takes the product of their scalars K: a
-// diagonal, anti-diagonal or general update whose class and cost a complex
-// scale leaves unchanged, else the last candidate, which then stays general.
-// Candidates whose K would bring the product below kPrpMinScale stay general,
-// so the amplitudes inside the pass grow by less than 2^24.
-int choose_prp(const std::vector<Op>& ops, std::vector<PrpForm>& forms, std::vector<char>& as_prp,
-               double* Kpass) {
+// A balanced real single-qubit gate whose four entries share one magnitude
+// (H, HX, XH, ZH, ...) = q11 [[1, s1], [r, r s3]] with s1, r, s3 = +-1: the
+// record applies the bracket, the scalar q11 is left out like K above.
+bool bal1_form(const Op& o) {
+    const double a = std::fabs(o.m[0]);
+    return o.kind == OP_1Q && o.cls == GC_REAL && a != 0.0 && std::fabs(o.m[2]) == a && std::fabs(o.m[4]) == a &&
+           std::fabs(o.m[6]) == a;
+}
+
+TileOpDF bal1_record(const Op& o, const int* bit_of) {
+    TileOpDF r{};
+    fill_common(r, o, bit_of);
+    r.cls = GC_REAL_BAL1;
+    r.c[2] = (o.m[2] == o.m[0]) ? 1.0f : -1.0f;   // s1 = q12 / q11
+    r.c[10] = (o.m[6] == o.m[4]) ? 1.0f : -1.0f;  // s3 = q22 / q21
+    r.c[8] = (o.m[4] == o.m[0]) ? 1.0f : -1.0f;   // r = q21 / q11
+    return r;
+}
+
+// Forms of the single-qubit ops of one pass (after fusion) that leave a
+// scalar out: 1 = phase-shear-phase (scalar K), 2 = balanced real without q11;
+// 0 = as given.  Returns the op (keeper) that takes the product of the
+// scalars left out: a diagonal, anti-diagonal or general update whose class
+// and cost a complex scale leaves unchanged; else the last phase-shear-phase
+// candidate, which then stays general; else (real scalars only) the last
+// balanced candidate, which keeps its scalar times the product.  Candidates
+// whose scalar would bring the product below kPrpMinScale keep their own, so
+// the amplitudes inside the pass grow by less than 2^24.  -1: no form taken.
+int choose_forms(const std::vector<Op>& ops, bool balanced, std::vector<PrpForm>& forms, std::vector<char>& form,
+                 double* Kpass) {
     forms.assign(ops.size(), PrpForm{});
-    as_prp.assign(ops.size(), 0);
+    form.assign(ops.size(), 0);
     Kpass[0] = 1.0;
     Kpass[1] = 0.0;
-    int keeper = -1, last = -1;
+    int keeper = -1, last_prp = -1, last_bal = -1;
     for (size_t i = 0; i < ops.size(); ++i) {
         if (prp_form(ops[i], forms[i])) {
-            as_prp[i] = 1;
-            last = (int)i;
+            form[i] = 1;
+            last_prp = (int)i;
+        } else if (balanced && bal1_form(ops[i])) {
+            form[i] = 2;
+            last_bal = (int)i;
         }
     }
-    if (last < 0) return -1;
+    if (last_prp < 0 && last_bal < 0) return -1;
     for (size_t i = 0; i < ops.size() && keeper < 0; ++i) {
         const Op& o = ops[i];
-        if (o.kind == OP_1Q && !as_prp[i] && (o.cls == GC_DIAG || o.cls == GC_ANTIDIAG || o.cls == GC_GENERAL))
+        if (o.kind == OP_1Q && !form[i] && (o.cls == GC_DIAG || o.cls == GC_ANTIDIAG || o.cls == GC_GENERAL))
             keeper = (int)i;
     }
     if (keeper < 0) {
-        keeper = last;
-        as_prp[last] = 0;
+        keeper = last_prp >= 0 ? last_prp : last_bal;
+        form[keeper] = 0;
     }
     double mag = 1.0;
     int used = 0;
     for (size_t i = 0; i < ops.size(); ++i) {
-        if (!as_prp[i]) continue;
-        const double k = std::hypot(forms[i].K[0], forms[i].K[1]);
+        if (!form[i]) continue;
+        const double kr = form[i] == 1 ? forms[i].K[0] : ops[i].m[0], ki = form[i] == 1 ? forms[i].K[1] : 0.0;
+        const double k = std::hypot(kr, ki);
         if (mag * k < kPrpMinScale) {
-            as_prp[i] = 0;
+            form[i] = 0;
             continue;
         }
         mag *= k;
-        cmul_acc(Kpass, forms[i].K[0], forms[i].K[1]);
+        cmul_acc(Kpass, kr, ki);
         ++used;
     }
     return used > 0 ? keeper : -1;
@@ -478,10 +504,11 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
         pp.moves_only = true;
         const bool runs = !(p->flags & QS_PLAN_NO_PHASE_RUNS);
         std::vector<PrpForm> forms;
-        std::vector<char> as_prp;
+        std::vector<char> form;
         double Kpass[2] = {1.0, 0.0};
-        const int keeper = (df && !(p->flags & QS_PLAN_NO_PRP)) ? choose_prp(fused, forms, as_prp, Kpass) : -1;
-        if (keeper < 0) as_prp.assign(fused.size(), 0);
+        const int keeper =
+            (df && !(p->flags & QS_PLAN_NO_PRP)) ? choose_forms(fused, true, forms, form, Kpass) : -1;
+        if (keeper < 0) form.assign(fused.size(), 0);
         for (size_t i = 0; i < fused.size();) {
             int pivot = -1;
             const size_t len = runs ? find_phase_run(fused, i, d.bit_of, p->s->dt, pivot) : 0;
@@ -500,10 +527,10 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
             Op o = fused[at];
             pp.op_counts[o.kind][o.cls] += 1;
             if constexpr (std::is_same<OpT, TileOpDF>::value) {
-                if (as_prp[at]) {
-                    tops.push_back(prp_record(o, forms[at], d.bit_of));
+                if (form[at]) {
+                    tops.push_back(form[at] == 1 ? prp_record(o, forms[at], d.bit_of) : bal1_record(o, d.bit_of));
                     t64.push_back(to_tile_op<TileOp<double>>(o, d.bit_of));
-                    pp.prp += 1;
+                    pp.forms[form[at] - 1] += 1;
                     pp.moves_only = false;
                     p->device_ops += 1;
                     continue;
@@ -788,10 +815,11 @@ qs_status qs_plan_pass_balanced(const qs_plan* p, int i, int* counts) {
     return QS_OK;
 }
 
-qs_status qs_plan_pass_prp(const qs_plan* p, int i, int* count) {
-    if (!p || !count) return fail(QS_EINVAL, "NULL argument");
+qs_status qs_plan_pass_prp(const qs_plan* p, int i, int* counts) {
+    if (!p || !counts) return fail(QS_EINVAL, "NULL argument");
     if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
-    *count = p->passes[i].prp;
+    counts[0] = p->passes[i].forms[0];
+    counts[1] = p->passes[i].forms[1];
     return QS_OK;
 }
 

@@ -31,7 +31,12 @@ enum GateClass : int {
     // (double 2, 0 <= t <= 1) and z (doubles 4, 5); the complex scalar K is
     // left out and multiplied into another update of the same pass (plan.cu).
     GC_PRP = 7,
-    GC_PRP_X = 8
+    GC_PRP_X = 8,
+    // internal to double-float tile records (counted as GC_REAL): a balanced
+    // real gate whose four entries share one magnitude, applied without its
+    // scalar q11 (multiplied into another update of the pass, like K above):
+    // a' = a + s1 b, b' = r (a + s3 b) with s1 = c[2], s3 = c[10], r = q21/q11 = c[8]
+    GC_REAL_BAL1 = 9
 };
 
 // Operation kinds after lowering the gate records.  OP_PRUN and OP_PDATA occur

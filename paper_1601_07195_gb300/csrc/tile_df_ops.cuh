@@ -23,6 +23,12 @@ __device__ __forceinline__ void df_pair_update(const float* c, float4& a, float4
         const float4 a2 = df_bal(c, 0, c[2], a, b);
         const float4 b2 = df_bal(c, 4, c[10], a, b);
         a = a2; b = b2;
+    } else if constexpr (CLS == GC_REAL_BAL1) {  // signs in c[2], c[10], c[8]
+        const dfl ar = df_addsig(a.x, a.y, c[2], b.x, b.y), ai = df_addsig(a.z, a.w, c[2], b.z, b.w);
+        const dfl br = df_addsig(a.x, a.y, c[10], b.x, b.y), bi = df_addsig(a.z, a.w, c[10], b.z, b.w);
+        const float r = c[8];
+        a = make_float4(ar.h, ar.l, ai.h, ai.l);
+        b = make_float4(r * br.h, r * br.l, r * bi.h, r * bi.l);
     } else if constexpr (CLS == GC_PRP) {
         df_prp(c, a, b);
     } else if constexpr (CLS == GC_PRP_X) {
@@ -224,6 +230,7 @@ __device__ __forceinline__ void df_tile_pairs(float4* sm, uint32_t N, int cls, i
         case GC_GENERAL: df_tile_1q_any<GC_GENERAL, THREADS, B, L>(sm, N, tb, c); break;
         case GC_REAL: df_tile_1q_any<GC_REAL, THREADS, B, L>(sm, N, tb, c); break;
         case GC_REAL_BAL: df_tile_1q_any<GC_REAL_BAL, THREADS, B, L>(sm, N, tb, c); break;
+        case GC_REAL_BAL1: df_tile_1q_any<GC_REAL_BAL1, THREADS, B, L>(sm, N, tb, c); break;
         case GC_PRP: df_tile_1q_any<GC_PRP, THREADS, B, L>(sm, N, tb, c); break;
         case GC_PRP_X: df_tile_1q_any<GC_PRP_X, THREADS, B, L>(sm, N, tb, c); break;
         case GC_DIAG: df_tile_1q_any<GC_DIAG, THREADS, B, L>(sm, N, tb, c); break;

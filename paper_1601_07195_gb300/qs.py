@@ -311,12 +311,17 @@ class Plan:
         _check(load().qs_plan_pass_balanced(self._h, i, buf))
         return int(buf[0]), int(buf[1])
 
+    def scalar_free(self, i):
+        """(general, real) single-qubit updates of pass i applied with a scalar left
+        out: phase-shear-phase form and balanced real without q11 (complex128
+        double-float plans; see QS_PLAN_NO_PRP)."""
+        buf = (ctypes.c_int * 2)()
+        _check(load().qs_plan_pass_prp(self._h, i, buf))
+        return int(buf[0]), int(buf[1])
+
     def prp(self, i):
-        """General single-qubit updates of pass i applied in phase-shear-phase form
-        (complex128 double-float plans; see QS_PLAN_NO_PRP)."""
-        out = ctypes.c_int()
-        _check(load().qs_plan_pass_prp(self._h, i, ctypes.byref(out)))
-        return int(out.value)
+        """General single-qubit updates of pass i applied in phase-shear-phase form."""
+        return self.scalar_free(i)[0]
 
     def close(self):
         if self._h is not None and self._h.value:

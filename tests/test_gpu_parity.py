@@ -783,3 +783,45 @@ def test_prp_form_norm_and_closed_form(qs, n):
         p.close()
     assert np.max(np.abs(got - expected_input(psi, dt))) < 5 * TOL[dt]
     assert abs(nrm - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("n", [5, 13, 20])
+def test_balanced_without_scalar_closed_form_and_oracle(qs, n):
+    """complex128 tile passes apply H-like gates without their scalar 1/sqrt(2)
+    (multiplied into one update per pass): H on every qubit of |0> gives the
+    uniform state 2^(-n/2) (a pass holding only H gates: the last keeps the
+    scalar of all); layers of H, HX, XH, ZH with CZ, CNOT and T match the oracle
+    and the plan that keeps every scalar (PLAN_NO_PRP)."""
+    dt = qs.QS_C128
+    layer = G.concat([G.gate_u1(q, G.MAT_H) for q in range(n)])
+    with upload(qs, n, dt, np.eye(1, 1 << n, 0, dtype=np.complex128)[0]) as s:
+        p = s.plan(layer)
+        assert sum(p.scalar_free(i)[1] for i in range(p.stats()["passes"])) > 0
+        p.execute()
+        got = s.to_numpy()
+        p.close()
+    assert np.max(np.abs(got - 2.0 ** (-n / 2))) < TOL[dt]
+    h = G.MAT_H
+    shapes = [h, (h[1], h[0], h[3], h[2]), (h[2], h[3], h[0], h[1]), (h[0], h[1], -h[2], -h[3])]
+    rng = G.SplitMix64(606 + n)
+    out = []
+    for _ in range(12):
+        for q in range(n):
+            out.append(G.gate_u1(q, shapes[rng.randint(4)]))
+        for _ in range(n):
+            a = rng.randint(n)
+            b = (a + 1 + rng.randint(n - 1)) % n
+            w = rng.randint(3)
+            out.append(G.gate_cu(a, b, (1.0, 0.0, 0.0, -1.0)) if w == 0 else
+                       G.gate_cu(a, b, G.MAT_X) if w == 1 else G.gate_u1(a, G.MAT_T))
+    gates = G.concat(out)
+    psi = rand_state(n, 31)
+    want = O.run(expected_input(psi, dt), gates)
+    res = {}
+    for flags in (qs.PLAN_DEFAULT, qs.PLAN_NO_PRP):
+        with upload(qs, n, dt, psi) as s:
+            p = s.plan(gates, flags=flags)
+            p.execute()
+            res[flags] = s.to_numpy()
+            p.close()
+        assert np.max(np.abs(res[flags] - want)) < 5 * TOL[dt], flags

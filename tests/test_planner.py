@@ -160,7 +160,13 @@ def test_balanced_real_counts():
         real = sum(int(p.op_counts(i)[0][1]) + int(p.op_counts(i)[1][1]) for i in range(p.stats()["passes"]))
         return tuple(int(v) for v in bal), real
 
-    assert totals(qs.QS_C128) == ((3, 1), 5)  # 3 single-qubit + 1 controlled H-like, plus RY
+    # 3 single-qubit + 1 controlled H-like, plus RY
+    assert totals(qs.QS_C128, qs.PLAN_NO_PRP) == ((3, 1), 5)
+    # by default two of the single-qubit ones leave their scalar out (qs_plan_pass_prp),
+    # the third keeps it times theirs
+    assert totals(qs.QS_C128) == ((1, 1), 5)
+    p = qs.Plan(fake_state(n, qs.QS_C128), gates, theta, flags=qs.PLAN_DRY_RUN | qs.PLAN_NO_MERGE)
+    assert sum(p.scalar_free(i)[1] for i in range(p.stats()["passes"])) == 2
     assert totals(qs.QS_C64)[0] == (0, 0)
     assert totals(qs.QS_C128, qs.PLAN_ARITH_F64)[0] == (0, 0)
 
@@ -265,3 +271,30 @@ def test_prp_counts_keeper_and_scale_bound():
         long.append(G.gate_cu((k + 1) % 4, k % 4, G.MAT_X))
     n, prp, general = counts(long + [diag])
     assert n == 1 and general == 160 and 40 <= prp < 159
+
+
+def test_balanced_without_scalar_counts():
+    """H-like gates (four entries of one magnitude) leave q11 out in complex128
+    plans: all of them when a general or diagonal update of the pass takes the
+    scalars, all but the last when only they are present (it keeps its scalar
+    times the others'); gates whose rows differ in magnitude keep theirs."""
+    st = fake_state(10, qs.QS_C128)
+    H = G.MAT_H
+    hx = (G.MAT_H[1], G.MAT_H[0], G.MAT_H[3], G.MAT_H[2])  # H X
+    rows = (0.6, 0.6, 0.8, -0.8)  # balanced, rows of different magnitude
+
+    def forms(gates, flags=0):
+        p = qs.Plan(st, G.concat(gates), flags=qs.PLAN_DRY_RUN | flags)
+        n = p.stats()["passes"]
+        out = (n, [sum(p.scalar_free(i)[k] for i in range(n)) for k in range(2)],
+               sum(p.balanced(i)[0] for i in range(n)))
+        p.close()
+        return out
+
+    hs = [G.gate_u1(q, H) for q in range(5)] + [G.gate_u1(5, hx)]
+    assert forms(hs) == (1, [0, 5], 1)
+    diag = G.gate_u1(7, (np.exp(0.3j), 0.0, 0.0, np.exp(-0.2j)))
+    assert forms(hs + [diag]) == (1, [0, 6], 0)
+    assert forms(hs + [G.gate_u1(8, G.haar_2x2(G.SplitMix64(3)))]) == (1, [0, 6], 0)
+    assert forms(hs + [G.gate_u1(6, rows)]) == (1, [0, 5], 2)
+    assert forms(hs, flags=qs.PLAN_NO_PRP) == (1, [0, 0], 6)
