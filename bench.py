@@ -98,12 +98,14 @@ _DF_FLOPS_PRP = 74.0
 # a balanced real gate without its scalar (qs_plan_pass_prp counts[1]): per component
 # an exact signed sum (10), times +-1 for the second row (1 more): 44 per pair, 22 per amplitude
 _DF_FLOPS_BALANCED_FREE = 22.0
+# phase-shear-phase without the trailing product by z (qs_plan_pass_prp counts[2]): 148 - 44 per pair
+_DF_FLOPS_PRP_NZ = 52.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 # DRAM bytes (read + write) of one double-float tile launch, from the ncu capture
 # of the n=26 case (profiles/k_tile_df_c128_n26_full.md); a tile pass reads and
 # writes the whole state once, so traffic scales with 2^n.  Update (or set to
 # None) whenever the kernel changes.
-DF_TILE_TRAFFIC_N26 = 1.074085e9 + 1.012289e9
+DF_TILE_TRAFFIC_N26 = 1.073906e9 + 1.012308e9
 # the same for the complex64 tile kernel, one n=27 launch (profiles/k_tile_c64_n27_full.md)
 C64_TILE_TRAFFIC_N27 = 1.074006e9 + 1.012051e9
 
@@ -397,8 +399,9 @@ def run_ours(args):
         for i in tile_idx:
             b1, bc = plan.balanced(i)
             fp32_flops -= (_DF_FLOPS["real"] - _DF_FLOPS_BALANCED) * N * (b1 + 0.5 * bc)
-            prp, bal_free = plan.scalar_free(i)
+            prp, bal_free, prp_nz = plan.scalar_free(i)
             fp32_flops -= (_DF_FLOPS["general"] - _DF_FLOPS_PRP) * N * prp
+            fp32_flops -= (_DF_FLOPS_PRP - _DF_FLOPS_PRP_NZ) * N * prp_nz
             fp32_flops -= (_DF_FLOPS["real"] - _DF_FLOPS_BALANCED_FREE) * N * bal_free
     achieved_tf = fp32_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
     roofline = {"bound": "alu", "kernel": "k_tile_df (fused tile pass, double-float)" if df else "k_tile_p<float, 12> (fused tile pass, FP32)",
@@ -415,7 +418,8 @@ def run_ours(args):
                 "flops_counted": ("FP32 flops of the double-float updates the kernel applies (after in-pass "
                                   "fusion of same-qubit gates) per touched amplitude: general 104, "
                                   "real/diagonal/anti-diagonal 44, balanced real (H-like) 34 or 22 without its scalar, "
-                                  "general single-qubit in phase-shear-phase form 74, permutation 0; a fused phase "
+                                  "general single-qubit in phase-shear-phase form 74 or 52 without its "
+                                  "trailing phase, permutation 0; a fused phase "
                                   "run counts as one diagonal update") if df else
                                  "FP32 flops of the updates the kernel applies",
                 "fp64_equivalent_tflops": fp64_tf,

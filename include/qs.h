@@ -217,8 +217,11 @@ QS_API qs_status qs_plan_pass_balanced(const qs_plan* p, int i, int* counts);
 /* Single-qubit updates of pass i that the complex128 double-float kernel
  * applies with a scalar left out (QS_PLAN_NO_PRP): counts[0] general ones
  * (class 0 above) in phase-shear-phase form, counts[1] real ones (class 1,
- * not counted by qs_plan_pass_balanced) as a signed sum without q11.  Zero
- * for other plans. */
+ * not counted by qs_plan_pass_balanced) as a signed sum without q11,
+ * counts[2] of counts[0] those whose trailing phase diag(1, z) a later update
+ * of the pass on the same qubit took into its matrix (a general, diagonal or
+ * anti-diagonal single-qubit update, with only updates that commute with the
+ * phase in between), so they skip that product.  Zero for other plans. */
 QS_API qs_status qs_plan_pass_prp(const qs_plan* p, int i, int* counts);
 
 /* Per-pass description: for pass i, its kind (0 = single gate, 1 = tile),

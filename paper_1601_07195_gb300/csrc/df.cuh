@@ -157,7 +157,9 @@ __device__ __forceinline__ float4 df_bal(const float* c, int j, float s, float4 
 }
 
 // phase, shear, phase (GC_PRP): bt = y b; a' = a + t bt; b' = z (bt - t a),
-// with y = doubles (0, 1), the real t = double 2, z = doubles (4, 5)
+// with y = doubles (0, 1), the real t = double 2, z = doubles (4, 5); Z = false
+// leaves out the product by z (z = 1, GC_PRP_NZ)
+template <bool Z>
 __device__ __forceinline__ void df_prp(const float* c, float4& a, float4& b) {
     const float4 bt = df_cmul(c, 0, 1, b);
     const dfl ar = df_dot2({a.x, a.y}, df_mul(QH(2), QL(2), bt.x, bt.y));
@@ -165,7 +167,8 @@ __device__ __forceinline__ void df_prp(const float* c, float4& a, float4& b) {
     const dfl br = df_dot2({bt.x, bt.y}, df_mul(-QH(2), -QL(2), a.x, a.y));
     const dfl bi = df_dot2({bt.z, bt.w}, df_mul(-QH(2), -QL(2), a.z, a.w));
     a = make_float4(ar.h, ar.l, ai.h, ai.l);
-    b = df_cmul(c, 4, 5, make_float4(br.h, br.l, bi.h, bi.l));
+    if constexpr (Z) b = df_cmul(c, 4, 5, make_float4(br.h, br.l, bi.h, bi.l));
+    else b = make_float4(br.h, br.l, bi.h, bi.l);
 }
 
 #undef QH

@@ -45,7 +45,8 @@ struct PlanPass {
     std::vector<int> members;  // circuit positions of the pass's gates, in execution order
     int op_counts[3][6];       // ops the kernel applies, by kind (1q, controlled, swap) and class
     int balanced[2];           // of the real ones: balanced (H-like) single-qubit / controlled records
-    int forms[2];              // single-qubit records that leave a scalar out: phase-shear-phase, balanced real
+    int forms[3];              // single-qubit records that leave a scalar out: phase-shear-phase, balanced
+                               // real; and of the first, those whose trailing phase a later op took
 };
 
 inline int popc(uint64_t x) { return __builtin_popcountll(x); }
@@ -155,7 +156,8 @@ void cdiv(double ar, double ai, double br, double bi, double& r, double& i) {
     i = (ai * br - ar * bi) / d;
 }
 
-bool prp_form(const Op& o, PrpForm& f) {
+// unit_z: take z = 1 exactly (an op whose trailing phase a later op has taken)
+bool prp_form(const Op& o, PrpForm& f, bool unit_z = false) {
     if (o.kind != OP_1Q || o.cls != GC_GENERAL) return false;
     const double* m = o.m;
     f.swap = std::hypot(m[2], m[3]) > std::hypot(m[0], m[1]);
@@ -174,8 +176,8 @@ bool prp_form(const Op& o, PrpForm& f) {
     if (!(f.t <= 1.0 + 1e-12)) return false;
     double q[2];
     cdiv(v[4], v[5], v[0], v[1], q[0], q[1]);
-    f.z[0] = -q[0] / f.t;
-    f.z[1] = -q[1] / f.t;
+    f.z[0] = unit_z ? 1.0 : -q[0] / f.t;
+    f.z[1] = unit_z ? 0.0 : -q[1] / f.t;
     cdiv(v[6], v[7], v[0], v[1], q[0], q[1]);
     cdiv(q[0], q[1], f.z[0], f.z[1], f.y[0], f.y[1]);
     // the entries the form gives, against V
@@ -205,13 +207,44 @@ bool prp_form(const Op& o, PrpForm& f) {
 TileOpDF prp_record(const Op& o, const PrpForm& f, const int* bit_of) {
     TileOpDF r{};
     fill_common(r, o, bit_of);
-    r.cls = f.swap ? GC_PRP_X : GC_PRP;
+    const bool unit_z = f.z[0] == 1.0 && f.z[1] == 0.0;
+    r.cls = f.swap ? (unit_z ? GC_PRP_X_NZ : GC_PRP_X) : (unit_z ? GC_PRP_NZ : GC_PRP);
     split_to_floats(f.y[0], r.c[0], r.c[1]);
     split_to_floats(f.y[1], r.c[2], r.c[3]);
     split_to_floats(f.t, r.c[4], r.c[5]);
     split_to_floats(f.z[0], r.c[8], r.c[9]);
     split_to_floats(f.z[1], r.c[10], r.c[11]);
     return r;
+}
+
+// The trailing factor diag(1, z) of a phase-shear-phase op on qubit q can move
+// into the next op of the pass that involves q when every op in between
+// commutes with it (controlled ops with q as control, diagonal controlled ops)
+// and that op takes it into its matrix at no cost: a general, diagonal or
+// anti-diagonal single-qubit op on q (U diag(1, z) keeps its class).  Returns
+// that op's index, or -1.
+int phase_taker(const std::vector<Op>& ops, size_t i) {
+    const int q = ops[i].t;
+    for (size_t j = i + 1; j < ops.size(); ++j) {
+        const Op& o = ops[j];
+        if (o.t != q && o.c != q) continue;
+        if (o.kind == OP_1Q)
+            return (o.cls == GC_GENERAL || o.cls == GC_DIAG || o.cls == GC_DIAG1 || o.cls == GC_ANTIDIAG) ? (int)j
+                                                                                                          : -1;
+        if (o.kind == OP_CU && (o.c == q || o.cls == GC_DIAG || o.cls == GC_DIAG1)) continue;
+        return -1;
+    }
+    return -1;
+}
+
+// m := diag(1, conj(z)) m (row 2) or m := m diag(1, z) (column 2)
+void scale_row2(double* m, const double* z) {
+    cmul_acc(&m[4], z[0], -z[1]);
+    cmul_acc(&m[6], z[0], -z[1]);
+}
+void scale_col2(double* m, const double* z) {
+    cmul_acc(&m[2], z[0], z[1]);
+    cmul_acc(&m[6], z[0], z[1]);
 }
 
 // A balanced real single-qubit gate whose four entries share one magnitude
@@ -242,8 +275,13 @@ TileOpDF bal1_record(const Op& o, const int* bit_of) {
 // balanced candidate, which keeps its scalar times the product.  Candidates
 // whose scalar would bring the product below kPrpMinScale keep their own, so
 // the amplitudes inside the pass grow by less than 2^24.  -1: no form taken.
-int choose_forms(const std::vector<Op>& ops, bool balanced, std::vector<PrpForm>& forms, std::vector<char>& form,
-                 double* Kpass) {
+//
+// With pass_phase, a phase-shear-phase op whose trailing phase another op can
+// take (phase_taker) hands it over first: ops[i] becomes diag(1, conj(z)) U_i,
+// whose form has z = 1, and ops[j] becomes U_j diag(1, z), so the product of
+// the pass is unchanged whatever form each op takes afterwards.
+int choose_forms(std::vector<Op>& ops, bool balanced, bool pass_phase, std::vector<PrpForm>& forms,
+                 std::vector<char>& form, double* Kpass) {
     forms.assign(ops.size(), PrpForm{});
     form.assign(ops.size(), 0);
     Kpass[0] = 1.0;
@@ -253,6 +291,20 @@ int choose_forms(const std::vector<Op>& ops, bool balanced, std::vector<PrpForm>
         if (prp_form(ops[i], forms[i])) {
             form[i] = 1;
             last_prp = (int)i;
+            const int j = pass_phase ? phase_taker(ops, i) : -1;
+            if (j >= 0) {
+                const Op keep_i = ops[i], keep_j = ops[(size_t)j];
+                const double z[2] = {forms[i].z[0], forms[i].z[1]};
+                scale_row2(ops[i].m, z);
+                scale_col2(ops[(size_t)j].m, z);
+                PrpForm f;
+                if (prp_form(ops[i], f, true)) {
+                    forms[i] = f;
+                } else {  // the form with z = 1 misses the tolerance: keep both as they were
+                    ops[i] = keep_i;
+                    ops[(size_t)j] = keep_j;
+                }
+            }
         } else if (balanced && bal1_form(ops[i])) {
             form[i] = 2;
             last_bal = (int)i;
@@ -500,14 +552,14 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
         pp.kind = 1;
         pp.tp = d.tp;
         pp.tp.op0 = (int)tops.size();
-        const std::vector<Op> fused = fuse_single_qubit(ops, d.members, p->s->dt, !(p->flags & QS_PLAN_NO_MERGE));
+        std::vector<Op> fused = fuse_single_qubit(ops, d.members, p->s->dt, !(p->flags & QS_PLAN_NO_MERGE));
         pp.moves_only = true;
         const bool runs = !(p->flags & QS_PLAN_NO_PHASE_RUNS);
         std::vector<PrpForm> forms;
         std::vector<char> form;
         double Kpass[2] = {1.0, 0.0};
         const int keeper =
-            (df && !(p->flags & QS_PLAN_NO_PRP)) ? choose_forms(fused, true, forms, form, Kpass) : -1;
+            (df && !(p->flags & QS_PLAN_NO_PRP)) ? choose_forms(fused, true, true, forms, form, Kpass) : -1;
         if (keeper < 0) form.assign(fused.size(), 0);
         for (size_t i = 0; i < fused.size();) {
             int pivot = -1;
@@ -531,6 +583,7 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
                     tops.push_back(form[at] == 1 ? prp_record(o, forms[at], d.bit_of) : bal1_record(o, d.bit_of));
                     t64.push_back(to_tile_op<TileOp<double>>(o, d.bit_of));
                     pp.forms[form[at] - 1] += 1;
+                    if (tops.back().cls == GC_PRP_NZ || tops.back().cls == GC_PRP_X_NZ) pp.forms[2] += 1;
                     pp.moves_only = false;
                     p->device_ops += 1;
                     continue;
@@ -820,6 +873,7 @@ qs_status qs_plan_pass_prp(const qs_plan* p, int i, int* counts) {
     if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
     counts[0] = p->passes[i].forms[0];
     counts[1] = p->passes[i].forms[1];
+    counts[2] = p->passes[i].forms[2];
     return QS_OK;
 }
 

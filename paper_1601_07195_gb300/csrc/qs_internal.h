@@ -36,7 +36,11 @@ enum GateClass : int {
     // real gate whose four entries share one magnitude, applied without its
     // scalar q11 (multiplied into another update of the pass, like K above):
     // a' = a + s1 b, b' = r (a + s3 b) with s1 = c[2], s3 = c[10], r = q21/q11 = c[8]
-    GC_REAL_BAL1 = 9
+    GC_REAL_BAL1 = 9,
+    // GC_PRP / GC_PRP_X with z = 1: the trailing phase diag(1, z) was moved into
+    // a later op of the pass (plan.cu), so the record skips that product
+    GC_PRP_NZ = 10,
+    GC_PRP_X_NZ = 11
 };
 
 // Operation kinds after lowering the gate records.  OP_PRUN and OP_PDATA occur

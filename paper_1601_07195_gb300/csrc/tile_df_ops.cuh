@@ -29,10 +29,10 @@ __device__ __forceinline__ void df_pair_update(const float* c, float4& a, float4
         const float r = c[8];
         a = make_float4(ar.h, ar.l, ai.h, ai.l);
         b = make_float4(r * br.h, r * br.l, r * bi.h, r * bi.l);
-    } else if constexpr (CLS == GC_PRP) {
-        df_prp(c, a, b);
-    } else if constexpr (CLS == GC_PRP_X) {
-        df_prp(c, b, a);  // U = U' X: the pair enters swapped, U' = PRP
+    } else if constexpr (CLS == GC_PRP || CLS == GC_PRP_NZ) {
+        df_prp<CLS == GC_PRP>(c, a, b);
+    } else if constexpr (CLS == GC_PRP_X || CLS == GC_PRP_X_NZ) {
+        df_prp<CLS == GC_PRP_X>(c, b, a);  // U = U' X: the pair enters swapped, U' = PRP
         const float4 t = a; a = b; b = t;
     } else if constexpr (CLS == GC_DIAG) {
         a = df_cmul(c, 0, 1, a);
@@ -233,6 +233,8 @@ __device__ __forceinline__ void df_tile_pairs(float4* sm, uint32_t N, int cls, i
         case GC_REAL_BAL1: df_tile_1q_any<GC_REAL_BAL1, THREADS, B, L>(sm, N, tb, c); break;
         case GC_PRP: df_tile_1q_any<GC_PRP, THREADS, B, L>(sm, N, tb, c); break;
         case GC_PRP_X: df_tile_1q_any<GC_PRP_X, THREADS, B, L>(sm, N, tb, c); break;
+        case GC_PRP_NZ: df_tile_1q_any<GC_PRP_NZ, THREADS, B, L>(sm, N, tb, c); break;
+        case GC_PRP_X_NZ: df_tile_1q_any<GC_PRP_X_NZ, THREADS, B, L>(sm, N, tb, c); break;
         case GC_DIAG: df_tile_1q_any<GC_DIAG, THREADS, B, L>(sm, N, tb, c); break;
         case GC_DIAG1: df_tile_1q_any<GC_DIAG1, THREADS, B, L>(sm, N, tb, c); break;
         case GC_ANTIDIAG: df_tile_1q_any<GC_ANTIDIAG, THREADS, B, L>(sm, N, tb, c); break;

@@ -312,12 +312,13 @@ class Plan:
         return int(buf[0]), int(buf[1])
 
     def scalar_free(self, i):
-        """(general, real) single-qubit updates of pass i applied with a scalar left
-        out: phase-shear-phase form and balanced real without q11 (complex128
-        double-float plans; see QS_PLAN_NO_PRP)."""
-        buf = (ctypes.c_int * 2)()
+        """(general, real, general without the trailing phase) single-qubit updates of
+        pass i applied with a scalar left out: phase-shear-phase form, balanced real
+        without q11, and of the first those whose trailing phase a later update took
+        (complex128 double-float plans; see QS_PLAN_NO_PRP and qs_plan_pass_prp)."""
+        buf = (ctypes.c_int * 3)()
         _check(load().qs_plan_pass_prp(self._h, i, buf))
-        return int(buf[0]), int(buf[1])
+        return int(buf[0]), int(buf[1]), int(buf[2])
 
     def prp(self, i):
         """General single-qubit updates of pass i applied in phase-shear-phase form."""

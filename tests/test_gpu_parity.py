@@ -745,8 +745,9 @@ def _general_heavy_circuit(n, seed, count=300):
 @pytest.mark.parametrize("n,tile_bits", [(3, 0), (8, 5), (14, 0), (14, 10 | (2 << 8)), (18, 0)])
 def test_prp_form_matches_full_products_and_oracle(qs, n, tile_bits):
     """complex128 tile passes apply general single-qubit unitaries as phase, shear,
-    phase with the pass's scalars multiplied into one other update: the state
-    matches the oracle and the plan with full complex products (PLAN_NO_PRP)."""
+    phase with the pass's scalars multiplied into one other update, some handing
+    their trailing phase to a later update: the state matches the oracle and the
+    plan with full complex products (PLAN_NO_PRP)."""
     dt = qs.QS_C128
     gates = G.concat([_general_heavy_circuit(n, 7070 + n), G.random_circuit(n, 200, 7171 + n)[0]])
     psi = rand_state(n, 23)
@@ -755,12 +756,13 @@ def test_prp_form_matches_full_products_and_oracle(qs, n, tile_bits):
     for flags in (qs.PLAN_DEFAULT, qs.PLAN_NO_PRP):
         with upload(qs, n, dt, psi) as s:
             p = s.plan(gates, flags=flags, tile_bits=tile_bits)
-            prp[flags] = sum(p.prp(i) for i in range(p.stats()["passes"]))
+            prp[flags] = np.sum([p.scalar_free(i) for i in range(p.stats()["passes"])], axis=0)
             p.execute()
             got[flags] = s.to_numpy()
             p.close()
         assert np.max(np.abs(got[flags] - want)) < 5 * TOL[dt], flags
-    assert prp[qs.PLAN_DEFAULT] > 0 and prp[qs.PLAN_NO_PRP] == 0
+    # every form taken: phase-shear-phase, H-like without scalar, trailing phase handed over
+    assert np.all(prp[qs.PLAN_DEFAULT] > 0) and not np.any(prp[qs.PLAN_NO_PRP])
     assert np.max(np.abs(got[qs.PLAN_DEFAULT] - got[qs.PLAN_NO_PRP])) < 5 * TOL[dt]
 
 

@@ -298,3 +298,33 @@ def test_balanced_without_scalar_counts():
     assert forms(hs + [G.gate_u1(8, G.haar_2x2(G.SplitMix64(3)))]) == (1, [0, 6], 0)
     assert forms(hs + [G.gate_u1(6, rows)]) == (1, [0, 5], 2)
     assert forms(hs, flags=qs.PLAN_NO_PRP) == (1, [0, 0], 6)
+
+
+def test_trailing_phase_hand_over_counts():
+    """A phase-shear-phase update hands its trailing phase diag(1, z) to the next
+    update of the pass on the same qubit when that one is general, diagonal or
+    anti-diagonal and only updates that commute with the phase (controlled ones
+    with the qubit as control, diagonal controlled ones) lie in between; an H-like,
+    X or controlled-X-target update in between stops it."""
+    rng = G.SplitMix64(17)
+    st = fake_state(10, qs.QS_C128)
+    diag = G.gate_u1(7, (np.exp(0.3j), 0.0, 0.0, np.exp(-0.2j)))
+
+    def nz(gates):
+        p = qs.Plan(st, G.concat(gates + [diag]), flags=qs.PLAN_DRY_RUN | qs.PLAN_NO_MERGE)
+        n = p.stats()["passes"]
+        out = [sum(p.scalar_free(i)[k] for i in range(n)) for k in (0, 2)]
+        p.close()
+        return out
+
+    u = lambda q: G.gate_u1(q, G.haar_2x2(rng))
+    cz = G.gate_cu(1, 0, (1.0, 0.0, 0.0, -1.0))
+    cx_ctl = G.gate_cu(0, 1, G.MAT_X)   # qubit 0 as control: commutes
+    cx_tgt = G.gate_cu(1, 0, G.MAT_X)   # qubit 0 as target: stops
+    t0 = G.gate_u1(0, G.MAT_T)
+    assert nz([u(0), cz, cx_ctl, u(0)]) == [2, 1]
+    assert nz([u(0), cz, t0]) == [1, 1]
+    assert nz([u(0), cx_tgt, u(0)]) == [2, 0]
+    assert nz([u(0), G.gate_u1(0, G.MAT_H), u(0)]) == [2, 0]
+    assert nz([u(0), G.gate_u1(0, G.MAT_X), u(0)]) == [2, 0]
+    assert nz([u(0), u(1), u(0)]) == [3, 1]
