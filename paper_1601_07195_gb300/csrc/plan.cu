@@ -28,6 +28,7 @@
 #include <type_traits>
 
 #include "device.cuh"
+#include "../../include/qs_records.h"
 
 namespace qs {
 namespace {
@@ -900,6 +901,26 @@ qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* n_gates, uint64_
     if (kind) *kind = pp.kind;
     if (n_gates) *n_gates = pp.n_gates;
     if (tile_mask) *tile_mask = pp.mask;
+    return QS_OK;
+}
+
+qs_status qs_plan_pass_records(const qs_plan* p, int i, void* out, int cap, int* n, int* tile_qubits, int* b) {
+    static_assert(sizeof(qs::TileOpDF) == 96, "record layout of qs_records.h");
+    if (!p || !n) return fail(QS_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
+    const PlanPass& pp = p->passes[i];
+    const bool has = pp.kind == 1 && !p->h_ops_df.empty();
+    *n = has ? pp.tp.nops : 0;
+    if (b) *b = has ? pp.tp.b : 0;
+    if (!has) return QS_OK;
+    if (tile_qubits) {
+        for (int k = 0; k < pp.tp.b0; ++k) tile_qubits[k] = k;
+        for (int k = pp.tp.b0; k < pp.tp.b; ++k) tile_qubits[k] = pp.tp.hi_q[k - pp.tp.b0];
+    }
+    if (out) {
+        if (cap < pp.tp.nops) return fail(QS_EINVAL, "record buffer too small");
+        std::memcpy(out, p->h_ops_df.data() + pp.tp.op0, sizeof(qs::TileOpDF) * (size_t)pp.tp.nops);
+    }
     return QS_OK;
 }
 

@@ -1,0 +1,144 @@
+"""The planner's arithmetic, on the CPU: the tile records of complex128
+double-float plans (dry-run plans, no device memory), applied by the host
+reading in record_interp.py, reproduce the oracle's state.
+
+This checks what the planner writes into the records: matrix products of
+adjacent same-qubit gates, phase-run tables (per-tile-bit and outside
+factors), the balanced, phase-shear-phase and scalar-free forms, the scalars
+those forms leave out and the record that takes them, trailing phases moved
+to a later record, and the pass order.  The kernels that read the records
+are checked against the oracle by the GPU tests.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import qsgen as G
+from oracle import oracle as O
+from paper_1601_07195_gb300 import qs
+from tests.record_interp import run_plan
+
+TOL = 1e-12
+
+
+def fake_state(n):
+    h = ctypes.c_void_p()
+    assert qs.load().qs_wrap(ctypes.c_void_p(1 << 30), n, qs.QS_C128, None, ctypes.byref(h)) == qs.QS_OK
+    return qs.State(h.value, n, qs.QS_C128)
+
+
+def rand_state(n, seed):
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    return v / np.linalg.norm(v)
+
+
+def mixed_circuit(n, count, seed):
+    """Every gate class, controlled gates, swaps, rotations, runs of phase gates
+    around one qubit, nearly diagonal and non-unitary general matrices."""
+    rng = G.SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        a = rng.randint(n)
+        b = (a + 1 + rng.randint(n - 1)) % n
+        k = rng.randint(13)
+        if k <= 1:
+            out.append(G.gate_u1(a, G.haar_2x2(rng)))
+        elif k == 2:
+            h = G.MAT_H
+            out.append(G.gate_u1(a, (h, (h[1], h[0], h[3], h[2]), (h[0], h[1], -h[2], -h[3]))[rng.randint(3)]))
+        elif k == 3:
+            out.append(G.gate_u1(a, G.MAT_T))
+        elif k == 4:
+            out.append(G.gate_u1(a, G.MAT_X))
+        elif k == 5:
+            out.append(G.gate_cu(a, b, G.MAT_X))
+        elif k == 6:  # a run of controlled phases around qubit a
+            for _ in range(1 + rng.randint(6)):
+                c = (a + 1 + rng.randint(n - 1)) % n
+                out.append(G.gate_cu(c, a, G.mat_cphase(rng.uniform_range(0.0, 6.0))))
+        elif k == 7:
+            out.append(G.gate_swap(a, b))
+        elif k == 8:
+            out.append(G.gate_rot(G.G_RZ, a, 0))
+        elif k == 9:
+            out.append(G.gate_rot(G.G_RY, a, 1))
+        elif k == 10:
+            out.append(G.gate_cu(a, b, G.haar_2x2(rng)))
+        elif k == 11:  # nearly diagonal unitary
+            e = 10.0 ** -(3 + rng.randint(9))
+            p = np.exp(1j * rng.uniform_range(0.0, 6.0))
+            out.append(G.gate_u1(a, (p * np.cos(e), -p * np.sin(e), np.sin(e), np.cos(e))))
+        else:  # general, not unitary
+            u = G.haar_2x2(rng)
+            out.append(G.gate_u1(a, (0.8 * u[0], 0.8 * u[1], u[2], u[3])))
+    return G.concat(out)
+
+
+def check(n, gates, theta, flags, tile_bits, seed):
+    psi = rand_state(n, seed)
+    want = O.run(psi.copy(), gates, theta)
+    p = qs.Plan(fake_state(n), gates, theta, flags=qs.PLAN_DRY_RUN | flags, tile_bits=tile_bits)
+    try:
+        got = run_plan(p, psi, gates, theta)
+        forms = np.sum([p.scalar_free(i) for i in range(p.stats()["passes"])], axis=0)
+    finally:
+        p.close()
+    err = np.max(np.abs(got - want))
+    assert err < TOL, (flags, tile_bits, err)
+    return forms
+
+
+FLAGS = [qs.PLAN_DEFAULT, qs.PLAN_NO_PRP, qs.PLAN_NO_MERGE, qs.PLAN_NO_PHASE_RUNS,
+         qs.PLAN_NO_MERGE | qs.PLAN_NO_PHASE_RUNS | qs.PLAN_NO_PRP]
+
+
+@pytest.mark.parametrize("flags", FLAGS)
+@pytest.mark.parametrize("n,tile_bits", [(3, 0), (6, 4 | (2 << 8)), (9, 6 | (3 << 8)), (12, 0), (13, 8 | (1 << 8))])
+def test_records_reproduce_oracle(n, tile_bits, flags):
+    gates = mixed_circuit(n, 260, 500 + n)
+    theta = np.array([0.7, -1.3])
+    forms = check(n, gates, theta, flags, tile_bits, 41 + n)
+    if flags in (qs.PLAN_DEFAULT, qs.PLAN_NO_MERGE, qs.PLAN_NO_PHASE_RUNS) and n >= 6:
+        assert forms[0] > 0 and forms[1] > 0 and forms[2] > 0  # every form taken
+    if flags & qs.PLAN_NO_PRP:
+        assert not np.any(forms)
+
+
+@pytest.mark.parametrize("n", [10, 14])
+def test_records_qft_and_random_workload_shape(n):
+    """The benchmark's circuit shape (QFT of a basis state, then random gates),
+    smaller: phase runs from the QFT's controlled-phase chains, swaps, H gates."""
+    r, _ = G.random_circuit(n, 300, 77 + n)
+    gates = G.concat([G.qft_circuit(n), r])
+    check(n, gates, None, qs.PLAN_DEFAULT, 0, 3 + n)
+
+
+def test_records_long_pass_scale_bound():
+    """One pass of 160 unitaries on qubits 0..3 that cannot merge (a controlled X
+    between neighbours on the same qubit), so the product of the scalars left out
+    reaches the 2^-24 bound and later candidates keep their own."""
+    rng = G.SplitMix64(8)
+    out = []
+    for k in range(160):
+        out.append(G.gate_u1(k % 4, G.haar_2x2(rng)))
+        out.append(G.gate_cu((k + 1) % 4, k % 4, G.MAT_X))
+        out.append(G.gate_u1((k + 2) % 4, G.MAT_H))
+    gates = G.concat(out)
+    forms = check(8, gates, None, qs.PLAN_DEFAULT, 0, 9)
+    assert 0 < forms[0] < 159
+
+
+def test_records_match_qs_records_layout():
+    """RECORD_DTYPE is the 96-byte layout include/qs_records.h states."""
+    assert qs.RECORD_DTYPE.itemsize == 96
+    n = 8
+    p = qs.Plan(fake_state(n), G.concat([G.gate_u1(0, G.MAT_H), G.gate_u1(1, G.MAT_T)]),
+                flags=qs.PLAN_DRY_RUN | qs.PLAN_NO_PRP)
+    recs, tq = p.records(0)
+    p.close()
+    assert list(recs["kind"]) == [0, 0] and list(recs["tq"]) == [0, 1] and len(tq) == 8
+    assert list(recs["cls"]) == [6, 3]  # balanced real (H), diagonal with q11 = 1 (T)
+    assert float(recs["c"][1][12]) + float(recs["c"][1][13]) == pytest.approx(np.cos(np.pi / 4), abs=1e-15)
