@@ -106,6 +106,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x F
 # writes the whole state once, so traffic scales with 2^n.  Update (or set to
 # None) whenever the kernel changes.
 DF_TILE_TRAFFIC_N26 = 1.073906e9 + 1.012308e9
+# warp instructions and duration of that n=26 launch (smsp__inst_executed.sum,
+# gpu__time_duration.sum): the kernel is bound by instruction issue, whose peak
+# is 152 SMs x 4 schedulers x 1 warp instruction per clock.  Update (or set to
+# None) with DF_TILE_TRAFFIC_N26.
+DF_TILE_ISSUE_N26 = (1.244201e9, 1.380032e-3)
+ISSUE_PEAK_PER_S = 152 * 4 * 2.07e9
 # the same for the complex64 tile kernel, one n=27 launch (profiles/k_tile_c64_n27_full.md)
 C64_TILE_TRAFFIC_N27 = 1.074006e9 + 1.012051e9
 
@@ -130,6 +136,17 @@ def gate_cost(g, n, s, table=None):
 
 
 _CLASSES = ["general", "real", "diag", "diag1", "antidiag", "perm"]
+
+
+def issue_summary(df):
+    """Instruction issue of the double-float tile kernel from its ncu capture
+    (None for complex64 or when no capture matches the kernel)."""
+    if not (df and DF_TILE_ISSUE_N26):
+        return None
+    inst, sec = DF_TILE_ISSUE_N26
+    return {"warp_instructions": inst, "launch_ms": sec * 1e3, "frac_of_issue_peak": inst / sec / ISSUE_PEAK_PER_S,
+            "source": "ncu capture of one n=26 launch (profiles/k_tile_df_c128_n26_full.md); "
+                      "issue peak 152 SMs x 4 schedulers x 2.07 GHz"}
 
 
 def kernel_flops(counts, n, table):
@@ -428,6 +445,7 @@ def run_ours(args):
                             "(profiles/k_tile_df_c128_n26_full.md)") if df else
                            ("shared-memory bandwidth: 83% of peak SMEM wavefronts, 86% issue "
                             "(profiles/k_tile_c64_n27_full.md)"),
+                "instruction_issue": issue_summary(df),
                 "launches_per_step": len(tile_idx), "avg_launch_ms": tile_launch_ms,
                 "hbm_frac_of_measured": (2 * N * s_bytes / (tile_launch_ms / 1e3)) / 6794.8e9 if tile_idx else None}
 
