@@ -18,7 +18,12 @@
 // rounding) as applying the gates one at a time.  Within a pass, adjacent
 // same-qubit gates are multiplied into one matrix and runs of phase gates
 // around one qubit become one table update; consecutive double-float passes
-// hand the state over as float pairs (qs_internal.h).
+// hand the state over as float pairs (qs_internal.h).  For double-float
+// passes the planner also rewrites single-qubit matrices into cheaper forms
+// that leave a scalar out (phase-shear-phase for general unitaries, H-like
+// gates without q11), moves those scalars into one other update of the pass
+// and trailing phases into later updates on the same qubit: each rewrite
+// changes matrices only, so the pass still applies the same product.
 #include <algorithm>
 #include <cmath>
 #include <utility>
