@@ -54,14 +54,19 @@
 extern "C" {
 #endif
 
-/* Records of pass i of plan p (complex128 double-float plans; zero records
- * for single-gate passes and for other plans).  *n receives the count; when
- * out is not NULL it receives the records (cap = room in records; QS_EINVAL
- * if too small).  tile_qubits, if not NULL, receives the qubit of each tile
- * bit (up to 14 ints) and *b, if not NULL, the number of tile bits.  The
- * plan keeps ownership of its records; this copies them. */
+/* Records of pass i of plan p (zero records for single-gate passes).  *n
+ * receives the count; when out is not NULL it receives the records (cap =
+ * room in records; QS_EINVAL if too small).  tile_qubits, if not NULL,
+ * receives the qubit of each tile bit (up to 14 ints), *b, if not NULL, the
+ * number of tile bits, and *format, if not NULL, the record format:
+ *   1 double-float (complex128 plans; the 96-byte layout above),
+ *   2 float (complex64 plans), 3 double (complex128 with QS_PLAN_ARITH_F64):
+ *     the same eight int32 fields followed by eight floats / doubles m[8]
+ *     (64 / 96 bytes) that hold the matrix q11, q12, q21, q22 as (re, im)
+ *     pairs; classes 0-5 only; a phase-run factor slot f is m[2f], m[2f+1].
+ * The plan keeps ownership of its records; this copies them. */
 QS_API qs_status qs_plan_pass_records(const qs_plan* p, int i, void* out, int cap, int* n, int* tile_qubits,
-                                      int* b);
+                                      int* b, int* format);
 
 #ifdef __cplusplus
 }

@@ -909,14 +909,22 @@ qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* n_gates, uint64_
     return QS_OK;
 }
 
-qs_status qs_plan_pass_records(const qs_plan* p, int i, void* out, int cap, int* n, int* tile_qubits, int* b) {
-    static_assert(sizeof(qs::TileOpDF) == 96, "record layout of qs_records.h");
+qs_status qs_plan_pass_records(const qs_plan* p, int i, void* out, int cap, int* n, int* tile_qubits, int* b,
+                               int* format) {
+    static_assert(sizeof(qs::TileOpDF) == 96 && sizeof(qs::TileOp<float>) == 64 &&
+                      sizeof(qs::TileOp<double>) == 96,
+                  "record layouts of qs_records.h");
     if (!p || !n) return fail(QS_EINVAL, "NULL argument");
     if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
     const PlanPass& pp = p->passes[i];
-    const bool has = pp.kind == 1 && !p->h_ops_df.empty();
+    const bool df = !p->h_ops_df.empty();
+    const size_t rec = df ? sizeof(qs::TileOpDF)
+                          : (p->s->dt == QS_C64 ? sizeof(qs::TileOp<float>) : sizeof(qs::TileOp<double>));
+    const unsigned char* base = df ? reinterpret_cast<const unsigned char*>(p->h_ops_df.data()) : p->h_ops.data();
+    const bool has = pp.kind == 1 && (df || !p->h_ops.empty());
     *n = has ? pp.tp.nops : 0;
     if (b) *b = has ? pp.tp.b : 0;
+    if (format) *format = df ? 1 : (p->s->dt == QS_C64 ? 2 : 3);
     if (!has) return QS_OK;
     if (tile_qubits) {
         for (int k = 0; k < pp.tp.b0; ++k) tile_qubits[k] = k;
@@ -924,7 +932,7 @@ qs_status qs_plan_pass_records(const qs_plan* p, int i, void* out, int cap, int*
     }
     if (out) {
         if (cap < pp.tp.nops) return fail(QS_EINVAL, "record buffer too small");
-        std::memcpy(out, p->h_ops_df.data() + pp.tp.op0, sizeof(qs::TileOpDF) * (size_t)pp.tp.nops);
+        std::memcpy(out, base + rec * (size_t)pp.tp.op0, rec * (size_t)pp.tp.nops);
     }
     return QS_OK;
 }

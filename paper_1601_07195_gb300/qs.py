@@ -21,9 +21,13 @@ PLAN_DEFAULT, PLAN_NO_FUSION, PLAN_GRAPH, PLAN_ARITH_F64, PLAN_DRY_RUN, PLAN_NO_
 PLAN_NO_PHASE_RUNS = 32
 PLAN_NO_PRP = 64
 
-# one tile-pass record of a complex128 double-float plan (include/qs_records.h)
-RECORD_DTYPE = np.dtype([("kind", "<i4"), ("cls", "<i4"), ("tb", "<i4"), ("tq", "<i4"), ("cb", "<i4"),
-                         ("cq", "<i4"), ("pad", "<i4", (2,)), ("c", "<f4", (16,))])
+# one tile-pass record (include/qs_records.h): double-float (complex128 plans),
+# float (complex64) and double (complex128 with PLAN_ARITH_F64) formats
+_REC_HEAD = [("kind", "<i4"), ("cls", "<i4"), ("tb", "<i4"), ("tq", "<i4"), ("cb", "<i4"), ("cq", "<i4"),
+             ("pad", "<i4", (2,))]
+RECORD_DTYPE = np.dtype(_REC_HEAD + [("c", "<f4", (16,))])
+RECORD_DTYPES = {1: RECORD_DTYPE, 2: np.dtype(_REC_HEAD + [("m", "<f4", (8,))]),
+                 3: np.dtype(_REC_HEAD + [("m", "<f8", (8,))])}
 
 _STATUS = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EDTYPE"}
 
@@ -69,7 +73,7 @@ _SIGS = {
     "qs_plan_pass_balanced": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "qs_plan_pass_prp": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "qs_plan_pass_records": [_vp, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
-                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "qs_plan_set_timing": [_vp, ctypes.c_int],
     "qs_plan_pass_times": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)],
     "qs_plan_destroy": [_vp],
@@ -327,15 +331,17 @@ class Plan:
         return int(buf[0]), int(buf[1]), int(buf[2])
 
     def records(self, i):
-        """(records, tile qubits) of pass i as its tile kernel reads them (complex128
-        double-float plans; RECORD_DTYPE, layout in include/qs_records.h)."""
-        n, b = ctypes.c_int(), ctypes.c_int()
+        """(records, tile qubits, format) of pass i as its tile kernel reads them
+        (RECORD_DTYPES[format], layouts in include/qs_records.h)."""
+        n, b, fmt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         tq = (ctypes.c_int * 14)()
-        _check(load().qs_plan_pass_records(self._h, i, None, 0, ctypes.byref(n), tq, ctypes.byref(b)))
-        out = np.zeros(n.value, dtype=RECORD_DTYPE)
+        _check(load().qs_plan_pass_records(self._h, i, None, 0, ctypes.byref(n), tq, ctypes.byref(b),
+                                           ctypes.byref(fmt)))
+        out = np.zeros(n.value, dtype=RECORD_DTYPES[fmt.value])
         if n.value:
-            _check(load().qs_plan_pass_records(self._h, i, out.ctypes.data, n.value, ctypes.byref(n), None, None))
-        return out, list(tq[:b.value])
+            _check(load().qs_plan_pass_records(self._h, i, out.ctypes.data, n.value, ctypes.byref(n), None, None,
+                                               None))
+        return out, list(tq[:b.value]), fmt.value
 
     def prp(self, i):
         """General single-qubit updates of pass i applied in phase-shear-phase form."""

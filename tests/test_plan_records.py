@@ -23,10 +23,10 @@ from tests.record_interp import run_plan
 TOL = 1e-12
 
 
-def fake_state(n):
+def fake_state(n, dt=qs.QS_C128):
     h = ctypes.c_void_p()
-    assert qs.load().qs_wrap(ctypes.c_void_p(1 << 30), n, qs.QS_C128, None, ctypes.byref(h)) == qs.QS_OK
-    return qs.State(h.value, n, qs.QS_C128)
+    assert qs.load().qs_wrap(ctypes.c_void_p(1 << 30), n, dt, None, ctypes.byref(h)) == qs.QS_OK
+    return qs.State(h.value, n, dt)
 
 
 def rand_state(n, seed):
@@ -77,17 +77,17 @@ def mixed_circuit(n, count, seed):
     return G.concat(out)
 
 
-def check(n, gates, theta, flags, tile_bits, seed):
+def check(n, gates, theta, flags, tile_bits, seed, dt=qs.QS_C128, tol=TOL):
     psi = rand_state(n, seed)
     want = O.run(psi.copy(), gates, theta)
-    p = qs.Plan(fake_state(n), gates, theta, flags=qs.PLAN_DRY_RUN | flags, tile_bits=tile_bits)
+    p = qs.Plan(fake_state(n, dt), gates, theta, flags=qs.PLAN_DRY_RUN | flags, tile_bits=tile_bits)
     try:
         got = run_plan(p, psi, gates, theta)
         forms = np.sum([p.scalar_free(i) for i in range(p.stats()["passes"])], axis=0)
     finally:
         p.close()
     err = np.max(np.abs(got - want))
-    assert err < TOL, (flags, tile_bits, err)
+    assert err < tol, (flags, tile_bits, err)
     return forms
 
 
@@ -131,14 +131,33 @@ def test_records_long_pass_scale_bound():
     assert 0 < forms[0] < 159
 
 
+@pytest.mark.parametrize("n,tile_bits", [(6, 4 | (2 << 8)), (12, 0), (13, 8 | (1 << 8))])
+@pytest.mark.parametrize("dt,flags,tol", [(qs.QS_C64, qs.PLAN_DEFAULT, 1e-5),
+                                          (qs.QS_C64, qs.PLAN_NO_MERGE | qs.PLAN_NO_PHASE_RUNS, 1e-5),
+                                          (qs.QS_C128, qs.PLAN_ARITH_F64, TOL)])
+def test_native_records_reproduce_oracle(n, tile_bits, dt, flags, tol):
+    """Native records (complex64 floats, complex128 doubles): products, phase-run
+    slots and outside-tile factors in those formats; no scalar-free forms."""
+    gates = mixed_circuit(n, 260, 600 + n)
+    forms = check(n, gates, np.array([0.7, -1.3]), flags, tile_bits, 43 + n, dt=dt, tol=tol)
+    assert not np.any(forms)
+
+
 def test_records_match_qs_records_layout():
     """RECORD_DTYPE is the 96-byte layout include/qs_records.h states."""
     assert qs.RECORD_DTYPE.itemsize == 96
     n = 8
     p = qs.Plan(fake_state(n), G.concat([G.gate_u1(0, G.MAT_H), G.gate_u1(1, G.MAT_T)]),
                 flags=qs.PLAN_DRY_RUN | qs.PLAN_NO_PRP)
-    recs, tq = p.records(0)
+    recs, tq, fmt = p.records(0)
     p.close()
-    assert list(recs["kind"]) == [0, 0] and list(recs["tq"]) == [0, 1] and len(tq) == 8
+    assert fmt == 1 and list(recs["kind"]) == [0, 0] and list(recs["tq"]) == [0, 1] and len(tq) == 8
     assert list(recs["cls"]) == [6, 3]  # balanced real (H), diagonal with q11 = 1 (T)
     assert float(recs["c"][1][12]) + float(recs["c"][1][13]) == pytest.approx(np.cos(np.pi / 4), abs=1e-15)
+    for dt, flags, want_fmt in ((qs.QS_C64, 0, 2), (qs.QS_C128, qs.PLAN_ARITH_F64, 3)):
+        p = qs.Plan(fake_state(n, dt), G.concat([G.gate_u1(0, G.MAT_H), G.gate_u1(1, G.MAT_T)]),
+                    flags=qs.PLAN_DRY_RUN | flags)
+        recs, tq, fmt = p.records(0)
+        p.close()
+        assert fmt == want_fmt and recs.dtype.itemsize == (64 if fmt == 2 else 96)
+        assert list(recs["cls"]) == [1, 3] and recs["m"][1][6] == pytest.approx(np.cos(np.pi / 4), rel=1e-7)
