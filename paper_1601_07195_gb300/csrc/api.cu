@@ -83,7 +83,8 @@ static void rotation(int kind, double th, double m[8]) {
 }
 
 qs_status lower_gates(const qs_gate* g, int ng, const double* theta, int np, int n, std::vector<Op>& out) {
-    if (ng < 0 || (ng > 0 && g == nullptr)) return fail(QS_EINVAL, "gate array is NULL");
+    if (ng < 0) return fail(QS_EINVAL, "negative gate count");
+    if (ng > 0 && g == nullptr) return fail(QS_EINVAL, "gate array is NULL");
     out.clear();
     out.reserve(ng);
     for (int j = 0; j < ng; ++j) {

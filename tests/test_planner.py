@@ -328,3 +328,49 @@ def test_trailing_phase_hand_over_counts():
     assert nz([u(0), G.gate_u1(0, G.MAT_H), u(0)]) == [2, 0]
     assert nz([u(0), G.gate_u1(0, G.MAT_X), u(0)]) == [2, 0]
     assert nz([u(0), u(1), u(0)]) == [3, 1]
+
+
+def test_plan_arguments_on_the_host():
+    """Plan creation on a dry-run state: an empty circuit gives an empty plan;
+    a negative count, a NULL gate array, an out-of-range or repeated qubit, an
+    unknown kind, a rotation without its angle and a tile of more than 14 bits
+    are rejected with QS_EINVAL and a message; a run of more low qubits than
+    tile bits is clamped to the tile."""
+    lib = qs.load()
+    st = fake_state(10, qs.QS_C128)
+    p = qs.Plan(st, G.concat([]), flags=qs.PLAN_DRY_RUN)
+    assert p.stats() == {"passes": 0, "tile_passes": 0, "launches": 0, "device_ops": 0}
+    p.close()
+
+    def create(gates, n=None, theta=None, tile_bits=0):
+        g = np.ascontiguousarray(gates, dtype=qs.GATE_DTYPE)
+        th = np.ascontiguousarray(theta if theta is not None else np.zeros(0), dtype=np.float64)
+        out = ctypes.c_void_p()
+        rc = lib.qs_plan_create(st.handle, g.ctypes.data if n != "null" else None,
+                                len(g) if n in (None, "null") else n,
+                                th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if th.size else None, th.size,
+                                qs.PLAN_DRY_RUN, tile_bits, ctypes.byref(out))
+        if rc == qs.QS_OK:
+            lib.qs_plan_destroy(out)
+        return rc, lib.qs_last_error().decode()
+
+    h = G.gate_u1(0, G.MAT_H)
+    assert create(h, n=-1) == (qs.QS_EINVAL, "negative gate count")
+    assert create(h, n="null")[0] == qs.QS_EINVAL
+    bad = h.copy()
+    bad["t"] = 10
+    assert create(bad) == (qs.QS_EINVAL, "gate 0: qubit out of range")
+    cu = G.gate_cu(1, 2, G.MAT_X)
+    cu["c"] = 2
+    assert create(cu)[0] == qs.QS_EINVAL
+    sw = G.gate_swap(1, 2)
+    sw["c"] = 1
+    assert create(sw)[0] == qs.QS_EINVAL
+    kind = h.copy()
+    kind["kind"] = 9
+    assert create(kind) == (qs.QS_EINVAL, "gate 0: unknown kind")
+    assert create(G.gate_rot(G.G_RY, 0, 0))[0] == qs.QS_EINVAL              # no angles
+    assert create(G.gate_rot(G.G_RY, 0, 3), theta=np.array([0.1]))[0] == qs.QS_EINVAL
+    assert create(h, tile_bits=15)[0] == qs.QS_EINVAL
+    assert create(h, tile_bits=12 | (13 << 8))[0] == qs.QS_OK
+    assert create(h, tile_bits=1)[0] == qs.QS_OK
