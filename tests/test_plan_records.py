@@ -161,3 +161,27 @@ def test_records_match_qs_records_layout():
         p.close()
         assert fmt == want_fmt and recs.dtype.itemsize == (64 if fmt == 2 else 96)
         assert list(recs["cls"]) == [1, 3] and recs["m"][1][6] == pytest.approx(np.cos(np.pi / 4), rel=1e-7)
+
+
+def test_record_view_arguments():
+    """qs_plan_pass_records: a NULL count or an out-of-range pass is QS_EINVAL,
+    a buffer smaller than the pass is QS_EINVAL and left untouched, single-gate
+    passes have no records."""
+    lib = qs.load()
+    n = 12
+    gates = G.concat([G.gate_u1(0, G.MAT_H), G.gate_u1(1, G.MAT_T), G.gate_u1(2, G.haar_2x2(G.SplitMix64(4)))])
+    p = qs.Plan(fake_state(n), gates, flags=qs.PLAN_DRY_RUN)
+    cnt = ctypes.c_int()
+    assert lib.qs_plan_pass_records(p._h, 0, None, 0, None, None, None, None) == qs.QS_EINVAL
+    assert lib.qs_plan_pass_records(p._h, 5, None, 0, ctypes.byref(cnt), None, None, None) == qs.QS_EINVAL
+    assert lib.qs_plan_pass_records(p._h, 0, None, 0, ctypes.byref(cnt), None, None, None) == qs.QS_OK
+    assert cnt.value == 3
+    buf = np.full(2, 7, dtype=qs.RECORD_DTYPE)
+    assert lib.qs_plan_pass_records(p._h, 0, buf.ctypes.data, 2, ctypes.byref(cnt), None, None, None) == qs.QS_EINVAL
+    assert np.all(buf["kind"] == 7)
+    p.close()
+    single = qs.Plan(fake_state(n), G.gate_u1(11, G.haar_2x2(G.SplitMix64(5))), flags=qs.PLAN_DRY_RUN)
+    assert single.passes()[0]["kind"] == "single"
+    recs, tq, fmt = single.records(0)
+    single.close()
+    assert len(recs) == 0 and tq == []
