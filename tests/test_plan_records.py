@@ -185,3 +185,24 @@ def test_record_view_arguments():
     recs, tq, fmt = single.records(0)
     single.close()
     assert len(recs) == 0 and tq == []
+
+
+def test_random_plans_records_reproduce_oracle():
+    """Property test over random circuits, qubit counts, tile shapes, plan flags
+    and record formats: the records of every pass, applied on the host,
+    reproduce the oracle's state."""
+    hyp = pytest.importorskip("hypothesis")
+    st_ = hyp.strategies
+    flag_sets = [qs.PLAN_DEFAULT, qs.PLAN_NO_PRP, qs.PLAN_NO_MERGE, qs.PLAN_NO_PHASE_RUNS, qs.PLAN_NO_FUSION]
+    modes = [(qs.QS_C128, 0, TOL), (qs.QS_C128, qs.PLAN_ARITH_F64, TOL), (qs.QS_C64, 0, 1e-5)]
+
+    @hyp.settings(max_examples=150, deadline=None, derandomize=True)
+    @hyp.given(n=st_.integers(2, 10), count=st_.integers(1, 150), seed=st_.integers(0, 10 ** 6),
+               b=st_.integers(1, 12), b0=st_.integers(0, 6), flags=st_.sampled_from(flag_sets),
+               mode=st_.sampled_from(modes))
+    def prop(n, count, seed, b, b0, flags, mode):
+        dt, arith, tol = mode
+        gates = mixed_circuit(n, count, seed)
+        check(n, gates, np.array([0.7, -1.3]), flags | arith, b | (min(b0, b) << 8), seed % 997, dt=dt, tol=tol)
+
+    prop()
