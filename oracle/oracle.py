@@ -25,22 +25,33 @@ _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 
 
-def compile_source(src: str, out: str) -> str:
-    """gcc -O2 -ffp-contract=off: separately rounded IEEE double operations."""
+_OMP_LIB_PATH = os.path.join(_BUILD, "liboracle_omp.so")
+_omp_lib = None
+
+
+def compile_source(src: str, out: str, parallel: bool = False) -> str:
+    """gcc -O2 -ffp-contract=off: separately rounded IEEE double operations.
+    parallel=True: the same source with -O3 -fopenmp (its pair loops split over
+    the host's cores; the same operations on every pair, so the same bits)."""
     tmp = out + f".tmp{os.getpid()}"
+    opt = ["-O3", "-fopenmp"] if parallel else ["-O2"]
     subprocess.check_call(
-        ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+        ["gcc", "-std=c99", *opt, "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
          src, "-o", tmp, "-lm"])
     os.replace(tmp, out)
     return out
 
 
-def build(force: bool = False) -> str:
-    """Compile qs_oracle.c into a shared library (plain gcc, no vector extensions)."""
+def build(force: bool = False, parallel: bool = True) -> str:
+    """Compile qs_oracle.c into a shared library (plain gcc, no vector extensions),
+    and (parallel=True) its OpenMP build beside it."""
     with _lock:
+        os.makedirs(_BUILD, exist_ok=True)
         if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-            os.makedirs(_BUILD, exist_ok=True)
             compile_source(_SRC, _LIB_PATH)
+        if parallel and (force or not os.path.exists(_OMP_LIB_PATH)
+                         or os.path.getmtime(_OMP_LIB_PATH) < os.path.getmtime(_SRC)):
+            compile_source(_SRC, _OMP_LIB_PATH, parallel=True)
     return _LIB_PATH
 
 
@@ -54,8 +65,27 @@ def load_library(path):
 def _load():
     global _lib
     if _lib is None:
-        _lib = load_library(build())
+        _lib = load_library(build(parallel=False))
     return _lib
+
+
+def _load_omp():
+    global _omp_lib
+    if _omp_lib is None:
+        build(parallel=True)
+        _omp_lib = load_library(_OMP_LIB_PATH)
+    return _omp_lib
+
+
+def threads() -> int:
+    """Threads the OpenMP build uses (OMP_NUM_THREADS, else every core the process may run on)."""
+    env = os.environ.get("OMP_NUM_THREADS")
+    if env and env.split(",")[0].isdigit():
+        return int(env.split(",")[0])
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def _declare(lib):
@@ -75,6 +105,13 @@ def _declare(lib):
     lib.or_grad.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int,
                             ctypes.c_void_p, ctypes.c_int, _dp, _dp]
     lib.or_grad.restype = ctypes.c_int
+    lib.or_qft_basis.argtypes = [_dp, ctypes.c_int, ctypes.c_uint64]
+    lib.or_apply_hamiltonian.argtypes = [_dp, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, _dp]
+    lib.or_apply_hamiltonian.restype = ctypes.c_int
+    lib.or_dot_re.argtypes = [_dp, _dp, ctypes.c_int]
+    lib.or_dot_re.restype = ctypes.c_double
+    lib.or_apply_gate.argtypes = [_dp, ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_int]
+    lib.or_apply_gate.restype = ctypes.c_int
 
 
 def _ptr(a):
@@ -124,20 +161,33 @@ def apply_swap(psi, a, b):
     _load().or_apply_swap(_ptr(psi.view(np.float64)), n, a, b)
 
 
-def run(psi, gates, theta=None):
-    """Apply the gate records in order, in place."""
+def run(psi, gates, theta=None, parallel=False):
+    """Apply the gate records in order, in place (parallel=True: the OpenMP build,
+    bit-identical result on all host cores)."""
     n = _state(psi)
     gates = np.ascontiguousarray(gates)
     th = np.ascontiguousarray(theta if theta is not None else np.zeros(0), dtype=np.float64)
-    rc = _load().or_run(_ptr(psi.view(np.float64)), n, gates.ctypes.data, len(gates),
-                        _ptr(th) if th.size else None, int(th.size))
+    lib = _load_omp() if parallel else _load()
+    rc = lib.or_run(_ptr(psi.view(np.float64)), n, gates.ctypes.data, len(gates),
+                    _ptr(th) if th.size else None, int(th.size))
     if rc != 0:
         raise ValueError("invalid gate record")
     return psi
 
 
-def simulate(n, gates, theta=None, x=0):
-    return run(basis(n, x), gates, theta)
+def simulate(n, gates, theta=None, x=0, parallel=False):
+    return run(basis(n, x), gates, theta, parallel=parallel)
+
+
+def qft_basis_state(n, x, parallel=False):
+    """The whole state QFT|x> from its closed form (or_qft_basis): amplitude y is
+    2^(-n/2) exp(2 pi i (x y mod 2^n) / 2^n), the product reduced exactly in
+    64-bit integers (n <= 32)."""
+    if not 1 <= n <= 32 or not 0 <= int(x) < (1 << n):
+        raise ValueError("need 1 <= n <= 32 and 0 <= x < 2^n")
+    psi = np.empty(1 << n, dtype=np.complex128)
+    (_load_omp() if parallel else _load()).or_qft_basis(_ptr(psi.view(np.float64)), n, int(x))
+    return psi
 
 
 def gate_matrix(gate, theta=None):
@@ -188,6 +238,56 @@ def grad(n, gates, theta, terms):
     if rc != 0:
         raise ValueError("invalid gradient input")
     return float(e[0]), g[: th.size].copy()
+
+
+def grad_sampled(n, gates, theta, terms, params, parallel=False):
+    """(energy, {p: dE/dtheta_p}) for the listed parameters only, from the same
+    definition as or_grad: dE/dtheta_p = 2 Re <H psi | U_P..U_{j+1} (dU_j/dtheta)
+    U_{j-1}..U_1 |0>> for the rotation gate j that carries p.  One forward run
+    keeps the prefix state U_{j-1}..U_1 |0> of each listed parameter in turn, so
+    a parameter costs only its gate's suffix.  Each listed parameter must belong
+    to exactly one rotation gate."""
+    gates = np.ascontiguousarray(gates)
+    terms = np.ascontiguousarray(terms)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    lib = _load_omp() if parallel else _load()
+    where = {}
+    for j, g in enumerate(gates):
+        if int(g["kind"]) in (3, 4, 5):
+            where.setdefault(int(g["param"]), []).append(j)
+    for p in params:
+        if len(where.get(int(p), [])) != 1:
+            raise ValueError(f"parameter {p} is not carried by exactly one rotation gate")
+    order = sorted({int(p) for p in params}, key=lambda p: where[p][0])
+
+    def apply(psi, j, deriv=0):
+        rc = lib.or_apply_gate(_ptr(psi.view(np.float64)), n, gates[j:j + 1].ctypes.data, _ptr(th), int(th.size), deriv)
+        if rc != 0:
+            raise ValueError("invalid gate record")
+
+    prefix = basis(n, 0)
+    done = 0
+    partial = {}
+    for p in order:
+        j = where[p][0]
+        for i in range(done, j):
+            apply(prefix, i)
+        done = j
+        d = prefix.copy()
+        apply(d, j, deriv=1)
+        for i in range(j + 1, len(gates)):
+            apply(d, i)
+        partial[p] = d
+    for i in range(done, len(gates)):
+        apply(prefix, i)
+    hpsi = np.empty_like(prefix)
+    if lib.or_apply_hamiltonian(_ptr(prefix.view(np.float64)), n, terms.ctypes.data, len(terms),
+                                _ptr(hpsi.view(np.float64))) != 0:
+        raise ValueError("invalid Pauli term")
+    energy = lib.or_dot_re(_ptr(prefix.view(np.float64)), _ptr(hpsi.view(np.float64)), n)
+    grads = {p: 2.0 * lib.or_dot_re(_ptr(hpsi.view(np.float64)), _ptr(d.view(np.float64)), n)
+             for p, d in partial.items()}
+    return energy, grads
 
 
 def qft_basis_amplitudes(n, x, ys):

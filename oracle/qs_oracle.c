@@ -18,6 +18,14 @@
  * Compiled with -ffp-contract=off: every product and sum is a separately
  * rounded IEEE double operation.  Reductions use Neumaier's compensated sum
  * (A. Neumaier, ZAMM 54, 1974) so the reference is tighter than the kernels.
+ *
+ * The same file is also compiled a second way, -O3 -fopenmp, for timing on
+ * all host cores and for reference states too large for one core: the
+ * "#pragma omp" lines below split the pair loops of the gate routines (and
+ * the closed-form QFT fill) across threads, the threading of Section 4.2.
+ * Every pair is still updated by the same separately rounded operations, so
+ * both builds give bit-identical states.  Reductions stay serial.  Without
+ * -fopenmp the pragmas are ignored.
  */
 #include <math.h>
 #include <stdint.h>
@@ -62,19 +70,31 @@ void or_init_basis(double* psi, int n, uint64_t x) {
 /* ---- Eq. 2 via the loop nest of Fig. 3 ------------------------------------- */
 /* alpha'_{..0_k..} = q11 alpha_{..0_k..} + q12 alpha_{..1_k..}
    alpha'_{..1_k..} = q21 alpha_{..0_k..} + q22 alpha_{..1_k..}
-   m = (q11, q12, q21, q22) as (re, im) pairs. */
+   m = (q11, q12, q21, q22) as (re, im) pairs; the pair is (i, i + s). */
+static void pair_update(double* psi, uint64_t i, uint64_t s, const double m[8]) {
+    cplx q11 = entry(m, 0), q12 = entry(m, 1), q21 = entry(m, 2), q22 = entry(m, 3);
+    cplx a, b;
+    a.re = psi[2 * i]; a.im = psi[2 * i + 1];
+    b.re = psi[2 * (i + s)]; b.im = psi[2 * (i + s) + 1];
+    cplx a2 = cadd(cmul(q11, a), cmul(q12, b));
+    cplx b2 = cadd(cmul(q21, a), cmul(q22, b));
+    psi[2 * i] = a2.re; psi[2 * i + 1] = a2.im;
+    psi[2 * (i + s)] = b2.re; psi[2 * (i + s) + 1] = b2.im;
+}
+
+/* Outer loop over the groups of 2^(k+1) amplitudes, inner loop over the 2^k
+ * pairs of a group.  The OpenMP build splits the outer loop across threads when
+ * there are many groups, else the inner loop of each group. */
 void or_apply_1q(double* psi, int n, int k, const double m[8]) {
     uint64_t N = (uint64_t)1 << n, s = (uint64_t)1 << k;
-    cplx q11 = entry(m, 0), q12 = entry(m, 1), q21 = entry(m, 2), q22 = entry(m, 3);
-    for (uint64_t g = 0; g < N; g += 2 * s) {
-        for (uint64_t i = g; i < g + s; ++i) {
-            cplx a, b;
-            a.re = psi[2 * i]; a.im = psi[2 * i + 1];
-            b.re = psi[2 * (i + s)]; b.im = psi[2 * (i + s) + 1];
-            cplx a2 = cadd(cmul(q11, a), cmul(q12, b));
-            cplx b2 = cadd(cmul(q21, a), cmul(q22, b));
-            psi[2 * i] = a2.re; psi[2 * i + 1] = a2.im;
-            psi[2 * (i + s)] = b2.re; psi[2 * (i + s) + 1] = b2.im;
+    if (N / (2 * s) >= 64) {
+#pragma omp parallel for schedule(static)
+        for (uint64_t g = 0; g < N; g += 2 * s)
+            for (uint64_t i = g; i < g + s; ++i) pair_update(psi, i, s, m);
+    } else {
+        for (uint64_t g = 0; g < N; g += 2 * s) {
+#pragma omp parallel for schedule(static) if (s >= 4096)
+            for (uint64_t i = g; i < g + s; ++i) pair_update(psi, i, s, m);
         }
     }
 }
@@ -82,17 +102,16 @@ void or_apply_1q(double* psi, int n, int k, const double m[8]) {
 /* ---- Eq. 3: Q on target t only where control bit c is 1 --------------------- */
 void or_apply_ctrl(double* psi, int n, int c, int t, const double m[8]) {
     uint64_t N = (uint64_t)1 << n, s = (uint64_t)1 << t;
-    cplx q11 = entry(m, 0), q12 = entry(m, 1), q21 = entry(m, 2), q22 = entry(m, 3);
-    for (uint64_t g = 0; g < N; g += 2 * s) {
-        for (uint64_t i = g; i < g + s; ++i) {
-            if (((i >> c) & 1u) == 0) continue;  /* control qubit in |0>: unchanged */
-            cplx a, b;
-            a.re = psi[2 * i]; a.im = psi[2 * i + 1];
-            b.re = psi[2 * (i + s)]; b.im = psi[2 * (i + s) + 1];
-            cplx a2 = cadd(cmul(q11, a), cmul(q12, b));
-            cplx b2 = cadd(cmul(q21, a), cmul(q22, b));
-            psi[2 * i] = a2.re; psi[2 * i + 1] = a2.im;
-            psi[2 * (i + s)] = b2.re; psi[2 * (i + s) + 1] = b2.im;
+    if (N / (2 * s) >= 64) {
+#pragma omp parallel for schedule(static)
+        for (uint64_t g = 0; g < N; g += 2 * s)
+            for (uint64_t i = g; i < g + s; ++i)
+                if ((i >> c) & 1u) pair_update(psi, i, s, m);  /* control in |0>: unchanged */
+    } else {
+        for (uint64_t g = 0; g < N; g += 2 * s) {
+#pragma omp parallel for schedule(static) if (s >= 4096)
+            for (uint64_t i = g; i < g + s; ++i)
+                if ((i >> c) & 1u) pair_update(psi, i, s, m);
         }
     }
 }
@@ -100,6 +119,8 @@ void or_apply_ctrl(double* psi, int n, int c, int t, const double m[8]) {
 /* ---- SWAP(a, b): |.. x_a .. x_b ..> -> |.. x_b .. x_a ..> (index permutation) */
 void or_apply_swap(double* psi, int n, int a, int b) {
     uint64_t N = (uint64_t)1 << n;
+    /* iteration i touches only i and its partner j, which no other iteration swaps */
+#pragma omp parallel for schedule(static) if (N >= 65536)
     for (uint64_t i = 0; i < N; ++i) {
         if (((i >> a) & 1u) == 0 && ((i >> b) & 1u) == 1) {
             uint64_t j = i ^ ((uint64_t)1 << a) ^ ((uint64_t)1 << b);
@@ -107,6 +128,22 @@ void or_apply_swap(double* psi, int n, int a, int b) {
             psi[2 * i] = psi[2 * j]; psi[2 * i + 1] = psi[2 * j + 1];
             psi[2 * j] = r; psi[2 * j + 1] = m;
         }
+    }
+}
+
+/* ---- closed form of the quantum Fourier transform of a basis state ---------
+ * QFT |x> = 2^(-n/2) sum_y exp(2 pi i x y / 2^n) |y>  (the transform the QFT
+ * workload of Section 5.3 applies; textbook form, Nielsen & Chuang 5.1).  The
+ * phase x y mod 2^n is taken in exact integer arithmetic (n <= 32, so x y
+ * fits 64 bits) before the double-precision cosine and sine. */
+void or_qft_basis(double* psi, int n, uint64_t x) {
+    uint64_t N = (uint64_t)1 << n, mask = N - 1;
+    double scale = pow(2.0, -0.5 * n), w = 2.0 * 3.14159265358979323846 / (double)N;
+#pragma omp parallel for schedule(static) if (N >= 65536)
+    for (uint64_t y = 0; y < N; ++y) {
+        double ph = w * (double)((x * y) & mask);
+        psi[2 * y] = scale * cos(ph);
+        psi[2 * y + 1] = scale * sin(ph);
     }
 }
 
@@ -235,11 +272,13 @@ double or_expect(const double* psi, int n, const or_term* t, int nt) {
     return nval(&a);
 }
 
-/* out = H psi (out must not alias psi) */
+/* out = H psi (out must not alias psi).  Terms are added to each amplitude in
+ * term order; the OpenMP build splits the amplitude loop, which keeps that order. */
 static void apply_hamiltonian(const double* psi, int n, const or_term* t, int nt, double* out) {
     uint64_t N = (uint64_t)1 << n;
     memset(out, 0, (size_t)N * 2 * sizeof(double));
     for (int j = 0; j < nt; ++j) {
+#pragma omp parallel for schedule(static) if (N >= 65536)
         for (uint64_t i = 0; i < N; ++i) {
             if (t[j].kind == OR_X) {
                 uint64_t k = i ^ ((uint64_t)1 << t[j].q0);
@@ -254,6 +293,31 @@ static void apply_hamiltonian(const double* psi, int n, const or_term* t, int nt
             }
         }
     }
+}
+
+/* out = H psi for a checked Pauli sum.  Returns -1 on a bad term. */
+int or_apply_hamiltonian(const double* psi, int n, const or_term* t, int nt, double* out) {
+    if (check_terms(t, nt, n)) return -1;
+    apply_hamiltonian(psi, n, t, nt, out);
+    return 0;
+}
+
+/* Re <a|b> = sum_i Re(conj(a_i) b_i), compensated. */
+double or_dot_re(const double* a, const double* b, int n) {
+    uint64_t N = (uint64_t)1 << n;
+    nsum s = {0, 0};
+    for (uint64_t i = 0; i < N; ++i) nadd(&s, a[2 * i] * b[2 * i] + a[2 * i + 1] * b[2 * i + 1]);
+    return nval(&s);
+}
+
+/* One checked gate record applied to psi; deriv != 0 applies dU/dtheta of a
+ * rotation instead of U (the factor the derivative of the circuit puts in gate
+ * j's place).  Returns -1 on a bad record. */
+int or_apply_gate(double* psi, int n, const or_gate* g, const double* theta, int n_params, int deriv) {
+    if (check_gate(g, n) || g->param >= n_params || (g->param >= 0 && theta == NULL)) return -1;
+    if (deriv && g->kind != OR_RX && g->kind != OR_RY && g->kind != OR_RZ) return -1;
+    apply_gate(psi, n, g, theta, deriv);
+    return 0;
 }
 
 /* Energy and gradient of E(theta) = <psi(theta)|H|psi(theta)>, psi(theta) = U_P..U_1 |0..0>.

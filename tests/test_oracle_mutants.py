@@ -18,6 +18,7 @@ PINS = [
     lambda: P.test_controlled_gate_equals_kronecker_operator(3),
     lambda: P.test_swap_equals_pauli_formula(3),
     lambda: P.test_qft_of_basis_state_closed_form(6),
+    lambda: P.test_qft_closed_form_routines_match_the_circuit(3),
     lambda: P.test_permutation_circuits_are_bit_exact(),
     lambda: P.test_reductions_brute_force(),
     lambda: P.test_gradient_closed_form_ry_z(),
@@ -28,11 +29,11 @@ PINS = [
 
 # (name, exact source text, replacement, occurrence index or None for all)
 MUTANTS = [
-    ("transposed q12/q21", "cplx a2 = cadd(cmul(q11, a), cmul(q12, b));\n            cplx b2 = cadd(cmul(q21, a)",
-     "cplx a2 = cadd(cmul(q11, a), cmul(q21, b));\n            cplx b2 = cadd(cmul(q12, a)", 0),
+    ("transposed q12/q21", "cplx a2 = cadd(cmul(q11, a), cmul(q12, b));\n    cplx b2 = cadd(cmul(q21, a)",
+     "cplx a2 = cadd(cmul(q11, a), cmul(q21, b));\n    cplx b2 = cadd(cmul(q12, a)", 0),
     ("dropped q21 term", "cplx b2 = cadd(cmul(q21, a), cmul(q22, b));", "cplx b2 = cmul(q22, b);", 0),
     ("conjugated product", "r.re = a.re * b.re - a.im * b.im;", "r.re = a.re * b.re + a.im * b.im;", None),
-    ("control on |0>", "if (((i >> c) & 1u) == 0) continue;", "if (((i >> c) & 1u) == 1) continue;", None),
+    ("control on |0>", "if ((i >> c) & 1u) pair_update", "if (((i >> c) & 1u) == 0) pair_update", None),
     ("stride 2^k+1", "uint64_t N = (uint64_t)1 << n, s = (uint64_t)1 << k;",
      "uint64_t N = (uint64_t)1 << n, s = (uint64_t)1 << (k ? k - 1 : 0);", None),
     ("swap condition", "if (((i >> a) & 1u) == 0 && ((i >> b) & 1u) == 1) {", "if (((i >> a) & 1u) == 0) {", None),
@@ -44,6 +45,9 @@ MUTANTS = [
     ("RZ derivative sign", "set(m, 0, -0.5 * s, -0.5 * c); set(m, 3, -0.5 * s, 0.5 * c);",
      "set(m, 0, -0.5 * s, 0.5 * c); set(m, 3, -0.5 * s, -0.5 * c);", None),
     ("gradient factor", "grads[g[j].param] += 2.0 * nval(&a);", "grads[g[j].param] += nval(&a);", None),
+    ("QFT closed-form phase sign", "psi[2 * y + 1] = scale * sin(ph);", "psi[2 * y + 1] = -scale * sin(ph);", None),
+    ("QFT closed-form phase product", "double ph = w * (double)((x * y) & mask);",
+     "double ph = w * (double)((x + y) & mask);", None),
     ("half angle", "double c = cos(0.5 * theta), s = sin(0.5 * theta);", "double c = cos(theta), s = sin(theta);", None),
 ]
 

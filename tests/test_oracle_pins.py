@@ -142,6 +142,48 @@ def test_qft_of_basis_state_closed_form(n):
     assert np.max(np.abs(psi - want)) < 1e-13
 
 
+@pytest.mark.parametrize("n", [1, 3, 8, 13])
+def test_qft_closed_form_routines_match_the_circuit(n):
+    """Both closed-form QFT routines of the oracle (the per-index Python one used
+    for sampled amplitudes, and or_qft_basis that fills a whole state, serial and
+    OpenMP builds) reproduce the oracle's own simulation of the QFT circuit, which
+    the closed form above and the Kronecker pins fix."""
+    for x in (0, 1, (1 << n) - 1, G.random_basis(n, 5 + n)):
+        circ = O.simulate(n, G.qft_circuit(n), x=x)
+        ys = np.arange(1 << n)
+        assert np.max(np.abs(O.qft_basis_amplitudes(n, x, ys) - circ)) < 1e-13
+        assert np.max(np.abs(O.qft_basis_state(n, x) - circ)) < 1e-13
+        assert np.array_equal(O.qft_basis_state(n, x, parallel=True), O.qft_basis_state(n, x))
+
+
+def test_openmp_build_is_bit_identical():
+    """The -O3 -fopenmp build of the same source splits only the pair loops, so its
+    states equal the serial build's bit for bit, for every gate kind and for
+    targets on both sides of the outer/inner split (n = 16: groups < 64 from k = 10)."""
+    n = 16
+    gates = G.concat([G.random_circuit(n, 400, 31)[0], G.qft_circuit(n), G.gate_swap(0, n - 1),
+                      G.gate_swap(n - 2, 3), G.gate_cu(n - 1, 0, G.haar_2x2(G.SplitMix64(2))),
+                      G.gate_cu(0, n - 1, G.haar_2x2(G.SplitMix64(4)))])
+    a = O.simulate(n, gates, x=12345)
+    b = O.simulate(n, gates, x=12345, parallel=True)
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+def test_sampled_gradient_equals_the_full_gradient():
+    """grad_sampled (the derivative's definition for chosen parameters, sharing
+    the prefix state) reproduces or_grad, which the parameter-shift and
+    closed-form pins below fix, for every parameter, in both builds."""
+    for n, obs in ((5, G.ising_observable(5, 2)), (7, G.z_zz_observable(7, 3))):
+        g, p = G.ansatz(n, 3)
+        g = G.concat([g, G.gate_rot(G.G_RX, n - 1, p), G.gate_swap(0, n - 1)])
+        th = G.angles(p + 1, 9)
+        e, gr = O.grad(n, g, th, obs)
+        for parallel in (False, True):
+            e2, gs = O.grad_sampled(n, g, th, obs, list(range(p + 1))[::-1], parallel=parallel)
+            assert abs(e2 - e) < 1e-14
+            assert max(abs(gs[k] - gr[k]) for k in gs) < 1e-14
+
+
 def test_qft_gate_counts_match_table3():
     rows = [tuple(map(int, ln.split())) for ln in open(_golden("qft_gate_counts.txt")) if ln.strip() and not ln.startswith("#")]
     assert len(rows) == 12
