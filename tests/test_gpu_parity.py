@@ -8,6 +8,9 @@ the whole state and tiles with ragged padding), fused and unfused plans, and
 CUDA-graph replay.
 """
 
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -19,6 +22,11 @@ pytestmark = pytest.mark.gpu
 TOL = {1: 1e-12, 0: 1e-5}
 DTYPES = [1, 0]  # QS_C128, QS_C64
 RED_TOL = {1: 1e-12, 0: 2e-6}
+# Energies and adjoint gradients are held to the same max-abs bounds as the
+# amplitudes.  Measured maxima over every instance of these tests: 1.8e-13
+# (complex128) and 1.2e-6 (complex64), for Pauli sums whose coefficients add
+# up to |c|_1 <= 24.
+GRAD_TOL = {1: 1e-12, 0: 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -28,6 +36,19 @@ def qs():
     from paper_1601_07195_gb300 import qs as _qs
     _qs.load()
     return _qs
+
+
+def maxerr(got, want):
+    """Max-abs difference of two results; with QS_ERRLOG set, each value is also
+    appended to that file (one JSON object per line) under the running test's id,
+    which is how the measured errors per result are collected."""
+    got, want = np.asarray(got), np.asarray(want)
+    e = float(np.max(np.abs(got - want))) if got.size else 0.0
+    path = os.environ.get("QS_ERRLOG")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0], "err": e}) + "\n")
+    return e
 
 
 def rand_state(n, seed):
@@ -72,7 +93,7 @@ def test_single_qubit_gate_every_qubit_every_class(qs, dt, native, n):
             if name == "X":
                 assert np.array_equal(got, want.astype(got.dtype)), f"X on {k} not bit-exact"
             else:
-                assert np.max(np.abs(got - want)) < TOL[dt], (name, k)
+                assert maxerr(got, want) < TOL[dt], (name, k)
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -93,7 +114,7 @@ def test_controlled_gate_every_pair(qs, dt, n):
                 if name == "X":
                     assert np.array_equal(got, want.astype(got.dtype))
                 else:
-                    assert np.max(np.abs(got - want)) < TOL[dt], (name, c, t)
+                    assert maxerr(got, want) < TOL[dt], (name, c, t)
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -109,7 +130,7 @@ def test_controlled_gate_sweep_n13(qs, dt):
                     s.apply_ctrl(c, t, m)
                     O.apply_ctrl(want, c, t, m)
         got = s.to_numpy()
-    assert np.max(np.abs(got - want)) < 20 * TOL[dt]
+    assert maxerr(got, want) < TOL[dt]
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -149,9 +170,9 @@ def test_random_circuit_n20(qs, dt, mode):
         probs = s.probs()
         nrm = s.norm()
         p.close()
-    assert np.max(np.abs(got - want)) < TOL[dt]
-    assert np.max(np.abs(marg - O.marginals(want))) < RED_TOL[dt]
-    assert np.max(np.abs(probs - O.probs(want))) < RED_TOL[dt]
+    assert maxerr(got, want) < TOL[dt]
+    assert maxerr(marg, O.marginals(want)) < RED_TOL[dt]
+    assert maxerr(probs, O.probs(want)) < RED_TOL[dt]
     assert abs(nrm - 1.0) < (1e-12 if dt == 1 else 1e-5)
 
 
@@ -173,7 +194,7 @@ def test_tile_sizes(qs, dt, tile_bits):
         p.close()
     assert sum(x["n_gates"] for x in st) == len(gates)
     assert any(x["kind"] == "tile" for x in st)
-    assert np.max(np.abs(got - want)) < 5 * TOL[dt]
+    assert maxerr(got, want) < TOL[dt]
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -188,7 +209,7 @@ def test_small_states_whole_state_tile(qs, dt, n):
     with upload(qs, n, dt, psi) as s:
         s.run(gates)
         got = s.to_numpy()
-    assert np.max(np.abs(got - want)) < TOL[dt]
+    assert maxerr(got, want) < TOL[dt]
 
 
 def _perm_circuit(n, count, seed):
@@ -233,7 +254,7 @@ def test_qft_closed_form_n18(qs, dt):
         s.run(G.qft_circuit(n))
         got = s.to_numpy()
     want = O.qft_basis_amplitudes(n, x, np.arange(1 << n))
-    assert np.max(np.abs(got - want)) < TOL[dt]
+    assert maxerr(got, want) < TOL[dt]
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -246,11 +267,11 @@ def test_reductions(qs, dt, n):
     terms = G.terms(rows)
     with upload(qs, n, dt, psi) as s:
         assert abs(s.norm() - O.norm2(ref)) < 1e-13
-        assert np.max(np.abs(s.marginals() - O.marginals(ref))) < 1e-13
+        assert maxerr(s.marginals(), O.marginals(ref)) < 1e-13
         for k in range(n):
             assert abs(s.prob(k) - O.marginals(ref)[k]) < 1e-13
-        assert abs(s.expect(terms) - O.expect(ref, terms)) < 1e-12
-        assert np.max(np.abs(s.probs() - O.probs(ref))) < 1e-15
+        assert maxerr(s.expect(terms), O.expect(ref, terms)) < 1e-12
+        assert maxerr(s.probs(), O.probs(ref)) < 1e-15
 
 
 def test_reductions_are_deterministic(qs):
@@ -279,11 +300,11 @@ def test_adjoint_gradients_match_oracle(qs, dt):
     larger n as grouped tile passes (n = 14 appears twice: a two-member group)."""
     insts = _grad_instances((2, 4, 6, 9, 13, 14, 14, 15))
     e, gr = qs.grad(insts, dt)
-    tol = 1e-10 if dt == 1 else 2e-4
+    tol = GRAD_TOL[dt]
     for i, inst in enumerate(insts):
         e_ref, g_ref = O.grad(inst["n"], inst["gates"], inst["theta"], inst["terms"])
-        assert abs(e[i] - e_ref) < tol, (i, inst["n"])
-        assert np.max(np.abs(gr[i] - g_ref)) < tol, (i, inst["n"])
+        assert maxerr(e[i], e_ref) < tol, (i, inst["n"])
+        assert maxerr(gr[i], g_ref) < tol, (i, inst["n"])
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -292,14 +313,14 @@ def test_batch_graph_replay_with_new_angles(qs, dt):
     b = qs.Batch(insts, dt)
     st = b.stats()
     assert st["small"] >= 2 and st["groups"] >= 1
-    tol = 1e-10 if dt == 1 else 2e-4
+    tol = GRAD_TOL[dt]
     for rep in range(2):
         thetas = [G.angles(len(x["theta"]), 100 * rep + k) for k, x in enumerate(insts)]
         e, gr = b.execute(thetas)
         for i, inst in enumerate(insts):
             e_ref, g_ref = O.grad(inst["n"], inst["gates"], thetas[i], inst["terms"])
-            assert abs(e[i] - e_ref) < tol
-            assert np.max(np.abs(gr[i] - g_ref)) < tol
+            assert maxerr(e[i], e_ref) < tol
+            assert maxerr(gr[i], g_ref) < tol
     e2, g2 = b.execute(None)  # the last angles again: identical (deterministic reductions)
     assert np.array_equal(e2, e) and all(np.array_equal(a, c) for a, c in zip(g2, gr))
     b.close()
@@ -333,8 +354,8 @@ def test_full_size_qft30_and_inverse_c128(qs):
         nrm = s.norm()
         p.close()
     want = O.qft_basis_amplitudes(n, x, ys)
-    assert np.max(np.abs(vals - want)) < 1e-12
-    assert abs(nrm - 1.0) < 1e-11
+    assert maxerr(vals, want) < 1e-12
+    assert maxerr(nrm, 1.0) < 1e-11
 
 
 def test_invalid_arguments_on_live_state(qs):
@@ -364,7 +385,7 @@ def test_c128_arithmetic_modes_deep_circuit(qs, arith, tile_bits):
         p.execute()
         got = s.to_numpy()
         p.close()
-    err = float(np.max(np.abs(got - want)))
+    err = float(maxerr(got, want))
     print(f"deep circuit n={n} {len(gates)} gates arith={arith} tile_bits={tile_bits}: max-abs error {err:.3e}")
     assert err < TOL[1]
 
@@ -378,7 +399,7 @@ def test_c128_df_error_at_n22_random(qs):
     with qs.State.create(n, 1) as s:
         s.run(gates)
         got = s.to_numpy()
-    err = float(np.max(np.abs(got - want)))
+    err = float(maxerr(got, want))
     print(f"n={n} 600 gates double-float max-abs error {err:.3e}")
     assert err < 1e-13
 
@@ -395,7 +416,7 @@ def test_autotuner_picks_a_valid_shape_and_stays_exact(qs, dt):
     with qs.State.create(n, dt) as s:
         s.run(gates)  # planned with the tuned shape
         got = s.to_numpy()
-    assert np.max(np.abs(got - want)) < TOL[dt]
+    assert maxerr(got, want) < TOL[dt]
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -418,7 +439,7 @@ def test_single_qubit_fusion_matches_unfused_and_oracle(qs, dt):
             p.close()
     assert outs[qs.PLAN_DEFAULT][0] < outs[qs.PLAN_NO_MERGE | qs.PLAN_NO_PHASE_RUNS][0] == len(gates)
     for flags, (_, got) in outs.items():
-        assert np.max(np.abs(got - want)) < 5 * TOL[dt]
+        assert maxerr(got, want) < TOL[dt]
     xx = G.concat([G.gate_u1(2, G.MAT_X), G.gate_u1(2, G.MAT_X), G.gate_cu(0, 5, G.MAT_X), G.gate_u1(9, G.MAT_X)])
     with upload(qs, n, dt, psi) as s:
         p = s.plan(xx)
@@ -472,7 +493,7 @@ def test_phase_runs_match_oracle_and_unfused_runs(qs, dt, tile_bits):
             p.execute()
             got = s.to_numpy()
             p.close()
-        assert np.max(np.abs(got - want)) < 5 * TOL[dt], flags
+        assert maxerr(got, want) < TOL[dt], flags
     assert ops[qs.PLAN_DEFAULT] < ops[qs.PLAN_NO_PHASE_RUNS]
 
 
@@ -499,7 +520,7 @@ def test_phase_runs_whole_state_tile(qs, dt, n):
         p.execute()
         got = s.to_numpy()
         p.close()
-    assert np.max(np.abs(got - want)) < 5 * TOL[dt]
+    assert maxerr(got, want) < TOL[dt]
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -517,7 +538,7 @@ def test_qft_closed_form_n20_phase_runs(qs, dt, tile_bits):
         p.close()
     assert counts[1][3] < n * (n - 1) // 2  # most controlled phases went into runs
     want = O.qft_basis_amplitudes(n, x, np.arange(1 << n))
-    assert np.max(np.abs(got - want)) < TOL[dt]
+    assert maxerr(got, want) < TOL[dt]
 
 
 def _hot_qubit_circuit(n, count, seed):
@@ -568,7 +589,7 @@ def test_hot_qubit_circuits_match_oracle(qs, dt, tile_bits):
             p.execute()
             got = s.to_numpy()
             p.close()
-        assert np.max(np.abs(got - want)) < 5 * TOL[dt], flags
+        assert maxerr(got, want) < TOL[dt], flags
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -610,7 +631,7 @@ def test_small_tiles_many_waves_n22(qs):
         p.execute()
         got = s.to_numpy()
         p.close()
-    assert np.max(np.abs(got - want)) < TOL[1]
+    assert maxerr(got, want) < TOL[1]
 
 
 def test_c128_norm_drift_over_many_passes(qs):
@@ -630,9 +651,9 @@ def test_c128_norm_drift_over_many_passes(qs):
         nrm = s.norm()
         got = s.to_numpy()
         p.close()
-    assert abs(nrm - 1.0) < 1e-11
+    assert maxerr(nrm, 1.0) < 1e-11
     want = O.qft_basis_amplitudes(n, x, np.arange(1 << n))
-    assert np.max(np.abs(got - want)) < TOL[1]
+    assert maxerr(got, want) < TOL[1]
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -670,7 +691,7 @@ def test_special_phase_and_balanced_gates_in_tiles(qs, dt):
             p.execute()
             got = s.to_numpy()
             p.close()
-        assert np.max(np.abs(got - want)) < 5 * TOL[dt], tile_bits
+        assert maxerr(got, want) < TOL[dt], tile_bits
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -697,8 +718,8 @@ def test_random_shapes_against_oracle(qs, dt):
             p.execute()
             got = s.to_numpy()
             p.close()
-        err = float(np.max(np.abs(got - want)))
-        assert err < 5 * TOL[dt], (case, n, b, b0, err)
+        err = float(maxerr(got, want))
+        assert err < TOL[dt], (case, n, b, b0, err)
 
 
 def _general_heavy_circuit(n, seed, count=300):
@@ -760,10 +781,10 @@ def test_prp_form_matches_full_products_and_oracle(qs, n, tile_bits):
             p.execute()
             got[flags] = s.to_numpy()
             p.close()
-        assert np.max(np.abs(got[flags] - want)) < 5 * TOL[dt], flags
+        assert maxerr(got[flags], want) < TOL[dt], flags
     # every form taken: phase-shear-phase, H-like without scalar, trailing phase handed over
     assert np.all(prp[qs.PLAN_DEFAULT] > 0) and not np.any(prp[qs.PLAN_NO_PRP])
-    assert np.max(np.abs(got[qs.PLAN_DEFAULT] - got[qs.PLAN_NO_PRP])) < 5 * TOL[dt]
+    assert maxerr(got[qs.PLAN_DEFAULT], got[qs.PLAN_NO_PRP]) < TOL[dt]
 
 
 @pytest.mark.parametrize("n", [10, 20])
@@ -783,7 +804,7 @@ def test_prp_form_norm_and_closed_form(qs, n):
         got = s.to_numpy()
         nrm = s.norm()
         p.close()
-    assert np.max(np.abs(got - expected_input(psi, dt))) < 5 * TOL[dt]
+    assert maxerr(got, expected_input(psi, dt)) < TOL[dt]
     assert abs(nrm - 1.0) < 1e-12
 
 
@@ -802,7 +823,7 @@ def test_balanced_without_scalar_closed_form_and_oracle(qs, n):
         p.execute()
         got = s.to_numpy()
         p.close()
-    assert np.max(np.abs(got - 2.0 ** (-n / 2))) < TOL[dt]
+    assert maxerr(got, 2.0 ** (-n / 2)) < TOL[dt]
     h = G.MAT_H
     shapes = [h, (h[1], h[0], h[3], h[2]), (h[2], h[3], h[0], h[1]), (h[0], h[1], -h[2], -h[3])]
     rng = G.SplitMix64(606 + n)
@@ -826,4 +847,4 @@ def test_balanced_without_scalar_closed_form_and_oracle(qs, n):
             p.execute()
             res[flags] = s.to_numpy()
             p.close()
-        assert np.max(np.abs(res[flags] - want)) < 5 * TOL[dt], flags
+        assert maxerr(res[flags], want) < TOL[dt], flags
