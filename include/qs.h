@@ -92,7 +92,12 @@ QS_API qs_status qs_create(int n, qs_dtype dt, void* cuda_stream, qs_state** out
 
 /* Wrap caller-owned device memory of 2^n amplitudes (interleaved re, im;
  * 16-byte aligned for complex128, 8-byte for complex64) without copying.
- * The caller keeps the memory alive until after qs_destroy. */
+ * The state belongs to the current device: where the CUDA runtime can
+ * classify dev_ptr, it must be device memory of that device (or managed
+ * memory), else QS_EINVAL.  The caller keeps the memory alive until after
+ * qs_destroy, and does not read or write it from other streams while this
+ * library's work on the state's stream is in flight (a plan's passes may hold
+ * it in an intermediate form, see qs_plan_execute). */
 QS_API qs_status qs_wrap(void* dev_ptr, int n, qs_dtype dt, void* cuda_stream, qs_state** out);
 
 /* Release the handle (and the memory, for qs_create).  NULL is accepted. */
@@ -137,8 +142,8 @@ enum {
     QS_PLAN_ARITH_F64 = 4,  /* complex128: native FP64 instructions for the gate arithmetic.
                                Without it, fused tile passes of complex128 states compute in
                                double-float form on the FP32 pipes (each double carried as an
-                               unevaluated float pair of about 48 bits; storage stays IEEE
-                               double): faster on GPUs whose FP64 rate is a small fraction of
+                               unevaluated float pair of about 48 bits; the state is IEEE
+                               double whenever no plan is running, see qs_plan_execute): faster on GPUs whose FP64 rate is a small fraction of
                                FP32, with a per-gate error of order 2^-44 relative to the
                                amplitudes involved instead of 2^-53. */
     QS_PLAN_DRY_RUN = 8,    /* plan on the host only (no device memory); cannot execute */

@@ -155,6 +155,22 @@ qs_status qs_wrap(void* dev_ptr, int n, qs_dtype dt, void* stream, qs_state** ou
     s->owned = false;
     s->stream = (cudaStream_t)stream;
     cudaGetDevice(&s->device);
+    // Where the runtime can classify the pointer, it must be device (or managed)
+    // memory of the current device: the state's kernels launch there.
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, dev_ptr) == cudaSuccess) {
+        if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+            delete s;
+            return fail(QS_EINVAL, "pointer is not device memory");
+        }
+        if (attr.type == cudaMemoryTypeDevice && attr.device != s->device) {
+            delete s;
+            return fail(QS_EINVAL, "pointer belongs to device " + std::to_string(attr.device) +
+                                       " but device " + std::to_string(s->device) + " is current");
+        }
+    } else {
+        cudaGetLastError();  // no device or driver here: the pointer cannot be checked
+    }
     *out = s;
     return QS_OK;
 }

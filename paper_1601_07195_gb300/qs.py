@@ -164,7 +164,8 @@ class State:
         if stream is None:
             stream = torch.cuda.current_stream(tensor.device)
         h = _vp()
-        _check(load().qs_wrap(tensor.data_ptr(), n, dt, _stream_handle(stream), ctypes.byref(h)))
+        with torch.cuda.device(tensor.device):  # the state belongs to the tensor's device
+            _check(load().qs_wrap(tensor.data_ptr(), n, dt, _stream_handle(stream), ctypes.byref(h)))
         return cls(h.value, n, dt, keepalive=tensor)
 
     @property
