@@ -101,19 +101,53 @@ _DF_FLOPS_BALANCED_FREE = 22.0
 # phase-shear-phase without the trailing product by z (qs_plan_pass_prp counts[2]): 148 - 44 per pair
 _DF_FLOPS_PRP_NZ = 52.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
-# DRAM bytes (read + write) of one double-float tile launch, from the ncu capture
-# of the n=26 case (profiles/k_tile_df_c128_n26_full.md); a tile pass reads and
-# writes the whole state once, so traffic scales with 2^n.  Update (or set to
-# None) whenever the kernel changes.
-DF_TILE_TRAFFIC_N26 = 1.073906e9 + 1.012308e9
-# warp instructions and duration of that n=26 launch (smsp__inst_executed.sum,
-# gpu__time_duration.sum): the kernel is bound by instruction issue, whose peak
-# is 152 SMs x 4 schedulers x 1 warp instruction per clock.  Update (or set to
-# None) with DF_TILE_TRAFFIC_N26.
-DF_TILE_ISSUE_N26 = (1.244201e9, 1.380032e-3)
-ISSUE_PEAK_PER_S = 152 * 4 * 2.07e9
-# the same for the complex64 tile kernel, one n=27 launch (profiles/k_tile_c64_n27_full.md)
-C64_TILE_TRAFFIC_N27 = 1.074006e9 + 1.012051e9
+FFMA_MEASURED_TFLOPS = 74.2  # a dependent-chain-free FFMA loop on this GPU (152 SMs, 2.07 GHz)
+ISSUE_PEAK_PER_S = 152 * 4 * 2.07e9  # 152 SMs x 4 schedulers x 1 warp instruction per clock
+HBM_FALLBACK_GBS = 6800.0  # used only when no measured copy bandwidth is available
+
+# Counters of one launch of each tile kernel from an ncu capture of a small case:
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum), warp instructions
+# (smsp__inst_executed.sum) and duration (gpu__time_duration.sum), with the
+# SHA-256 of the kernel's source files at capture time.  A tile pass reads and
+# writes the whole state once, so DRAM bytes scale with 2^n.  When the sources
+# no longer hash to `sha`, the kernel has changed since the capture and its
+# counters are reported as null.
+CSRC = os.path.join(ROOT, "paper_1601_07195_gb300", "csrc")
+NCU_COUNTERS = {
+    "df": {"kernel": "k_tile_df_p<12>", "sources": ["tile_df.cu", "tile_df_ops.cuh", "df.cuh"],
+           "sha": None, "n": 26, "dram_bytes": None, "warp_inst": None, "ms": None},
+    "c64": {"kernel": "k_tile_p<float, 12>", "sources": ["tile.cu", "tile_ops.cuh"],
+            "sha": None, "n": 27, "dram_bytes": None, "warp_inst": None, "ms": None},
+}
+
+
+def sources_sha(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_counters(kind):
+    """The capture's counters for tile kernel `kind`, or None when none is
+    recorded or the kernel's sources changed since it was taken."""
+    c = NCU_COUNTERS.get(kind)
+    if not c or c["sha"] is None or c["sha"] != sources_sha(c["sources"]):
+        return None
+    return c
+
+
+def hbm_peak():
+    """(GB/s, source) of the HBM roofline: the measured copy bandwidth, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
 
 
 def gate_cost(g, n, s, table=None):
@@ -138,14 +172,15 @@ def gate_cost(g, n, s, table=None):
 _CLASSES = ["general", "real", "diag", "diag1", "antidiag", "perm"]
 
 
-def issue_summary(df):
-    """Instruction issue of the double-float tile kernel from its ncu capture
-    (None for complex64 or when no capture matches the kernel)."""
-    if not (df and DF_TILE_ISSUE_N26):
+def issue_summary(kind):
+    """Instruction issue of tile kernel `kind` from its ncu capture (None when the
+    capture is missing or stale)."""
+    c = ncu_counters(kind)
+    if c is None or c["warp_inst"] is None:
         return None
-    inst, sec = DF_TILE_ISSUE_N26
-    return {"warp_instructions": inst, "launch_ms": sec * 1e3, "frac_of_issue_peak": inst / sec / ISSUE_PEAK_PER_S,
-            "source": "ncu capture of one n=26 launch (profiles/k_tile_df_c128_n26_full.md); "
+    return {"warp_instructions": c["warp_inst"], "launch_ms": c["ms"],
+            "frac_of_issue_peak": c["warp_inst"] / (c["ms"] / 1e3) / ISSUE_PEAK_PER_S,
+            "source": f"ncu capture of one n={c['n']} launch of {c['kernel']}; "
                       "issue peak 152 SMs x 4 schedulers x 2.07 GHz"}
 
 
@@ -219,26 +254,54 @@ class ClockSampler:
 
 # ---- measurement legs ----------------------------------------------------------------
 
-def cpu_baseline(n, gates, s_bytes, target_s=15.0):
-    """Time the CPU FP64 oracle, as it stands, on a bounded sample of the workload:
-    gates spread evenly over the circuit, applied to the n-qubit state on the host."""
-    from oracle import oracle as O
-    O.build()
+def _oracle_sample(O, n, gates, s_bytes, target_s, parallel):
+    """Gates spread evenly over the circuit, applied to the n-qubit host state by the
+    oracle until target_s seconds of work: (GB/s in the paper's convention, gates used, s)."""
     psi = O.basis(n, G.random_basis(n, G.SEEDS["qft30"]))
-    idx = np.linspace(0, len(gates) - 1, 64).astype(int)
+    idx = np.linspace(0, len(gates) - 1, 256).astype(int)
     done_bytes, elapsed, used = 0.0, 0.0, []
     for j in idx:
         t0 = time.perf_counter()
-        O.run(psi, gates[j:j + 1])
+        O.run(psi, gates[j:j + 1], parallel=parallel)
         elapsed += time.perf_counter() - t0
         done_bytes += gate_cost(gates[j], n, s_bytes)[0]
         used.append(int(j))
         if elapsed > target_s:
             break
-    return {"value": done_bytes / elapsed / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+    return done_bytes / elapsed / 1e9, used, elapsed
+
+
+def cpu_baseline(n, gates, s_bytes, target_s=10.0):
+    """Time the CPU FP64 oracle, as it stands, on a bounded sample of the workload:
+    its OpenMP build on every host core, and its single-threaded build."""
+    from oracle import oracle as O
+    O.build()
+    v, used, el = _oracle_sample(O, n, gates, s_bytes, target_s, parallel=True)
+    v1, used1, el1 = _oracle_sample(O, n, gates, s_bytes, target_s, parallel=False)
+    return {"value": v, "unit": "GB/s", "cores": O.threads(), "kind": "oracle",
             "sample": f"{len(used)} gates spread over the n={n} workload (circuit positions {used[0]}..{used[-1]}), "
-                      f"applied by the single-threaded FP64 oracle to a 2^{n} complex128 host state; "
-                      f"{elapsed:.1f} s of CPU work"}
+                      f"applied by the oracle's OpenMP build (-O3 -fopenmp, {O.threads()} threads) to a 2^{n} "
+                      f"complex128 host state; {el:.1f} s of work",
+            "cpu_model": _cpu_model(),
+            "single_thread": {"value": v1, "unit": "GB/s", "cores": 1,
+                              "sample": f"{len(used1)} gates, single-threaded -O2 build; {el1:.1f} s of work"}}
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def run_reference(args):
@@ -252,13 +315,13 @@ def run_reference(args):
     from oracle import oracle as O
     O.build()
     psi = O.basis(n, x)
-    idx = np.linspace(0, len(gates) - 1, 3 * (args.steps + args.warmup)).astype(int)
+    idx = np.linspace(0, len(gates) - 1, 8 * (args.steps + args.warmup)).astype(int)
     chunks = np.array_split(idx, args.steps + args.warmup)
     times, bts = [], []
     for i, ch in enumerate(chunks):
         t0 = time.perf_counter()
         for j in ch:
-            O.run(psi, gates[j:j + 1])
+            O.run(psi, gates[j:j + 1], parallel=True)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
@@ -269,8 +332,9 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"QFT({n}) on a random basis state + 1000-gate random circuit, complex128",
                        "n": n, "gates": len(gates)},
-            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"3 gates per step spread over the n={n} workload, single-threaded oracle"},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": O.threads(), "kind": "oracle",
+                             "sample": f"8 gates per step spread over the n={n} workload, the oracle's OpenMP "
+                                       f"build on {O.threads()} host threads", "cpu_model": _cpu_model()},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -295,16 +359,23 @@ def secondary_gradients(qs, dtype, torch):
     t_replay = (time.perf_counter() - t0) / reps
     bstats = batch.stats()
     batch.close()
-    # finite-difference comparator: 2P+1 energy evaluations per instance, on a sample
-    sample = insts[:2]
-    t0 = time.perf_counter()
-    for inst in sample:
-        n, th = inst["n"], inst["theta"]
+    # finite-difference comparator: 2P+1 planned energy evaluations per instance (complex128
+    # central differences, h = 1e-6), one instance of every qubit count in the batch, weighted
+    # by how many instances of that count the batch holds
+    by_n = {}
+    for inst in insts:
+        by_n.setdefault(inst["n"], []).append(inst)
+    fd_s = {}
+    for n, group in sorted(by_n.items()):
+        inst = group[0]
+        th = inst["theta"]
         with qs.State.create(n, dtype, stream=stream) as st:
             def energy(theta):
                 st.init_basis(0)
                 st.run(inst["gates"], theta)
                 return st.expect(inst["terms"])
+            energy(th)
+            t0 = time.perf_counter()
             energy(th)
             for p in range(len(th)):
                 tp, tm = th.copy(), th.copy()
@@ -312,15 +383,31 @@ def secondary_gradients(qs, dtype, torch):
                 tm[p] -= 1e-6
                 energy(tp)
                 energy(tm)
-    t_fd = (time.perf_counter() - t0) / len(sample)
+            fd_s[n] = time.perf_counter() - t0
+    fd_total = sum(fd_s[n] * len(g) for n, g in by_n.items())
+    # arithmetic the batch applies, for its bound: forward on psi, then the reverse sweep on
+    # phi and lambda, every gate once per state; RY (real) and RZ (diagonal) updates at
+    # 44 FP32 flops per amplitude in double-float (complex128) or 6 in FP32 (complex64),
+    # CNOTs as moves; the gradient products and lambda = H psi are left out (an underestimate)
+    per_amp = 44.0 if dtype == 1 else 6.0
+    flops = sum(3 * 2 * inst["n"] * 8 * per_amp * float(1 << inst["n"]) for inst in insts)  # L = 8 layers
+    tf = flops / t_adj / 1e12
     return {"metric": "batched adjoint-gradient circuits/sec", "value": len(insts) / t_adj, "unit": "circuits/s",
             "instances": len(insts), "dtype": "c128" if dtype == 1 else "c64", "setup_s": t_setup,
             "s_per_execution_new_angles": t_adj, "s_per_execution_same_angles": t_replay,
             "persistent_small_instances": bstats["small"], "structure_groups": bstats["groups"],
             "launches_per_execution": bstats["launches"],
             "timing": "host wall clock per qs_batch_execute (angle staging + graph replay + results), mean of 3",
-            "fd_circuits_per_s": 1.0 / t_fd, "fd_sample": len(sample),
-            "speedup_vs_fd": (len(insts) / t_adj) * t_fd}
+            "fd_circuits_per_s": len(insts) / fd_total,
+            "fd_sample": "one instance per qubit count (n = %d..%d), weighted by the batch's counts" % (min(by_n),
+                                                                                                    max(by_n)),
+            "fd_s_by_n": {str(k): v for k, v in fd_s.items()},
+            "speedup_vs_fd": fd_total / t_adj,
+            "roofline": {"bound": "alu", "achieved": tf, "unit": "TFLOP/s",
+                         "peak": FFMA_MEASURED_TFLOPS, "frac": tf / FFMA_MEASURED_TFLOPS,
+                         "peak_source": "measured FFMA rate of this GPU",
+                         "what": "estimate: FP32 flops of the rotation updates on psi, phi and lambda "
+                                 "(lower bound on the arithmetic), per second of execution"}}
 
 
 def job_value(local_ms, step_bytes, steps, world, dist=None):
@@ -366,52 +453,49 @@ def run_ours(args):
     plan_ms = 1e3 * (time.perf_counter() - t0)
     passes = plan.passes()
     device_ops = plan.stats()["device_ops"]
-    plan.set_timing(args.steps)
-
-    def step():
-        state.init_basis(x)
-        plan.execute()
-        nrm = state.norm()
-        marg = state.marginals()
-        return nrm, marg
-
-    for _ in range(args.warmup):
-        nrm, marg = step()
-    if abs(nrm - 1.0) > (1e-9 if dtype == qs.QS_C128 else 1e-4):  # complex64: FP32 rounding drift
-        raise RuntimeError(f"norm drifted: {nrm}")
+    hbm, hbm_src = hbm_peak()
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-        ev1.record(stream)
-        ev1.synchronize()
-    barrier()
-    value, ms_per_step = job_value(ev0.elapsed_time(ev1), step_bytes, args.steps, world,
-                                   dist if world > 1 else None)
+    def timed_steps(pl, steps, warmup):
+        """W untimed and K timed steps of pl (init |x>, the plan, FP64 norm and
+        marginals), CUDA events on the state's stream, clocks sampled meanwhile."""
+        pl.set_timing(steps)
 
-    # per-pass timing of the timed steps (events on the launching stream)
+        def step():
+            state.init_basis(x)
+            pl.execute()
+            return state.norm(), state.marginals()
+
+        for _ in range(warmup):
+            nrm, _ = step()
+        if abs(nrm - 1.0) > (1e-9 if dtype == qs.QS_C128 else 1e-4):  # complex64: FP32 rounding drift
+            raise RuntimeError(f"norm drifted: {nrm}")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for _ in range(steps):
+                step()
+            ev1.record(stream)
+            ev1.synchronize()
+        barrier()
+        times = np.array([pl.pass_times(r) for r in range(steps)])  # steps x passes, events on the same stream
+        return ev0.elapsed_time(ev1), times, clk.summary()
+
+    total_ms, times, clocks = timed_steps(plan, args.steps, args.warmup)
+    value, ms_per_step = job_value(total_ms, step_bytes, args.steps, world, dist if world > 1 else None)
+
     tile_idx = [i for i, p in enumerate(passes) if p["kind"] == "tile"]
-    times = np.array([plan.pass_times(r) for r in range(args.steps)])  # steps x passes
-    pass_flops = []
-    for p in passes:
-        pass_flops.append(sum(gate_cost(gates[j], n, s_bytes)[1] for j in p["gates"]))
     tile_ms = times[:, tile_idx].sum(axis=1).mean() if tile_idx else 0.0
     tile_launch_ms = times[:, tile_idx].mean() if tile_idx else float("nan")
-    tile_flops = sum(pass_flops[i] for i in tile_idx)
     gates_ms = times.sum(axis=1).mean()
-    fp64_tf = tile_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
     df = dtype == qs.QS_C128
-    # FP32 flops of the kernel's own algorithm: double-float update for complex128, plain FP32 for complex64
-    table = _DF_FLOPS if df else _FLOPS
-    fp32_flops = sum(kernel_flops(plan.op_counts(i), n, table) for i in tile_idx)
+    # FP32 flops of the kernel's own algorithm: double-float updates for complex128, plain FP32 for complex64
+    fp32_flops = sum(kernel_flops(plan.op_counts(i), n, _DF_FLOPS if df else _FLOPS) for i in tile_idx)
     if df:  # balanced real and phase-shear-phase updates were counted as real / general ones above
         for i in tile_idx:
             b1, bc = plan.balanced(i)
@@ -420,56 +504,58 @@ def run_ours(args):
             fp32_flops -= (_DF_FLOPS["general"] - _DF_FLOPS_PRP) * N * prp
             fp32_flops -= (_DF_FLOPS_PRP - _DF_FLOPS_PRP_NZ) * N * prp_nz
             fp32_flops -= (_DF_FLOPS["real"] - _DF_FLOPS_BALANCED_FREE) * N * bal_free
-    achieved_tf = fp32_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
-    roofline = {"bound": "alu", "kernel": "k_tile_df (fused tile pass, double-float)" if df else "k_tile_p<float, 12> (fused tile pass, FP32)",
-                "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP32_PEAK_TFLOPS,
-                "traffic": (DF_TILE_TRAFFIC_N26 * 2.0 ** (n - 26)) if (df and DF_TILE_TRAFFIC_N26) else
-                           ((C64_TILE_TRAFFIC_N27 * 2.0 ** (n - 27)) if (not df and C64_TILE_TRAFFIC_N27) else None),
-                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one n=26 launch, "
-                                   "scaled by 2^(n-26)") if df else
-                                  ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one n=27 launch, "
-                                   "scaled by 2^(n-27)"),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; MEASURED_PEAKS.json "
-                               "has no FP32 figure (an FFMA probe on this GPU measured 74.2 TFLOP/s)",
-                "flops_counted": ("FP32 flops of the double-float updates the kernel applies (after in-pass "
-                                  "fusion of same-qubit gates) per touched amplitude: general 104, "
-                                  "real/diagonal/anti-diagonal 44, balanced real (H-like) 34 or 22 without its scalar, "
-                                  "general single-qubit in phase-shear-phase form 74 or 52 without its "
-                                  "trailing phase, permutation 0; a fused phase "
-                                  "run counts as one diagonal update") if df else
-                                 "FP32 flops of the updates the kernel applies",
-                "fp64_equivalent_tflops": fp64_tf,
-                "fp64_equivalent_frac_of_fp64_peak": fp64_tf / FP64_PEAK_TFLOPS,
-                "limiter": ("instruction issue: double-float FP32 arithmetic plus SMEM sweeps and index work "
-                            "(profiles/k_tile_df_c128_n26_full.md)") if df else
-                           ("shared-memory bandwidth: 83% of peak SMEM wavefronts, 86% issue "
-                            "(profiles/k_tile_c64_n27_full.md)"),
-                "instruction_issue": issue_summary(df),
-                "launches_per_step": len(tile_idx), "avg_launch_ms": tile_launch_ms,
-                "hbm_frac_of_measured": (2 * N * s_bytes / (tile_launch_ms / 1e3)) / 6794.8e9 if tile_idx else None}
-
+    fp32_tf = fp32_flops / (tile_ms / 1e3) / 1e12 if tile_ms else 0.0
+    kind = "df" if df else "c64"
+    cnt = ncu_counters(kind)
+    pass_bytes = 2 * N * s_bytes  # one tile pass reads and writes the whole state once
+    achieved = pass_bytes / (tile_launch_ms / 1e3) / 1e9 if tile_idx else 0.0
+    roofline = {
+        "bound": "hbm", "kernel": ("k_tile_df_p<12> (fused tile pass, double-float)" if df
+                                   else "k_tile_p<float, 12> (fused tile pass, FP32)"),
+        "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+        "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured"
+                       else "fallback 6.8 TB/s (no measured copy bandwidth available)",
+        "bytes_per_launch": pass_bytes, "launches_per_step": len(tile_idx), "avg_launch_ms": tile_launch_ms,
+        "traffic": cnt["dram_bytes"] * 2.0 ** (n - cnt["n"]) if cnt else None,
+        "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one n={cnt['n']} launch, "
+                           f"scaled by 2^(n-{cnt['n']})") if cnt else "no ncu capture of the current kernel source",
+        "alu": {"what": ("FP32 flops of the double-float updates the kernel applies after fusion, per touched "
+                         "amplitude: general 104, general in phase-shear-phase form 74 (52 without its trailing "
+                         "phase), real / diagonal / anti-diagonal 44, balanced real 34 (22 without its scalar), "
+                         "permutation 0; a phase run counts as one diagonal update") if df else
+                        "FP32 flops of the updates the kernel applies after fusion",
+                "tflops": fp32_tf, "frac_of_measured_ffma": fp32_tf / FFMA_MEASURED_TFLOPS,
+                "frac_of_derived_fp32_peak": fp32_tf / FP32_PEAK_TFLOPS,
+                "instruction_issue": issue_summary(kind)},
+        "limiter": ("instruction issue of the double-float arithmetic, shared-memory sweeps and index work"
+                    if df else "shared-memory bandwidth and instruction issue"),
+    }
     launches_per_step = 1 + len(passes) + 2 + 2  # init, passes, norm (2 kernels), marginals (2 kernels)
 
     native = None
     if dtype == qs.QS_C128 and not args.no_native:
-        # the same step with native FP64 instructions for the gate arithmetic (1 warm-up, 1 timed)
+        # the same step with native FP64 instructions for the gate arithmetic (the paper's
+        # precision), under the same protocol; fewer steps, each takes about 4 s
         pn = state.plan(gates, flags=qs.PLAN_ARITH_F64)
-        state.init_basis(x)
-        pn.execute()
-        state.norm()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        state.init_basis(x)
-        pn.execute()
-        state.norm()
-        state.marginals()
-        e1.record(stream)
-        e1.synchronize()
-        nms = e0.elapsed_time(e1)
-        native = {"value": world * step_bytes / (nms / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": nms,
-                  "dtype": "f64", "note": "same step, plan flag QS_PLAN_ARITH_F64 (FP64 pipe)"}
+        k_native, w_native = min(args.steps, 5), max(3, min(args.warmup, 3))
+        n_ms, n_times, n_clocks = timed_steps(pn, k_native, w_native)
+        n_value, n_ms_step = job_value(n_ms, step_bytes, k_native, world, dist if world > 1 else None)
+        n_tile = n_times[:, tile_idx].mean() if tile_idx else float("nan")
+        n_tile_ms = n_times[:, tile_idx].sum(axis=1).mean() if tile_idx else 0.0
+        f64_flops = sum(kernel_flops(pn.op_counts(i), n, _FLOPS) for i in tile_idx)
+        f64_tf = f64_flops / (n_tile_ms / 1e3) / 1e12 if n_tile_ms else 0.0
+        native = {"value": n_value, "unit": "GB/s", "ms_per_step": n_ms_step, "steps": k_native,
+                  "warmup": w_native, "dtype": "f64", "clocks": n_clocks,
+                  "note": "same step, plan flag QS_PLAN_ARITH_F64 (IEEE double arithmetic on the FP64 pipe)",
+                  "roofline": {"bound": "alu", "kernel": "k_tile_p<double, 12> (fused tile pass, FP64)",
+                               "achieved": f64_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": f64_tf / FP64_PEAK_TFLOPS,
+                               "peak_source": "derived: 152 SMs x 2 DFMA (4 flop) per clock x 2.07 GHz",
+                               "what": "FP64 flops of the updates the kernel applies after fusion: 14 per "
+                                       "amplitude of a general update, 6 of a real / diagonal / anti-diagonal "
+                                       "one, 0 of a permutation",
+                               "avg_launch_ms": n_tile,
+                               "hbm_frac": pass_bytes / (n_tile / 1e3) / 1e9 / hbm if tile_idx else None}}
         pn.close()
 
     e2e = None
@@ -478,30 +564,33 @@ def run_ours(args):
         host = torch.zeros(1 << n, dtype=torch.complex128 if dtype == qs.QS_C128 else torch.complex64,
                            pin_memory=True)
         host[x] = 1.0
-        e2e_steps = max(1, min(args.steps, 2))
+        e2e_steps = 5
         state.copy_in_ptr(host.data_ptr(), 1 << n)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        parts = [0.0, 0.0, 0.0]  # each call below returns after its work is done
+        parts = [[], [], []]  # each call below returns after its work is done
         for _ in range(e2e_steps):
             ta = time.perf_counter()
             state.copy_in_ptr(host.data_ptr(), 1 << n)
             tb = time.perf_counter()
             state.run(gates)
             tc = time.perf_counter()
-            res = state.marginals()
+            state.marginals()
             td = time.perf_counter()
-            parts[0] += tb - ta
-            parts[1] += tc - tb
-            parts[2] += td - tc
+            parts[0].append(tb - ta)
+            parts[1].append(tc - tb)
+            parts[2].append(td - tc)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         e2e_bytes = gate_bytes + 2 * N * s_bytes  # h2d of the state + marginals read (plus gates)
         e2e = {"value": world * e2e_bytes / e2e_s / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": int(N * s_bytes + gates.nbytes), "d2h_bytes_per_step": int(8 * n),
                "ms_per_step": 1e3 * e2e_s, "steps": e2e_steps,
-               "breakdown_ms": {"h2d_state": 1e3 * parts[0] / e2e_steps, "qs_run": 1e3 * parts[1] / e2e_steps,
-                                "marginals_to_host": 1e3 * parts[2] / e2e_steps}}
+               "breakdown_ms": {"h2d_state": 1e3 * statistics.mean(parts[0]),
+                                "h2d_state_each": [round(1e3 * v, 1) for v in parts[0]],
+                                "qs_run": 1e3 * statistics.mean(parts[1]),
+                                "marginals_to_host": 1e3 * statistics.mean(parts[2])},
+               "h2d_GBps": N * s_bytes / statistics.mean(parts[0]) / 1e9}
         del host
 
     secondary = None
@@ -526,10 +615,11 @@ def run_ours(args):
                                    f"({'complex128' if dtype == qs.QS_C128 else 'complex64'}, n={n})",
                        "n": n, "gates": len(gates), "state_bytes": int(N * s_bytes),
                        "l2": "state larger than L2 (129 MB): no flush needed", "parallelism": f"replicas x{world}",
-                       "arith": ("complex128 state in IEEE double; gate arithmetic in double-float (FP32 pairs, "
-                                 "error-free transforms); native FP64 in native_f64")
+                       "arith": ("complex128 state, IEEE double at plan boundaries; gate arithmetic in "
+                                 "double-float (FP32 pairs, error-free transforms), parity with the FP64 oracle "
+                                 "at 1e-12 on every amplitude of this step; native FP64 in native_f64")
                        if dtype == qs.QS_C128 else "complex64 state, FP32 arithmetic, FP64 reductions"},
-            "hbm_frac_of_measured": value / 6794.8,
+            "effective_over_hbm_peak": value / hbm,
             "breakdown": {"plan_ms": plan_ms, "gates_ms": gates_ms, "tile_ms": tile_ms, "passes": len(passes),
                           "device_ops_after_fusion": device_ops,
                           "tile_passes": len(tile_idx), "gates_in_tile_passes": kinds.get("tile", 0),
@@ -539,7 +629,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "secondary": secondary,
             "native_f64": native,
         }
@@ -584,7 +674,7 @@ def run_random33(args):
         out["runs"].append({"n": n, "dtype": "c128" if dt == qs.QS_C128 else "c64", "gates": len(gates),
                             "passes": plan.stats()["passes"], "ms_per_circuit": ms,
                             "gates_per_s": len(gates) / (ms / 1e3), "GBps": bytes_ / (ms / 1e3) / 1e9,
-                            "hbm_frac_of_measured": bytes_ / (ms / 1e3) / 6794.8e9, "norm_minus_1": nrm - 1.0})
+                            "hbm_frac": bytes_ / (ms / 1e3) / 1e9 / hbm_peak()[0], "norm_minus_1": nrm - 1.0})
         plan.close()
         st.close()
         torch.cuda.empty_cache()

@@ -1,7 +1,7 @@
 """bench.py's roofline accounting, on the CPU: algorithmic bytes per gate in the
 paper's convention (Section 5.2), the FP32 flop counts of the double-float
 updates rebuilt from their parts, the per-pass flop sum over a dry-run plan,
-and the instruction-issue summary."""
+the instruction-issue summary and the roofline peak."""
 
 import ctypes
 
@@ -57,9 +57,23 @@ def test_kernel_flops_of_a_dry_run_plan():
     assert got == pytest.approx(2 * 104 * N + 44 * N * 0.5)
 
 
-def test_issue_summary():
-    s = bench.issue_summary(True)
-    assert 0.0 < s["frac_of_issue_peak"] <= 1.0
-    assert s["frac_of_issue_peak"] == pytest.approx(s["warp_instructions"] / (s["launch_ms"] / 1e3)
-                                                    / (152 * 4 * 2.07e9))
-    assert bench.issue_summary(False) is None
+def test_counters_go_stale_with_the_kernel_source(monkeypatch):
+    """Counters from an ncu capture are used only while the kernel's sources hash
+    to the value recorded with them; the issue summary is their plain ratio."""
+    entry = dict(bench.NCU_COUNTERS["df"], n=26, dram_bytes=2.0e9, warp_inst=1.2e9, ms=1.4)
+    entry["sha"] = bench.sources_sha(entry["sources"])
+    monkeypatch.setitem(bench.NCU_COUNTERS, "df", entry)
+    s = bench.issue_summary("df")
+    assert s["frac_of_issue_peak"] == pytest.approx(1.2e9 / 1.4e-3 / (152 * 4 * 2.07e9))
+    assert bench.ncu_counters("df")["dram_bytes"] == 2.0e9
+    monkeypatch.setitem(bench.NCU_COUNTERS, "df", dict(entry, sha="0" * 16))
+    assert bench.issue_summary("df") is None and bench.ncu_counters("df") is None
+    assert bench.issue_summary("nonexistent") is None
+
+
+def test_hbm_peak_prefers_the_measured_copy_bandwidth(tmp_path, monkeypatch):
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6679.8}')
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.hbm_peak() == (6679.8, "measured")
+    (tmp_path / "MEASURED_PEAKS.json").unlink()
+    assert bench.hbm_peak() == (bench.HBM_FALLBACK_GBS, "fallback")
