@@ -112,6 +112,7 @@ def _declare(lib):
     lib.or_dot_re.restype = ctypes.c_double
     lib.or_apply_gate.argtypes = [_dp, ctypes.c_int, ctypes.c_void_p, _dp, ctypes.c_int, ctypes.c_int]
     lib.or_apply_gate.restype = ctypes.c_int
+    lib.or_apply_dense.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp]
 
 
 def _ptr(a):
@@ -159,6 +160,18 @@ def apply_swap(psi, a, b):
     if not (0 <= a < n and 0 <= b < n and a != b):
         raise ValueError("bad swap qubits")
     _load().or_apply_swap(_ptr(psi.view(np.float64)), n, a, b)
+
+
+def apply_dense(psi, U, parallel=False):
+    """y = U x on every group of 2^q consecutive amplitudes (U: 2^q x 2^q complex,
+    acting on qubits 0..q-1), in place."""
+    n = _state(psi)
+    U = np.ascontiguousarray(U, dtype=np.complex128)
+    q = int(U.shape[0]).bit_length() - 1
+    if U.shape != (1 << q, 1 << q) or not 1 <= q <= min(n, 10):
+        raise ValueError("U must be 2^q x 2^q with 1 <= q <= min(n, 10)")
+    (_load_omp() if parallel else _load()).or_apply_dense(_ptr(psi.view(np.float64)), n, q, _ptr(U.view(np.float64)))
+    return psi
 
 
 def run(psi, gates, theta=None, parallel=False):

@@ -116,6 +116,30 @@ void or_apply_ctrl(double* psi, int n, int c, int t, const double m[8]) {
     }
 }
 
+/* ---- a dense 2^q x 2^q matrix on qubits 0..q-1 -------------------------------
+ * Not in the paper: the product of a run of gates on the q lowest qubits as one
+ * matrix U (row-major, U[r][c] at U[2 (r 2^q + c)], (re, im)), applied to every
+ * group of 2^q consecutive amplitudes x (fixed higher bits): y_r = sum_c U[r][c] x_c,
+ * summed in column order.  1 <= q <= 10. */
+void or_apply_dense(double* psi, int n, int q, const double* U) {
+    uint64_t N = (uint64_t)1 << n, G = (uint64_t)1 << q;
+#pragma omp parallel for schedule(static) if (N / G >= 64)
+    for (uint64_t g = 0; g < N; g += G) {
+        double y[2 * 1024];
+        for (uint64_t r = 0; r < G; ++r) {
+            cplx acc = {0.0, 0.0};
+            for (uint64_t c = 0; c < G; ++c) {
+                cplx u, x;
+                u.re = U[2 * (r * G + c)]; u.im = U[2 * (r * G + c) + 1];
+                x.re = psi[2 * (g + c)]; x.im = psi[2 * (g + c) + 1];
+                acc = cadd(acc, cmul(u, x));
+            }
+            y[2 * r] = acc.re; y[2 * r + 1] = acc.im;
+        }
+        for (uint64_t r = 0; r < G; ++r) { psi[2 * (g + r)] = y[2 * r]; psi[2 * (g + r) + 1] = y[2 * r + 1]; }
+    }
+}
+
 /* ---- SWAP(a, b): |.. x_a .. x_b ..> -> |.. x_b .. x_a ..> (index permutation) */
 void or_apply_swap(double* psi, int n, int a, int b) {
     uint64_t N = (uint64_t)1 << n;

@@ -19,6 +19,7 @@ PINS = [
     lambda: P.test_swap_equals_pauli_formula(3),
     lambda: P.test_qft_of_basis_state_closed_form(6),
     lambda: P.test_qft_closed_form_routines_match_the_circuit(3),
+    lambda: P.test_dense_block_equals_kronecker_operator(6, 3),
     lambda: P.test_permutation_circuits_are_bit_exact(),
     lambda: P.test_reductions_brute_force(),
     lambda: P.test_gradient_closed_form_ry_z(),
@@ -48,6 +49,8 @@ MUTANTS = [
     ("QFT closed-form phase sign", "psi[2 * y + 1] = scale * sin(ph);", "psi[2 * y + 1] = -scale * sin(ph);", None),
     ("QFT closed-form phase product", "double ph = w * (double)((x * y) & mask);",
      "double ph = w * (double)((x + y) & mask);", None),
+    ("dense block transposed", "u.re = U[2 * (r * G + c)]; u.im = U[2 * (r * G + c) + 1];",
+     "u.re = U[2 * (c * G + r)]; u.im = U[2 * (c * G + r) + 1];", None),
     ("half angle", "double c = cos(0.5 * theta), s = sin(0.5 * theta);", "double c = cos(theta), s = sin(theta);", None),
 ]
 

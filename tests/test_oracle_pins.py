@@ -184,6 +184,63 @@ def test_sampled_gradient_equals_the_full_gradient():
             assert max(abs(gs[k] - gr[k]) for k in gs) < 1e-14
 
 
+def _gate_operator(g, q):
+    """The 2^q x 2^q operator of one gate record on qubits < q, from numpy.kron
+    (qubit q-1 leftmost, Eq. 1 with the stride-2^k order)."""
+    m = g["m"]
+    Q = np.array([[m[0] + 1j * m[1], m[2] + 1j * m[3]], [m[4] + 1j * m[5], m[6] + 1j * m[7]]])
+    if int(g["kind"]) == G.G_U1:
+        return _embed(Q, g["t"], q)
+    P0, P1 = np.diag([1.0, 0.0]), np.diag([0.0, 1.0])
+    return _kron_list([P0 if k == g["c"] else np.eye(2) for k in reversed(range(q))]) + \
+        _kron_list([P1 if k == g["c"] else (Q if k == g["t"] else np.eye(2)) for k in reversed(range(q))])
+
+
+def _kron_list(ms):
+    out = np.eye(1)
+    for m in ms:
+        out = np.kron(out, m)
+    return out
+
+
+def _embed(Q, k, q):
+    return _kron_list([Q if j == k else np.eye(2) for j in reversed(range(q))])
+
+
+@pytest.mark.parametrize("n,q", [(3, 1), (6, 3), (8, 6), (8, 8)])
+def test_dense_block_equals_kronecker_operator(n, q):
+    """or_apply_dense applies I (x) U: qubits 0..q-1 are the low bits of the index."""
+    rng = np.random.default_rng(n * 10 + q)
+    U = rng.standard_normal((1 << q, 1 << q)) + 1j * rng.standard_normal((1 << q, 1 << q))
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    want = np.kron(np.eye(1 << (n - q)), U) @ psi
+    for parallel in (False, True):
+        got = O.apply_dense(psi.copy(), U, parallel=parallel)
+        assert np.max(np.abs(got - want)) < 1e-12
+
+
+def test_dense_block_of_a_gate_run_equals_the_run():
+    """The product of a run of gates on the lowest q qubits, built from Kronecker
+    operators, applied as one block reproduces the oracle's gate-by-gate run."""
+    n, q = 12, 6
+    rng = G.SplitMix64(77)
+    gates = []
+    for j in range(40):
+        t = j % q
+        if j % 3 == 2:
+            gates.append(G.gate_cu((t + 1 + j % (q - 1)) % q, t, G.haar_2x2(rng)))
+        else:
+            gates.append(G.gate_u1(t, G.haar_2x2(rng)))
+    gates = G.concat(gates)
+    U = np.eye(1 << q, dtype=np.complex128)
+    for g in gates:
+        U = _gate_operator(g, q) @ U
+    psi = np.random.default_rng(5).standard_normal(1 << n) + 0j
+    psi /= np.linalg.norm(psi)
+    want = O.run(psi.copy(), gates)
+    assert np.max(np.abs(O.apply_dense(psi.copy(), U) - want)) < 1e-13
+
+
 def test_qft_gate_counts_match_table3():
     rows = [tuple(map(int, ln.split())) for ln in open(_golden("qft_gate_counts.txt")) if ln.strip() and not ln.startswith("#")]
     assert len(rows) == 12
