@@ -55,9 +55,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 comparison step")
-    ap.add_argument("--workload", default="qft30", choices=["qft30", "random33", "adjoint28", "sweeps", "batch512"],
+    ap.add_argument("--parts", default="gate1q,ctrl,iqft", help="sweeps: which of gate1q, ctrl, iqft to run")
+    ap.add_argument("--workload", default="qft30", choices=["qft30", "random33", "adjoint28", "sweeps", "batch512", "dense"],
                     help="qft30: the headline n=30 step; random33: n=33 complex128 / n=34 complex64 500-gate "
-                         "circuits and the n=26 error table; adjoint28: n=28 complex64 adjoint vs parameter shift")
+                         "circuits and the n=26 error table; adjoint28: n=28 complex64 adjoint vs parameter shift; "
+                         "dense: the tensor-core 64x64 block vs the SIMT tile pass on gate runs on qubits 0..5")
     return ap.parse_args()
 
 
@@ -115,9 +117,13 @@ HBM_FALLBACK_GBS = 6800.0  # used only when no measured copy bandwidth is availa
 CSRC = os.path.join(ROOT, "paper_1601_07195_gb300", "csrc")
 NCU_COUNTERS = {
     "df": {"kernel": "k_tile_df_p<12>", "sources": ["tile_df.cu", "tile_df_ops.cuh", "df.cuh"],
-           "sha": None, "n": 26, "dram_bytes": None, "warp_inst": None, "ms": None},
+           "sha": "8ef778991bf53526", "n": 26, "dram_bytes": 1.073873e9 + 1.013033e9, "warp_inst": 2.532212736e9,
+           "ms": 2.721536},
     "c64": {"kernel": "k_tile_p<float, 12>", "sources": ["tile.cu", "tile_ops.cuh"],
             "sha": None, "n": 27, "dram_bytes": None, "warp_inst": None, "ms": None},
+    "dense": {"kernel": "k_dense6_tc", "sources": ["dense_tc.cu"],
+              "sha": "3d24d6586cc3e940", "n": 25, "dram_bytes": 268.633856e6 + 206.706176e6, "warp_inst": 37385190.0,
+              "ms": 0.11456},
 }
 
 
@@ -755,57 +761,147 @@ def run_adjoint28(args):
 
 
 def run_sweeps(args):
-    """Per-target single-gate GB/s at n=30 complex128 (strided kernels), the
-    controlled-gate (c, t) grid at n=30 (the Fig. 6 analogue), and IQFT fused
-    vs unfused for n = 18..30 (the Fig. 8 analogue)."""
+    """Per-target single-gate GB/s at n (default 30) complex128 (strided kernels),
+    the controlled-gate (c, t) grid (the Fig. 6 analogue), and IQFT fused vs
+    unfused for n = 18..33 (the Fig. 8 analogue; the largest sizes as memory allows)."""
     import torch
     torch.cuda.set_device(0)
     from paper_1601_07195_gb300 import qs
-    n = 30
+    n = args.n
+    hbm, _ = hbm_peak()
     stream = torch.cuda.Stream()
-    out = {"workload": "sweeps", "n": n, "dtype": "c128"}
+    out = {"workload": "sweeps", "n": n, "dtype": "c128", "hbm_peak_GBps": hbm}
     haar = G.gate_u1(0, G.haar_2x2(G.SplitMix64(9)))[0]["m"]
     N = float(1 << n)
+    parts = set(args.parts.split(","))
     with qs.State.create(n, qs.QS_C128, stream=stream) as st:
         st.init_basis(0)
-        for name, native in (("df", False), ("f64", True)):
+        for name, native in ((("df", False), ("f64", True)) if "gate1q" in parts else ()):
             st.set_arith(native)
-            st.apply_1q(0, haar)
+            for _ in range(3):
+                st.apply_1q(0, haar)
             per_k = []
             for k in range(n):
                 ms, _ = _timed(lambda: [st.apply_1q(k, haar) for _ in range(3)], stream, torch)
                 per_k.append(2 * N * 16 / (ms / 3 / 1e3) / 1e9)
             out[f"gate1q_GBps_by_target_{name}"] = per_k
+            out[f"gate1q_frac_{name}"] = {"min": min(per_k) / hbm, "max": max(per_k) / hbm}
         st.set_arith(False)
         grid = [[None] * n for _ in range(n)]
-        for c in range(n):
+        for c in (range(n) if "ctrl" in parts else ()):
             for t in range(n):
                 if c == t:
                     continue
                 ms, _ = _timed(lambda: st.apply_ctrl(c, t, haar), stream, torch)
                 grid[c][t] = N * 16 / (ms / 1e3) / 1e9
         flat = [v for row in grid for v in row if v is not None]
+    if flat:
         out["ctrl_GBps_grid"] = grid
         out["ctrl_GBps_summary"] = {"min": min(flat), "max": max(flat), "mean": statistics.mean(flat),
                                    "c0_mean": statistics.mean(v for v in grid[0] if v is not None),
-                                   "c_ge_10_mean": statistics.mean(v for c in range(10, n) for v in grid[c] if v is not None)}
+                                   "c_ge_10_mean": statistics.mean(v for c in range(min(10, n - 1), n)
+                                                                   for v in grid[c] if v is not None)}
     torch.cuda.empty_cache()
     iqft = []
-    for m in range(18, 31):
+    free = torch.cuda.mem_get_info()[0]
+    for m in (range(18, 34) if "iqft" in parts else ()):
+        if (16 << m) > 0.9 * free:
+            iqft.append({"n": m, "skipped": "state does not fit device memory"})
+            continue
         gates = G.inverse_circuit(G.qft_circuit(m))
         bytes_ = sum(gate_cost(g, m, 16)[0] for g in gates)
-        row = {"n": m, "gates": len(gates)}
+        row = {"n": m, "gates": len(gates), "algorithmic_GB": bytes_ / 1e9}
         with qs.State.create(m, qs.QS_C128, stream=stream) as st:
             for name, flags in (("fused", qs.PLAN_DEFAULT), ("unfused", qs.PLAN_NO_FUSION)):
                 p = st.plan(gates, flags=flags)
                 st.init_basis(1)
                 p.execute()
                 ms, _ = _timed(p.execute, stream, torch)
+                row[f"{name}_ms"] = ms
                 row[f"{name}_GBps"] = bytes_ / (ms / 1e3) / 1e9
                 row[f"{name}_passes"] = p.stats()["passes"]
                 p.close()
+        row["fused_over_unfused"] = row["unfused_ms"] / row["fused_ms"]
         iqft.append(row)
-    out["iqft_fused_vs_unfused"] = iqft
+        torch.cuda.empty_cache()
+    if iqft:
+        out["iqft_fused_vs_unfused"] = iqft
+    print(json.dumps(out), flush=True)
+
+
+def _gate_run_low6(depth, seed):
+    """`depth` gates on qubits 0..5 (two Haar single-qubit gates, then a controlled
+    Haar gate, repeating), and their product as a 64 x 64 matrix (host, FP64)."""
+    rng = G.SplitMix64(seed)
+    gates = []
+    for j in range(depth):
+        t = j % 6
+        gates.append(G.gate_cu((t + 1 + j % 5) % 6, t, G.haar_2x2(rng)) if j % 3 == 2 else G.gate_u1(t, G.haar_2x2(rng)))
+    gates = G.concat(gates)
+    U = np.eye(64, dtype=np.complex128)
+    eye2 = np.eye(2)
+    for g in gates:
+        m = g["m"]
+        Q = np.array([[m[0] + 1j * m[1], m[2] + 1j * m[3]], [m[4] + 1j * m[5], m[6] + 1j * m[7]]])
+        if int(g["kind"]) == G.G_U1:
+            op = np.eye(1)
+            for k in reversed(range(6)):
+                op = np.kron(op, Q if k == g["t"] else eye2)
+        else:
+            p0, p1 = np.eye(1), np.eye(1)
+            for k in reversed(range(6)):
+                p0 = np.kron(p0, np.diag([1.0, 0.0]) if k == g["c"] else eye2)
+                p1 = np.kron(p1, np.diag([0.0, 1.0]) if k == g["c"] else (Q if k == g["t"] else eye2))
+            op = p0 + p1
+        U = op @ U
+    return gates, U
+
+
+def run_dense(args):
+    """The dense 64 x 64 block on qubits 0..5 of an n = 30 complex64 state on the
+    tensor cores (qs_apply_dense), against the same gate runs applied by the
+    fused SIMT tile pass (one tile pass of `depth` updates), CUDA events."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1601_07195_gb300 import qs
+    n = args.n
+    N = float(1 << n)
+    hbm, hbm_src = hbm_peak()
+    stream = torch.cuda.Stream()
+    out = {"workload": "dense", "n": n, "dtype": "c64", "runs": []}
+    with qs.State.create(n, qs.QS_C64, stream=stream) as st:
+        st.init_basis(0)
+        for depth in (8, 32, 128):
+            gates, U = _gate_run_low6(depth, 40 + depth)
+            for _ in range(max(3, args.warmup)):
+                st.apply_dense(U)
+            ms = []
+            for _ in range(max(3, args.steps)):
+                m, _ = _timed(lambda: st.apply_dense(U), stream, torch)
+                ms.append(m)
+            tc_ms = statistics.median(ms)
+            p = st.plan(gates)
+            for _ in range(3):
+                p.execute()
+            sm = []
+            for _ in range(max(3, args.steps)):
+                m, _ = _timed(p.execute, stream, torch)
+                sm.append(m)
+            simt_ms = statistics.median(sm)
+            stats = p.stats()
+            p.close()
+            bytes_ = 2 * N * 8
+            flops = 6 * 2 * 128 * 128 * (N / 64)  # six bf16 piece products per 64-amplitude row
+            out["runs"].append({
+                "depth": depth, "tensor_ms": tc_ms, "simt_tile_ms": simt_ms,
+                "simt_passes": stats["passes"], "simt_device_ops": stats["device_ops"],
+                "speedup_tensor_vs_simt": simt_ms / tc_ms,
+                "roofline": {"bound": "hbm", "achieved": bytes_ / (tc_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": bytes_ / (tc_ms / 1e3) / 1e9 / hbm, "peak_source": hbm_src,
+                             "traffic": (ncu_counters("dense")["dram_bytes"] * 2.0 ** (n - 25)
+                                         if ncu_counters("dense") else None),
+                             "tensor_tflops": flops / (tc_ms / 1e3) / 1e12,
+                             "tensor_frac_of_measured_bf16": flops / (tc_ms / 1e3) / 1e12 / 1960.8}})
     print(json.dumps(out), flush=True)
 
 
@@ -819,6 +915,8 @@ def main():
         run_adjoint28(args)
     elif args.workload == "sweeps":
         run_sweeps(args)
+    elif args.workload == "dense":
+        run_dense(args)
     elif args.workload == "batch512":
         import torch
         torch.cuda.set_device(0)

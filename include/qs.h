@@ -271,6 +271,24 @@ QS_API qs_status qs_autotune(qs_state* s, const qs_gate* gates, int n_gates, con
 /* Plan, execute and destroy in one call. */
 QS_API qs_status qs_run(qs_state* s, const qs_gate* gates, int n_gates, const double* theta, int n_params);
 
+/* ---- dense block on the tensor cores (not in the paper) --------------------- */
+
+/* Apply a dense 2^q x 2^q complex matrix U (row-major, U[r][c] as the (re, im)
+ * doubles U[2 (r 2^q + c)], U[2 (r 2^q + c) + 1]) to qubits 0..q-1 of a
+ * complex64 state: every group of 2^q consecutive amplitudes x (fixed higher
+ * bits) becomes U x.  This is the product of a run of gates of Eq. 2 / Eq. 3
+ * on those qubits applied as one matrix, where Section 4.4 applies the run
+ * gate by gate inside a cached block.  It runs on the tensor cores: the block
+ * is widened to 64 x 64 (I (x) U), the state and the matrix are split into
+ * three bf16 pieces each, and six piece products accumulate in FP32 (an
+ * error of the order of complex64 rounding).  One pass reads and writes the
+ * state once.
+ *   1 <= q <= 6, n >= 6, complex64 only (QS_EDTYPE for complex128); U need
+ *   not be unitary.  The first call allocates a 96 KiB device buffer and a
+ *   pinned host buffer kept by the state.  The call synchronises the state's
+ *   stream; QS_ETIMEOUT if a bounded wait inside the kernel gave up. */
+QS_API qs_status qs_apply_dense(qs_state* s, int q, const double* U);
+
 /* ---- FP64 reductions (not in the paper) ---------------------------------- */
 
 /* *out = sum_i |alpha_i|^2 (squared 2-norm = total probability). */

@@ -205,6 +205,8 @@ qs_status qs_destroy(qs_state* s) {
     if (s->owned && s->data) cudaFree(s->data);
     if (s->d_partials) cudaFree(s->d_partials);
     if (s->h_result) cudaFreeHost(s->h_result);
+    if (s->d_dense) cudaFree(s->d_dense);
+    if (s->h_dense) cudaFreeHost(s->h_dense);
     delete s;
     return QS_OK;
 }

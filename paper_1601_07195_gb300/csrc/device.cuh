@@ -8,6 +8,9 @@
 
 #include "qs_internal.h"
 
+#define QS_PRAGMA(x) _Pragma(#x)
+#define QS_UNROLL(n) QS_PRAGMA(unroll n)
+
 namespace qs {
 
 template <class R> struct Amp;

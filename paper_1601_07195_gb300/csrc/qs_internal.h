@@ -158,6 +158,8 @@ struct qs_state {
     double* h_result;    // pinned host staging for reduction results
     size_t h_result_cap;
     bool arith_f64;      // complex128 single-gate kernels: native FP64 instead of double-float
+    void* d_dense;       // dense tensor-core block: operand image (bf16 pieces) + error flag
+    void* h_dense;       // pinned host staging of that operand image
 };
 
 namespace qs {
@@ -206,6 +208,11 @@ size_t tile_smem_bytes(qs_dtype dt, int b);
 inline size_t tile_pass_smem(qs_dtype dt, int b, int b0) {
     return tile_smem_bytes(dt, b) + 16 * prun_table_entries(b) + ((size_t)8 << (b - b0));
 }
+
+// Dense 64 x 64 block on qubits 0..5 of a complex64 state, tensor cores (dense_tc.cu).
+void dense_tc_operand(const double* U, uint16_t* out);
+size_t dense_tc_operand_bytes();
+cudaError_t launch_dense_tc(qs_state* s, const void* d_w, int* d_err, int max_ctas);
 
 // Reductions (reduce.cu).
 qs_status ensure_scratch(qs_state* s, size_t partial_doubles, size_t result_doubles);

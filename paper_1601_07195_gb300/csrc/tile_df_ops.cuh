@@ -86,6 +86,13 @@ __device__ __forceinline__ void df_tile_1q_body(float4* sm, uint32_t half, int t
 // independent pairs loaded before any is computed, per step of the fixed paths
 constexpr int kDfIlp = QS_DF_ILP;
 
+// Unroll depth of the step loops of the fixed-size paths (each step applies
+// STEP independent pairs).  Full unrolling removes the loop's integer work but
+// multiplies the code of every gate class; compile with -DQS_DF_STEP_UNROLL=n to bound it.
+#ifndef QS_DF_STEP_UNROLL
+#define QS_DF_STEP_UNROLL 2  // n = 30 step: 771 ms at 2, 773 at 1, 794 fully unrolled (instruction-cache misses)
+#endif
+
 template <int CLS, int THREADS, int B, class L = FlatLayout>
 __device__ __forceinline__ void df_tile_1q_fixed(float4* sm, int tb, const float* c) {
     constexpr int PAIRS = (1 << (B - 1)) / THREADS;
@@ -95,7 +102,7 @@ __device__ __forceinline__ void df_tile_1q_fixed(float4* sm, int tb, const float
     const uint32_t e0 = insert_zero32(threadIdx.x, tb);
     float4* s0 = sm + L::at(e0);
     float4* s1 = sm + L::at(e0 | (1u << tb));
-#pragma unroll
+QS_UNROLL(QS_DF_STEP_UNROLL)
     for (int m = 0; m < PAIRS; m += STEP) {
         uint32_t d[STEP];
         float4 a[STEP], b[STEP];
@@ -125,7 +132,7 @@ __device__ __forceinline__ void df_tile_cu_fixed(float4* sm, int cb, int tb, con
     const uint32_t e0 = insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb);
     float4* s0 = sm + L::at(e0);
     float4* s1 = sm + L::at(e0 | (1u << tb));
-#pragma unroll
+QS_UNROLL(QS_DF_STEP_UNROLL)
     for (int m = 0; m < ITEMS; m += STEP) {
         uint32_t d[STEP];
         float4 a[STEP], b[STEP];

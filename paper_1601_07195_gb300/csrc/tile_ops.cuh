@@ -70,6 +70,13 @@ __device__ __forceinline__ void tile_cu(typename Amp<R>::T* sm, uint32_t N, int 
 // independent pairs loaded before any is computed, per step of the fixed paths
 constexpr int kTileIlp = QS_TILE_ILP;
 
+// Unroll depth of the step loops of the fixed-size paths (each step applies
+// STEP independent pairs).  Full unrolling removes the loop's integer work but
+// multiplies the code of every gate class; compile with -DQS_TILE_STEP_UNROLL=n to bound it.
+#ifndef QS_TILE_STEP_UNROLL
+#define QS_TILE_STEP_UNROLL 64  // complex64 n = 30 step: 291 ms fully unrolled, 297 at 2, 302 at 1
+#endif
+
 template <class R, int CLS, int THREADS, int B, class L = FlatLayout>
 __device__ __forceinline__ void tile_1q_fixed(typename Amp<R>::T* sm, int tb, const R* m) {
     using T = typename Amp<R>::T;
@@ -79,7 +86,7 @@ __device__ __forceinline__ void tile_1q_fixed(typename Amp<R>::T* sm, int tb, co
     const uint32_t e0 = insert_zero32(threadIdx.x, tb);
     T* s0 = sm + L::at(e0);
     T* s1 = sm + L::at(e0 | (1u << tb));
-#pragma unroll
+QS_UNROLL(QS_TILE_STEP_UNROLL)
     for (int k = 0; k < PAIRS; k += STEP) {
         uint32_t d[STEP];
         T a[STEP], b[STEP];
@@ -109,7 +116,7 @@ __device__ __forceinline__ void tile_cu_fixed(typename Amp<R>::T* sm, int cb, in
     const uint32_t e0 = insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb);
     T* s0 = sm + L::at(e0);
     T* s1 = sm + L::at(e0 | (1u << tb));
-#pragma unroll
+QS_UNROLL(QS_TILE_STEP_UNROLL)
     for (int k = 0; k < ITEMS; k += STEP) {
         uint32_t d[STEP];
         T a[STEP], b[STEP];

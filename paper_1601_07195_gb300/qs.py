@@ -62,6 +62,7 @@ _SIGS = {
     "qs_apply_1q": [_vp, ctypes.c_int, _dp],
     "qs_apply_ctrl": [_vp, ctypes.c_int, ctypes.c_int, _dp],
     "qs_apply_swap": [_vp, ctypes.c_int, ctypes.c_int],
+    "qs_apply_dense": [_vp, ctypes.c_int, _dp],
     "qs_plan_create": [_vp, _vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)],
     "qs_plan_execute": [_vp],
     "qs_plan_stats": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
@@ -229,6 +230,14 @@ class State:
 
     def apply_swap(self, a, b):
         _check(load().qs_apply_swap(self._h, a, b))
+
+    def apply_dense(self, U):
+        """Dense 2^q x 2^q complex matrix on qubits 0..q-1 (complex64 states, tensor cores)."""
+        u = np.ascontiguousarray(U, dtype=np.complex128)
+        q = int(u.shape[0]).bit_length() - 1
+        if u.ndim != 2 or u.shape != (1 << q, 1 << q):
+            raise ValueError("U must be a 2^q x 2^q matrix")
+        _check(load().qs_apply_dense(self._h, q, u.view(np.float64).ctypes.data_as(_dp)))
 
     def run(self, gates, theta=None):
         g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
