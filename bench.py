@@ -120,7 +120,8 @@ NCU_COUNTERS = {
            "sha": "8ef778991bf53526", "n": 26, "dram_bytes": 1.073873e9 + 1.013033e9, "warp_inst": 2.532212736e9,
            "ms": 2.721536},
     "c64": {"kernel": "k_tile_p<float, 12>", "sources": ["tile.cu", "tile_ops.cuh"],
-            "sha": None, "n": 27, "dram_bytes": None, "warp_inst": None, "ms": None},
+            "sha": "bc1fbe4910456e8f", "n": 27, "dram_bytes": 1.074498e9 + 1.012733e9, "warp_inst": 2.035941376e9,
+            "ms": 1.8864},
     "dense": {"kernel": "k_dense6_tc", "sources": ["dense_tc.cu"],
               "sha": "3d24d6586cc3e940", "n": 25, "dram_bytes": 268.633856e6 + 206.706176e6, "warp_inst": 37385190.0,
               "ms": 0.11456},
@@ -890,10 +891,22 @@ def run_dense(args):
             simt_ms = statistics.median(sm)
             stats = p.stats()
             p.close()
+            # the same run planned with QS_PLAN_DENSE: one tensor-core pass when it is long enough
+            pd = st.plan(gates, flags=qs.PLAN_DENSE)
+            for _ in range(3):
+                pd.execute()
+            dm = []
+            for _ in range(max(3, args.steps)):
+                m, _ = _timed(pd.execute, stream, torch)
+                dm.append(m)
+            planned_ms = statistics.median(dm)
+            dense_passes = sum(1 for ps in pd.passes() if ps["kind"] == "dense")
+            pd.close()
             bytes_ = 2 * N * 8
             flops = 6 * 2 * 128 * 128 * (N / 64)  # six bf16 piece products per 64-amplitude row
             out["runs"].append({
                 "depth": depth, "tensor_ms": tc_ms, "simt_tile_ms": simt_ms,
+                "planned_dense_ms": planned_ms, "planned_dense_passes": dense_passes,
                 "simt_passes": stats["passes"], "simt_device_ops": stats["device_ops"],
                 "speedup_tensor_vs_simt": simt_ms / tc_ms,
                 "roofline": {"bound": "hbm", "achieved": bytes_ / (tc_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",

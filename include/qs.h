@@ -156,7 +156,7 @@ enum {
                                is applied as one update: per tile, a table of phase products
                                over the low and the high half of the tile bits, and two complex
                                products per amplitude whose bit j is 1. */
-    QS_PLAN_NO_PRP = 64     /* complex128 double-float plans: apply every general single-qubit
+    QS_PLAN_NO_PRP = 64,    /* complex128 double-float plans: apply every general single-qubit
                                unitary with its full complex 2x2 product.  Without it, inside a
                                tile pass, such a unitary U is applied as
                                U = K diag(1, z) [[1, t], [-t, 1]] diag(1, y)  (|t| <= 1; when
@@ -172,6 +172,13 @@ enum {
                                r, s3, is applied as the bracket (two exact sums and no product
                                per component) with q11 left out.  The scalars left out of one
                                pass multiply to at least 2^-24. */
+    QS_PLAN_DENSE = 128     /* complex64 plans (QS_EDTYPE otherwise): a run of at least 10
+                               consecutive gates whose qubits all lie in 0..5 is multiplied into
+                               one 64 x 64 matrix on the host (FP64) and applied as one pass on
+                               the tensor cores (see qs_apply_dense); the rest of the circuit is
+                               planned as usual around it.  qs_plan_pass reports such a pass with
+                               kind 2.  qs_plan_destroy returns QS_ETIMEOUT if a bounded wait
+                               inside one of these passes gave up. */
 };
 
 /* Build an execution plan for `gates` (copied in) on state s: gate classes,
@@ -229,7 +236,8 @@ QS_API qs_status qs_plan_pass_balanced(const qs_plan* p, int i, int* counts);
  * phase in between), so they skip that product.  Zero for other plans. */
 QS_API qs_status qs_plan_pass_prp(const qs_plan* p, int i, int* counts);
 
-/* Per-pass description: for pass i, its kind (0 = single gate, 1 = tile),
+/* Per-pass description: for pass i, its kind (0 = single gate, 1 = tile,
+ * 2 = dense block on qubits 0..5, see QS_PLAN_DENSE),
  * first gate and gate count in plan order, and the tile's qubit mask. */
 QS_API qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* n_gates, uint64_t* tile_mask);
 
@@ -247,7 +255,8 @@ QS_API qs_status qs_plan_set_timing(qs_plan* p, int records);
  * waits for that record's last event. */
 QS_API qs_status qs_plan_pass_times(qs_plan* p, int record, float* ms);
 
-/* Free the plan; waits for the plan's launches on the state's stream first. */
+/* Free the plan; waits for the plan's launches on the state's stream first.
+ * QS_ETIMEOUT if a bounded wait inside a dense pass gave up (QS_PLAN_DENSE). */
 QS_API qs_status qs_plan_destroy(qs_plan* p);
 
 /* ---- tile-shape tuning (the planner's fusion block size) ------------------- */
@@ -319,9 +328,10 @@ QS_API qs_status qs_expect(qs_state* s, const qs_term* terms, int n_terms, doubl
  *   dev_out:   device buffer of n + 1 doubles: out[k] = P(qubit k = 1) for
  *              k < n, out[n] = sum_i |alpha_i|^2.
  * Asynchronous on cuda_stream; read dev_out after the stream has finished.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array and every value
+ * Each call whose stream is not capturing looks up the array's device
+ * address (cudaGetSymbolAddress) with the current device; a captured call
+ * reuses the address of the last such call on the device, so make the first
+ * call on a device before any stream capture (QS_EINVAL otherwise).  All calls share the one array and every value
  * they read from it is written earlier in the same call, so nothing needs
  * clearing, but calls whose work overlaps on the GPU (other streams, other
  * threads) race on it and must be serialised by the caller. */

@@ -35,9 +35,10 @@
 //
 // Roles of the persistent CTA (one per SM: the operands take 192 KiB of
 // shared memory):
-//   warps 0-3  epilogue: tensor memory -> registers -> the state (in place)
-//   warps 4-7  producers: state rows -> registers -> bf16 pieces in shared memory
-//   warp 8     allocates tensor memory; its lane 0 issues the MMAs
+//   warps 0-3   epilogue: tensor memory -> registers -> the state (in place)
+//   warps 4-11  producers: state rows -> registers -> bf16 pieces in shared memory,
+//               the loads of the next K chunk in flight while one is split and stored
+//   warp 12     allocates tensor memory; its lane 0 issues the MMAs
 // A tile passes through two shared-memory stages (one per K chunk) and two
 // tensor-memory accumulators, so loads of the next tile, the MMAs of this one
 // and the stores of the previous one overlap.  Every wait on an mbarrier is
@@ -47,6 +48,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "device.cuh"
 
@@ -57,7 +59,11 @@ namespace {
 constexpr int kRows = 128;             // state rows per tile (the MMA's N)
 constexpr int kComps = 128;            // floats per row (64 complex amplitudes)
 constexpr int kChunkBytes = 128 * 128; // one K chunk of one operand piece: 128 rows x 128 bytes
-constexpr int kThreads = 288;          // 9 warps
+constexpr int kProducerWarps = 8;
+constexpr int kProducerThreads = 32 * kProducerWarps;
+constexpr int kUnits = kRows * 8 / kProducerThreads;  // 8-float units per producer thread per K chunk
+constexpr int kMmaWarp = 4 + kProducerWarps;
+constexpr int kThreads = 32 * (kMmaWarp + 1);      // epilogue 4 warps, producers, MMA warp
 constexpr int kSmemBytes = 12 * kChunkBytes + 1024;  // W: 3 pieces x 2 chunks; X: 2 stages x 3 pieces; alignment
 constexpr uint32_t kTmemCols = 256;    // two accumulators of 128 fp32 columns
 constexpr long long kWaitLimit = 1ll << 22;
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense6_tc(DenseArgs args) {
     }
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
-            mbar_init(&full_bar[s], 128);
+            mbar_init(&full_bar[s], kProducerThreads);
             mbar_init(&empty_bar[s], 1);
             mbar_init(&accf_bar[s], 1);
             mbar_init(&acce_bar[s], 128);
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense6_tc(DenseArgs args) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (warp == 8) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -192,49 +198,66 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense6_tc(DenseArgs args) {
     const uint32_t tmem = tmem_base;
     const unsigned long long tiles = args.tiles, rows = args.rows;
 
-    if (warp >= 4 && warp < 8) {
-        // ---- producers: 128 threads, 8 units of 8 floats each per K chunk
+    if (warp >= 4 && warp < 4 + kProducerWarps) {
+        // ---- producers: kProducerThreads threads, kUnits units of 8 floats each per K chunk.
+        // Chunk j is K chunk (j & 1) of tile blockIdx.x + (j >> 1) gridDim.x; the loads of
+        // chunk j + 1 are issued before chunk j is split and stored (two register sets).
         const int pt = tid - 128;
-        unsigned long long chunk = 0;
-        for (unsigned long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-            for (int kc = 0; kc < 2; ++kc, ++chunk) {
-                const int s = (int)(chunk & 1);
-                float4 v[16];
+        auto tile_of = [&](unsigned long long j) { return (unsigned long long)blockIdx.x + (j >> 1) * gridDim.x; };
+        auto load = [&](float4 (&v)[2 * kUnits], unsigned long long j) {
+            const unsigned long long t = tile_of(j);
+            const int kc = (int)(j & 1);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int unit = pt + 128 * j, r = unit >> 3, u = unit & 7;
-                    const unsigned long long row = t * kRows + r;
-                    if (row < rows) {
-                        const float4* src = reinterpret_cast<const float4*>(args.psi + row * kComps + kc * 64 + u * 8);
-                        v[2 * j] = src[0];
-                        v[2 * j + 1] = src[1];
-                    } else {
-                        v[2 * j] = v[2 * j + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
+            for (int q = 0; q < kUnits; ++q) {
+                const int unit = pt + kProducerThreads * q, r = unit >> 3, u = unit & 7;
+                const unsigned long long row = t * kRows + r;
+                if (row < rows) {
+                    const float4* src = reinterpret_cast<const float4*>(args.psi + row * kComps + kc * 64 + u * 8);
+                    v[2 * q] = src[0];
+                    v[2 * q + 1] = src[1];
+                } else {
+                    v[2 * q] = v[2 * q + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                if (!mbar_wait(&empty_bar[s], (uint32_t)(((chunk >> 1) & 1) ^ 1))) {
-                    atomicOr(args.err, 1);
-                    goto producers_done;
-                }
+            }
+        };
+        auto store = [&](const float4 (&v)[2 * kUnits], unsigned long long j) -> bool {
+            const int s = (int)(j & 1);
+            if (!mbar_wait(&empty_bar[s], (uint32_t)(((j >> 1) & 1) ^ 1))) return false;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int unit = pt + 128 * j, r = unit >> 3, u = unit & 7;
-                    uint4 q1, q2, q3;
-                    split3(v[2 * j].x, v[2 * j].y, q1.x, q2.x, q3.x);
-                    split3(v[2 * j].z, v[2 * j].w, q1.y, q2.y, q3.y);
-                    split3(v[2 * j + 1].x, v[2 * j + 1].y, q1.z, q2.z, q3.z);
-                    split3(v[2 * j + 1].z, v[2 * j + 1].w, q1.w, q2.w, q3.w);
-                    const uint32_t off = r * 128 + ((u ^ (r & 7)) << 4);
-                    *reinterpret_cast<uint4*>(sX + (3 * s + 0) * kChunkBytes + off) = q1;
-                    *reinterpret_cast<uint4*>(sX + (3 * s + 1) * kChunkBytes + off) = q2;
-                    *reinterpret_cast<uint4*>(sX + (3 * s + 2) * kChunkBytes + off) = q3;
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(&full_bar[s]);
+            for (int q = 0; q < kUnits; ++q) {
+                const int unit = pt + kProducerThreads * q, r = unit >> 3, u = unit & 7;
+                uint4 q1, q2, q3;
+                split3(v[2 * q].x, v[2 * q].y, q1.x, q2.x, q3.x);
+                split3(v[2 * q].z, v[2 * q].w, q1.y, q2.y, q3.y);
+                split3(v[2 * q + 1].x, v[2 * q + 1].y, q1.z, q2.z, q3.z);
+                split3(v[2 * q + 1].z, v[2 * q + 1].w, q1.w, q2.w, q3.w);
+                const uint32_t off = r * 128 + ((u ^ (r & 7)) << 4);
+                *reinterpret_cast<uint4*>(sX + (3 * s + 0) * kChunkBytes + off) = q1;
+                *reinterpret_cast<uint4*>(sX + (3 * s + 1) * kChunkBytes + off) = q2;
+                *reinterpret_cast<uint4*>(sX + (3 * s + 2) * kChunkBytes + off) = q3;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&full_bar[s]);
+            return true;
+        };
+        float4 va[2 * kUnits], vb[2 * kUnits];
+        unsigned long long j = 0;
+        if (tile_of(0) < tiles) {
+            load(va, 0);
+            for (;;) {
+                bool next = tile_of(j + 1) < tiles;
+                if (next) load(vb, j + 1);
+                if (!store(va, j)) { atomicOr(args.err, 1); break; }
+                ++j;
+                if (!next) break;
+                next = tile_of(j + 1) < tiles;
+                if (next) load(va, j + 1);
+                if (!store(vb, j)) { atomicOr(args.err, 1); break; }
+                ++j;
+                if (!next) break;
             }
         }
-    producers_done:;
-    } else if (warp == 8) {
+    } else if (warp == kMmaWarp) {
         // ---- MMA issue (one lane)
         if (lane == 0) {
             // the six piece products (W piece, X piece), smallest weights first
@@ -296,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense6_tc(DenseArgs args) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 8)
+    if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
@@ -338,16 +361,35 @@ void dense_tc_operand(const double* U, uint16_t* out) {
 
 size_t dense_tc_operand_bytes() { return (size_t)3 * 128 * 128 * 2; }
 
+// The kernel's shared-memory size, set once per device.  Plans call this when
+// they are created, so a plan captured into a CUDA graph never sets it during
+// the capture.
+cudaError_t dense_tc_prepare() {
+    static_assert(kSmemBytes <= 227 * 1024, "operands exceed shared memory");
+    static bool configured[64] = {false};
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!configured[dev]) {
+        e = cudaFuncSetAttribute(k_dense6_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    return cudaSuccess;
+}
+
 // Launch on s->stream: the operand image is at d_w (device), err a device int.
 cudaError_t launch_dense_tc(qs_state* s, const void* d_w, int* d_err, int max_ctas) {
-    static_assert(kSmemBytes <= 227 * 1024, "operands exceed shared memory");
     DenseArgs a;
     a.psi = reinterpret_cast<float*>(s->data);
     a.w = reinterpret_cast<const uint4*>(d_w);
     a.rows = 1ull << (s->n - 6);
     a.tiles = (a.rows + kRows - 1) / kRows;
     a.err = d_err;
-    cudaError_t e = cudaFuncSetAttribute(k_dense6_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = dense_tc_prepare();
     if (e != cudaSuccess) return e;
     unsigned long long grid = a.tiles;
     const unsigned long long cap = (unsigned long long)(max_ctas > 0 ? max_ctas : sm_count());

@@ -42,7 +42,8 @@ constexpr int kWindow = 512;     // gates scanned ahead when filling a pass
 constexpr int kSearchRounds = 4; // local-search rounds over the tile set of a pass
 
 struct PlanPass {
-    int kind;        // 0 = single gate, 1 = tile pass
+    int kind;        // 0 = single gate, 1 = tile pass, 2 = dense block on qubits 0..5 (tensor cores)
+    int dense = -1;  // dense pass: index of its operand image in the plan's dense buffer
     Op op;           // single gate
     TilePass tp;     // tile pass
     uint64_t mask;   // tile qubits (tile pass) or the gate's qubits
@@ -89,6 +90,10 @@ struct qs_plan {
     int records = 0;
     int next_record = 0;
     int device_ops = 0;  // gate updates the kernels apply per execution (after fusion)
+    // dense passes (QS_PLAN_DENSE): operand images, uploaded once, then an error flag
+    std::vector<uint16_t> h_dense;
+    void* d_dense = nullptr;
+    int n_dense = 0;
 };
 
 namespace qs {
@@ -535,17 +540,85 @@ size_t find_phase_run(const std::vector<Op>& ops, size_t i, const int* bit_of, q
     return best;
 }
 
+// ---- dense blocks on qubits 0..5 (QS_PLAN_DENSE, complex64) --------------------
+// A run of at least kDenseMinOps consecutive gates (circuit order) whose qubits
+// all lie in 0..5 is multiplied into one 64 x 64 matrix on the host (FP64) and
+// applied by the tensor-core block kernel (dense_tc.cu) as its own pass.  At
+// n = 30 (complex64) one such pass takes 2.6 ms, about one HBM round trip, while
+// each update of these gates costs the SIMT tile kernel about 0.25 ms inside a
+// pass it shares with other gates, so shorter runs stay in tile passes.
+constexpr int kDenseQubits = 6;
+constexpr size_t kDenseMinOps = 10;
+
+std::vector<std::pair<size_t, size_t>> dense_runs(const std::vector<Op>& ops) {
+    std::vector<std::pair<size_t, size_t>> runs;
+    size_t i = 0;
+    while (i < ops.size()) {
+        size_t j = i;
+        while (j < ops.size() && ops[j].t < kDenseQubits && ops[j].c < kDenseQubits) ++j;
+        if (j - i >= kDenseMinOps) runs.push_back({i, j});
+        i = j > i ? j : i + 1;
+    }
+    return runs;
+}
+
+// U = product of ops[a..b) (last op leftmost) on qubits 0..5, row-major (re, im):
+// every op applied to every column, as Eq. 2 / Eq. 3 apply it to a state.
+void dense_product(const std::vector<Op>& ops, size_t a, size_t b, std::vector<double>& U) {
+    const int D = 1 << kDenseQubits;
+    U.assign(2 * D * D, 0.0);
+    for (int i = 0; i < D; ++i) U[2 * (i * D + i)] = 1.0;
+    for (size_t j = a; j < b; ++j) {
+        const Op& o = ops[j];
+        for (int col = 0; col < D; ++col) {
+            double* u = &U[0];
+            auto re = [&](int r) -> double& { return u[2 * (r * D + col)]; };
+            auto im = [&](int r) -> double& { return u[2 * (r * D + col) + 1]; };
+            if (o.kind == OP_SWAP) {
+                for (int r = 0; r < D; ++r) {
+                    if (((r >> o.t) & 1) || !((r >> o.c) & 1)) continue;
+                    const int r2 = r ^ (1 << o.t) ^ (1 << o.c);
+                    std::swap(re(r), re(r2));
+                    std::swap(im(r), im(r2));
+                }
+                continue;
+            }
+            const double* m = o.m;
+            for (int r = 0; r < D; ++r) {
+                if ((r >> o.t) & 1) continue;
+                if (o.kind == OP_CU && !((r >> o.c) & 1)) continue;
+                const int r1 = r | (1 << o.t);
+                const double ar = re(r), ai = im(r), br = re(r1), bi = im(r1);
+                re(r) = m[0] * ar - m[1] * ai + m[2] * br - m[3] * bi;
+                im(r) = m[0] * ai + m[1] * ar + m[2] * bi + m[3] * br;
+                re(r1) = m[4] * ar - m[5] * ai + m[6] * br - m[7] * bi;
+                im(r1) = m[4] * ai + m[5] * ar + m[6] * bi + m[7] * br;
+            }
+        }
+    }
+}
+
 template <class OpT>
-qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse, bool upload) {
-    std::vector<PassDesc> descs;
-    if (qs_status st = plan_passes(p->s->n, ops, b, b0, fuse, 2, descs)) return st;
+qs_status build(qs_plan* p, const std::vector<Op>& all_ops, int b, int b0, bool fuse, bool upload,
+                const std::vector<std::pair<size_t, size_t>>& dense) {
     std::vector<OpT> tops;
     std::vector<TileOp<double>> t64;  // parallel records for moves-only passes of double-float plans
     const bool df = std::is_same<OpT, TileOpDF>::value;
+    // segments of ordinary passes between the dense runs
+    size_t seg0 = 0;
+    for (size_t di = 0; di <= dense.size(); ++di) {
+    const size_t seg1 = di < dense.size() ? dense[di].first : all_ops.size();
+    std::vector<Op> seg_ops;
+    if (!dense.empty()) seg_ops.assign(all_ops.begin() + seg0, all_ops.begin() + seg1);
+    const std::vector<Op>& ops = dense.empty() ? all_ops : seg_ops;
+    std::vector<PassDesc> descs;
+    if (!ops.empty())
+        if (qs_status st = plan_passes(p->s->n, ops, b, b0, fuse, 2, descs)) return st;
     for (const PassDesc& d : descs) {
         PlanPass pp{};
         pp.n_gates = (int)d.members.size();
         pp.members = d.members;
+        for (int& m : pp.members) m += (int)seg0;  // circuit positions
         pp.mask = d.mask;
         if (!d.tile) {
             pp.kind = 0;
@@ -606,6 +679,32 @@ qs_status build(qs_plan* p, const std::vector<Op>& ops, int b, int b0, bool fuse
         pp.tp.nops = (int)tops.size() - pp.tp.op0;
         p->passes.push_back(pp);
     }
+    if (di < dense.size()) {  // the dense run after this segment
+        PlanPass pp{};
+        pp.kind = 2;
+        pp.dense = p->n_dense++;
+        pp.mask = (1ull << kDenseQubits) - 1ull;
+        pp.n_gates = (int)(dense[di].second - dense[di].first);
+        for (size_t j = dense[di].first; j < dense[di].second; ++j) pp.members.push_back((int)j);
+        pp.moves_only = false;
+        std::vector<double> U;
+        dense_product(all_ops, dense[di].first, dense[di].second, U);
+        const size_t per = dense_tc_operand_bytes() / sizeof(uint16_t);
+        p->h_dense.resize(p->h_dense.size() + per);
+        dense_tc_operand(U.data(), p->h_dense.data() + p->h_dense.size() - per);
+        p->device_ops += 1;
+        p->passes.push_back(pp);
+        seg0 = dense[di].second;
+    }
+    }
+    if (upload && p->n_dense > 0) {
+        const size_t bytes = p->h_dense.size() * sizeof(uint16_t);
+        cudaError_t e = cudaMalloc(&p->d_dense, bytes + 256);
+        if (e != cudaSuccess) { cudaGetLastError(); p->d_dense = nullptr; return fail(QS_ENOMEM, "plan: dense operands"); }
+        QS_CUDA_TRY(cudaMemcpy(p->d_dense, p->h_dense.data(), bytes, cudaMemcpyHostToDevice));
+        QS_CUDA_TRY(cudaMemset((char*)p->d_dense + bytes, 0, sizeof(int)));
+        QS_CUDA_TRY(dense_tc_prepare());
+    }
     if (df) {
         // Consecutive tile passes hand the state to each other as float pairs: in
         // each run of tile passes, the first double-float pass splits the doubles
@@ -650,7 +749,12 @@ qs_status launch_all(qs_plan* p, cudaEvent_t* ev) {
         if (ev) QS_CUDA_TRY(cudaEventRecord(ev[i], p->s->stream));
         qs_status st;
         if (pp.kind == 0) st = launch_op(p->s, pp.op, f64);
-        else if (!p->h_ops_df.empty()) {  // complex128 in double-float
+        else if (pp.kind == 2) {
+            const size_t per = dense_tc_operand_bytes();
+            int* d_err = reinterpret_cast<int*>((char*)p->d_dense + per * (size_t)p->n_dense);
+            cudaError_t e = launch_dense_tc(p->s, (const char*)p->d_dense + per * (size_t)pp.dense, d_err, 0);
+            st = e == cudaSuccess ? QS_OK : cuda_fail(e, "dense block kernel launch");
+        } else if (!p->h_ops_df.empty()) {  // complex128 in double-float
             if (pp.moves_only) {
                 st = pp.tp.nops <= tile_param_ops(true)
                          ? launch_tile_pass_params(p->s, p->h_ops_f64.data(), pp.tp, true)
@@ -821,10 +925,18 @@ qs_status qs_plan_create(qs_state* s, const qs_gate* gates, int n_gates, const d
     p->flags = flags;
     const bool fuse = !(flags & QS_PLAN_NO_FUSION);
     const bool upload = !(flags & QS_PLAN_DRY_RUN);
+    std::vector<std::pair<size_t, size_t>> dense;
+    if (flags & QS_PLAN_DENSE) {
+        if (s->dt != QS_C64) {
+            delete p;
+            return fail(QS_EDTYPE, "QS_PLAN_DENSE: dense blocks are available for complex64 states only");
+        }
+        if (s->n >= kDenseQubits && fuse) dense = dense_runs(ops);
+    }
     qs_status st;
-    if (s->dt == QS_C64) st = build<TileOp<float>>(p, ops, b, b0, fuse, upload);
-    else if (flags & QS_PLAN_ARITH_F64) st = build<TileOp<double>>(p, ops, b, b0, fuse, upload);
-    else st = build<TileOpDF>(p, ops, b, b0, fuse, upload);
+    if (s->dt == QS_C64) st = build<TileOp<float>>(p, ops, b, b0, fuse, upload, dense);
+    else if (flags & QS_PLAN_ARITH_F64) st = build<TileOp<double>>(p, ops, b, b0, fuse, upload, dense);
+    else st = build<TileOpDF>(p, ops, b, b0, fuse, upload, dense);
     if (st != QS_OK) {
         qs_plan_destroy(p);
         return st;
@@ -976,12 +1088,22 @@ qs_status qs_plan_pass_times(qs_plan* p, int record, float* ms) {
 qs_status qs_plan_destroy(qs_plan* p) {
     if (!p) return QS_OK;
     if (p->s && p->s->stream && !(p->flags & QS_PLAN_DRY_RUN)) cudaStreamSynchronize(p->s->stream);
+    int timed_out = 0;
+    if (p->d_dense) {  // did a bounded wait of a dense pass give up?
+        const size_t bytes = p->h_dense.size() * sizeof(uint16_t);
+        if (cudaMemcpy(&timed_out, (char*)p->d_dense + bytes, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            timed_out = 0;
+        }
+        cudaFree(p->d_dense);
+    }
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->d_ops) cudaFree(p->d_ops);
     if (p->d_ops_f64) cudaFree(p->d_ops_f64);
     delete p;
+    if (timed_out) return fail(QS_ETIMEOUT, "dense block: a bounded wait inside the kernel gave up");
     return QS_OK;
 }
 

@@ -213,6 +213,7 @@ inline size_t tile_pass_smem(qs_dtype dt, int b, int b0) {
 void dense_tc_operand(const double* U, uint16_t* out);
 size_t dense_tc_operand_bytes();
 cudaError_t launch_dense_tc(qs_state* s, const void* d_w, int* d_err, int max_ctas);
+cudaError_t dense_tc_prepare();
 
 // Reductions (reduce.cu).
 qs_status ensure_scratch(qs_state* s, size_t partial_doubles, size_t result_doubles);

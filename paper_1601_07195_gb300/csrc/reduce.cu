@@ -388,19 +388,27 @@ static __device__ __align__(256) double g_static_partials[kStaticPartials];
 std::mutex g_static_mu;
 void* g_static_addr[64] = {nullptr};
 
-// Device address of g_static_partials for the current device, looked up once
-// per device (with that device current).  In host code the symbol is only a
-// host-side stand-in, so kernels must be given this address.
-qs_status static_scratch(double** out) {
+// Device address of g_static_partials for the current device (with that device
+// current).  In host code the symbol is only a host-side stand-in, so kernels
+// must be given this address.  It is looked up afresh on every call whose
+// stream is not capturing, so a context torn down and created again (which
+// may place the array elsewhere) never leaves a stale address in use; during
+// a capture the address from the last such call on the device is used, which
+// is why the first call on a device must come before any capture.
+qs_status static_scratch(cudaStream_t st, double** out) {
     int dev = 0;
     QS_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(QS_EINVAL, "device ordinal out of range");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    QS_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
     std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
         g_static_addr[dev] = p;
+    } else if (!g_static_addr[dev]) {
+        return fail(QS_EINVAL, "qs_marginals_noalloc: the first call on a device must not be captured");
     }
     *out = (double*)g_static_addr[dev];
     return QS_OK;
@@ -414,7 +422,7 @@ qs_status marginals_noalloc_impl(const void* psi, int n, cudaStream_t st, double
         return QS_OK;
     }
     double* scratch = nullptr;
-    if (qs_status s = static_scratch(&scratch)) return s;
+    if (qs_status s = static_scratch(st, &scratch)) return s;
     const uint64_t chunks = 1ull << (n - kChunkBits);
     uint64_t b = (uint64_t)sm_count() * 4;
     const uint64_t fit = (uint64_t)kStaticPartials / (uint64_t)(n + 1);

@@ -20,6 +20,7 @@ QS_P_Z, QS_P_ZZ, QS_P_X = range(3)
 PLAN_DEFAULT, PLAN_NO_FUSION, PLAN_GRAPH, PLAN_ARITH_F64, PLAN_DRY_RUN, PLAN_NO_MERGE = 0, 1, 2, 4, 8, 16
 PLAN_NO_PHASE_RUNS = 32
 PLAN_NO_PRP = 64
+PLAN_DENSE = 128
 
 # one tile-pass record (include/qs_records.h): double-float (complex128 plans),
 # float (complex64) and double (complex128 with PLAN_ARITH_F64) formats
@@ -304,7 +305,7 @@ class Plan:
             _check(load().qs_plan_pass(self._h, i, ctypes.byref(k), ctypes.byref(ng), ctypes.byref(mask)))
             pos = (ctypes.c_int * max(1, ng.value))()
             _check(load().qs_plan_pass_gates(self._h, i, pos))
-            out.append({"kind": "tile" if k.value == 1 else "single", "n_gates": ng.value, "mask": mask.value,
+            out.append({"kind": {0: "single", 1: "tile", 2: "dense"}[k.value], "n_gates": ng.value, "mask": mask.value,
                         "gates": list(pos[:ng.value])})
         return out
 
@@ -358,9 +359,10 @@ class Plan:
         return self.scalar_free(i)[0]
 
     def close(self):
-        if self._h is not None and self._h.value:
-            load().qs_plan_destroy(self._h)
-        self._h = None
+        """Free the plan (raises QSError(QS_ETIMEOUT) if a dense pass's bounded wait gave up)."""
+        h, self._h = self._h, None
+        if h is not None and h.value:
+            _check(load().qs_plan_destroy(h))
 
     def __del__(self):
         try:

@@ -127,3 +127,48 @@ def test_dense_block_rejections(qs):
         bad[0, 0] = np.nan
         with pytest.raises(qs.QSError):
             s.apply_dense(bad)
+
+
+def _low_run(length, seed):
+    rng = G.SplitMix64(seed)
+    out = []
+    for j in range(length):
+        t = j % 6
+        if j % 7 == 6:
+            out.append(G.gate_swap(t, (t + 2) % 6))
+        elif j % 3 == 2:
+            out.append(G.gate_cu((t + 1) % 6, t, G.haar_2x2(rng)))
+        else:
+            out.append(G.gate_u1(t, G.haar_2x2(rng)))
+    return G.concat(out)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_dense_plan_matches_oracle(qs, graph):
+    """QS_PLAN_DENSE: long runs on qubits 0..5 run as tensor-core passes between
+    ordinary tile passes; the state matches the oracle and the plan without dense
+    passes, eager and replayed as a CUDA graph (twice)."""
+    import torch
+    n = 18
+    r1, _ = G.random_circuit(n, 60, 21)
+    r2, _ = G.random_circuit(n, 60, 22)
+    gates = G.concat([r1, _low_run(40, 7), r2, _low_run(64, 8), G.gate_u1(12, G.MAT_H)])
+    psi = rand_c64_state(n, 5)
+    want = O.run(psi.astype(np.complex128), gates)
+    stream = torch.cuda.Stream()
+    with qs.State.create(n, qs.QS_C64, stream=stream) as s:
+        s.from_numpy(psi)
+        flags = qs.PLAN_DENSE | (qs.PLAN_GRAPH if graph else 0)
+        p = s.plan(gates, flags=flags)
+        kinds = [ps["kind"] for ps in p.passes()]
+        assert kinds.count("dense") == 2 and "tile" in kinds
+        p.execute()
+        stream.synchronize()
+        got = s.to_numpy()
+        assert np.max(np.abs(got - want)) < TOL
+        if graph:  # a second replay applies the circuit again
+            p.execute()
+            stream.synchronize()
+            O.run(want, gates)
+            assert np.max(np.abs(s.to_numpy() - want)) < 2 * TOL
+        p.close()

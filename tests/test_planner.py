@@ -374,3 +374,62 @@ def test_plan_arguments_on_the_host():
     assert create(h, tile_bits=15)[0] == qs.QS_EINVAL
     assert create(h, tile_bits=12 | (13 << 8))[0] == qs.QS_OK
     assert create(h, tile_bits=1)[0] == qs.QS_OK
+
+
+def _low_run(length, seed):
+    """`length` gates on qubits 0..5: Haar single-qubit gates, controlled Haar gates, swaps."""
+    rng = G.SplitMix64(seed)
+    out = []
+    for j in range(length):
+        t = j % 6
+        if j % 7 == 6:
+            out.append(G.gate_swap(t, (t + 2) % 6))
+        elif j % 3 == 2:
+            out.append(G.gate_cu((t + 1) % 6, t, G.haar_2x2(rng)))
+        else:
+            out.append(G.gate_u1(t, G.haar_2x2(rng)))
+    return G.concat(out)
+
+
+def test_dense_runs_become_dense_passes():
+    """QS_PLAN_DENSE (complex64): runs of >= 10 consecutive gates on qubits 0..5
+    become one dense pass each, in circuit order, with every other gate planned
+    around them; a 9-gate run stays in tile passes; every gate lands once."""
+    n = 14
+    r1, _ = G.random_circuit(n, 40, 3)
+    r2, _ = G.random_circuit(n, 30, 4)
+    gates = G.concat([r1, _low_run(24, 1), r2, G.gate_u1(9, G.MAT_H), _low_run(9, 2), G.gate_u1(9, G.MAT_H),
+                      _low_run(10, 5)])
+    st = fake_state(n, qs.QS_C64)
+    p = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN | qs.PLAN_DENSE)
+    passes = p.passes()
+    dense = [ps for ps in passes if ps["kind"] == "dense"]
+    low = [int(g["t"]) < 6 and int(g["c"]) < 6 for g in gates]  # maximal runs of gates on qubits 0..5
+    want, i = [], 0
+    while i < len(gates):
+        j = i
+        while j < len(gates) and low[j]:
+            j += 1
+        if j - i >= 10:
+            want.append(list(range(i, j)))
+        i = max(j, i + 1)
+    assert len(want) == 2 and want[0][0] <= 40 and want[0][-1] >= 63 and want[1][-1] == len(gates) - 1
+    assert [ps["gates"] for ps in dense] == want
+    assert all(ps["mask"] == 0x3F for ps in dense)
+    seen = sorted(j for ps in passes for j in ps["gates"])
+    assert seen == list(range(len(gates)))
+    # passes before a dense pass hold only earlier gates, passes after it only later ones
+    for i, ps in enumerate(passes):
+        if ps["kind"] != "dense":
+            continue
+        lo, hi = ps["gates"][0], ps["gates"][-1]
+        assert all(max(q["gates"]) < lo for q in passes[:i]) and all(min(q["gates"]) > hi for q in passes[i + 1:])
+    p.close()
+    # without the flag, or for complex128, no dense pass
+    p = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN)
+    assert all(ps["kind"] != "dense" for ps in p.passes())
+    p.close()
+    st128 = fake_state(n, qs.QS_C128)
+    with pytest.raises(qs.QSError) as e:
+        qs.Plan(st128, gates, flags=qs.PLAN_DRY_RUN | qs.PLAN_DENSE)
+    assert e.value.status == qs.QS_EDTYPE

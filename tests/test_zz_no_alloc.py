@@ -8,7 +8,8 @@ that pytest collects it last.  The GPU test calls the entry point through the C
 ABI twice in a row on the same state: the second call runs over whatever the
 first left in the shared array.  Both calls must agree with the allocating
 entry point qs_prob(k = -1) and qs_norm within the tolerance the reduction
-tests use (1e-12).
+tests use (1e-12), and with the CPU FP64 oracle's marginals and norm of the
+state the GPU holds (copied out), which is computed with neither kernel.
 """
 
 import ctypes
@@ -17,6 +18,7 @@ import numpy as np
 import pytest
 
 import qsgen as G
+from oracle import oracle as O
 from paper_1601_07195_gb300 import qs
 
 TOL = 1e-12
@@ -35,6 +37,8 @@ def test_noalloc_marginals_match_allocating_entry_point(dt, n):
         s.run(G.random_circuit(n, 80, 31 + n)[0])
         ref = s.marginals()
         ref_norm = s.norm()
+        held = s.to_numpy().astype(np.complex128)
+        ora, ora_norm = O.marginals(held), O.norm2(held)
         dev = ctypes.c_void_p()
         assert lib.qs_info(s.handle, ctypes.byref(dev), None, None) == qs.QS_OK
         out = torch.empty(n + 1, dtype=torch.float64, device="cuda")
@@ -48,6 +52,8 @@ def test_noalloc_marginals_match_allocating_entry_point(dt, n):
             assert np.all(np.isfinite(got))
             assert np.max(np.abs(got[:n] - ref)) < TOL
             assert abs(got[n] - ref_norm) < TOL
+            assert np.max(np.abs(got[:n] - ora)) < TOL
+            assert abs(got[n] - ora_norm) < TOL
 
 
 def test_noalloc_rejects_bad_arguments_before_any_launch():
