@@ -123,8 +123,8 @@ NCU_COUNTERS = {
             "sha": "bc1fbe4910456e8f", "n": 27, "dram_bytes": 1.074498e9 + 1.012733e9, "warp_inst": 2.035941376e9,
             "ms": 1.8864},
     "dense": {"kernel": "k_dense6_tc", "sources": ["dense_tc.cu"],
-              "sha": "3d24d6586cc3e940", "n": 25, "dram_bytes": 268.633856e6 + 206.706176e6, "warp_inst": 37385190.0,
-              "ms": 0.11456},
+              "sha": "9a74760c8df754dc", "n": 25, "dram_bytes": 268.584960e6 + 206.582528e6, "warp_inst": 37525171.0,
+              "ms": 0.091456},
 }
 
 
