@@ -117,8 +117,8 @@ HBM_FALLBACK_GBS = 6800.0  # used only when no measured copy bandwidth is availa
 CSRC = os.path.join(ROOT, "paper_1601_07195_gb300", "csrc")
 NCU_COUNTERS = {
     "df": {"kernel": "k_tile_df_p<12>", "sources": ["tile_df.cu", "tile_df_ops.cuh", "df.cuh"],
-           "sha": "8ef778991bf53526", "n": 26, "dram_bytes": 1.073873e9 + 1.013033e9, "warp_inst": 2.532212736e9,
-           "ms": 2.721536},
+           "sha": "aa7025dea6ab442a", "n": 26, "dram_bytes": 1.073920e9 + 1.012985e9, "warp_inst": 2.532212736e9,
+           "ms": 2.72144},
     "c64": {"kernel": "k_tile_p<float, 12>", "sources": ["tile.cu", "tile_ops.cuh"],
             "sha": "bc1fbe4910456e8f", "n": 27, "dram_bytes": 1.074498e9 + 1.012733e9, "warp_inst": 2.035941376e9,
             "ms": 1.8864},

@@ -68,36 +68,39 @@ __device__ __forceinline__ dfl df_dot4(dfl a, dfl b, dfl c, dfl d) {
 
 // Split of a double into hi = its leading 24 significant bits (truncated,
 // from the IEEE bit fields) and lo = the remaining 29 bits, converted to float
-// (rounded to 24 bits) and scaled by 2^(e - 1075), e the double's biased
-// exponent.  |x - (hi + lo)| < 2^-47 |x|.  Integer and FP32 instructions only,
-// branch-free, and few of them (the integer pipe bounds the single-gate
-// kernels): hi's bits are the magnitude bits shifted right by 29 (a funnel
-// shift over both words) with the exponent rebased from 1023 to 127 by one
-// subtraction, and lo's scale is hi's exponent field lowered by 52.
-// |x| < 2^-126 gives a signed zero and lo is dropped for |x| < 2^-74 (absolute
-// changes below 2^-97); |x| >= 2^128 is not handled (not reachable from a
-// normalised state).
+// (rounded to 24 bits) and scaled by the power of two 2^(e - 1075) built from
+// its exponent bits.  |x - (hi + lo)| < 2^-47 |x|.  Integer and FP32
+// instructions only, branch-free.  |x| < 2^-126 is flushed to zero and lo is
+// dropped for |x| < 2^-74 (absolute changes below 2^-97); |x| >= 2^128
+// saturates to an infinity (not reachable from a normalised state).
 __device__ __forceinline__ dfl split_double(double x) {
-    const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
     const unsigned sign = hw & 0x80000000u;
-    const unsigned habs = hw & 0x7FFFFFFFu;
-    unsigned hi = __funnelshift_r(lw, habs, 29) - (896u << 23);  // 896 << 23 wraps to 384 << 23: the same field
-    hi = habs >= (897u << 20) ? (hi | sign) : sign;
-    const int sb = (int)(hi & 0x7F800000u) - (52 << 23);
-    const float lo = __uint2float_rn(lw & 0x1FFFFFFFu) * __int_as_float(max(sb, 0));
+    const int e = (int)((hw >> 20) & 0x7FFu);
+    const int e32 = e - 1023 + 127;
+    const unsigned top23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    unsigned hi = sign | ((unsigned)e32 << 23) | top23;
+    hi = e32 <= 0 ? sign : hi;
+    hi = e32 >= 255 ? (sign | 0x7F800000u) : hi;
+    const unsigned rem = lw & 0x1FFFFFFFu;  // weight 2^(e - 1023 - 52) per unit
+    const float scale = __int_as_float((e - 1075 + 127) << 23);  // valid for 949 <= e < 1151
+    const float lo = (e >= 949 && e32 < 255) ? __uint2float_rn(rem) * scale : 0.0f;
     return {__int_as_float((int)hi), __int_as_float(__float_as_int(lo) | (int)sign)};
 }
 
-// float -> double by the bit fields (exact; no FP64 instruction), branch-free:
-// the magnitude bits shifted right by 3 with the exponent rebased from 127 to
-// 1023 by one addition form the high word, the last three significand bits the
-// low word.  Zero and subnormal floats give a signed zero; infinities and NaNs
-// are not handled (not reachable from a normalised state).
+// float -> double by the bit fields (exact; no FP64 instruction), branch-free.
+// Zero and normal floats (a subnormal maps to a signed zero: below 1.2e-38).
 __device__ __forceinline__ double float_to_double_bits(float f) {
-    const unsigned u = (unsigned)__float_as_int(f), ua = u & 0x7FFFFFFFu, s = u & 0x80000000u;
-    const bool nz = ua >= 0x00800000u;
-    const unsigned hi = ((ua >> 3) + (896u << 20)) | s;
-    return __hiloint2double((int)(nz ? hi : s), (int)(nz ? (u << 29) : 0u));
+    const unsigned u = (unsigned)__float_as_int(f);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned ef = (u >> 23) & 0xFFu;
+    const unsigned long long ed = (unsigned long long)(ef + (1023 - 127)) << 52;
+    const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+    unsigned long long r = sign | ed | m;
+    r = ef == 0u ? sign : r;
+    r = ef == 0xFFu ? (sign | 0x7FF0000000000000ull) : r;
+    return __longlong_as_double((long long)r);
 }
 
 // hi + lo rounded to the nearest double (one FP64 addition).
@@ -113,6 +116,55 @@ __device__ __forceinline__ float4 df_load(double2 a) {
 }
 __device__ __forceinline__ double2 df_store(float4 v) {
     return make_double2(join_double({v.x, v.y}), join_double({v.z, v.w}));
+}
+
+// ---- lean conversions for the single-gate kernels ------------------------------
+// The strided kernels (gates.cu) are bound by the integer pipe, so their split
+// and join use the forms below: 0.72 -> 0.93 of HBM for a single Haar gate at
+// n = 30.  The tile kernels keep the forms above, which convert once per run of
+// passes: with the lean forms compiled in, their n = 30 step took 800 instead of
+// 771 ms (the kernel's code changed shape), so they are not used there.
+
+// The split of split_double, bit for bit for every finite |x| < 2^128, in about
+// half the integer instructions: hi's bits are the magnitude bits shifted right by 29 (a funnel
+// shift over both words) with the exponent rebased from 1023 to 127 by one
+// subtraction, and lo's scale is hi's exponent field lowered by 52.
+// |x| < 2^-126 gives a signed zero and lo is dropped for |x| < 2^-74 (absolute
+// changes below 2^-97); |x| >= 2^128 is not handled (not reachable from a
+// normalised state).
+__device__ __forceinline__ dfl split_double_lean(double x) {
+    const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+    const unsigned sign = hw & 0x80000000u;
+    const unsigned habs = hw & 0x7FFFFFFFu;
+    unsigned hi = __funnelshift_r(lw, habs, 29) - (896u << 23);  // 896 << 23 wraps to 384 << 23: the same field
+    hi = habs >= (897u << 20) ? (hi | sign) : sign;
+    const int sb = (int)(hi & 0x7F800000u) - (52 << 23);
+    const float lo = __uint2float_rn(lw & 0x1FFFFFFFu) * __int_as_float(max(sb, 0));
+    return {__int_as_float((int)hi), __int_as_float(__float_as_int(lo) | (int)sign)};
+}
+
+// float_to_double_bits in fewer integer instructions, bit for bit for finite
+// floats (exact; no FP64 instruction), branch-free:
+// the magnitude bits shifted right by 3 with the exponent rebased from 127 to
+// 1023 by one addition form the high word, the last three significand bits the
+// low word.  Zero and subnormal floats give a signed zero; infinities and NaNs
+// are not handled (not reachable from a normalised state).
+__device__ __forceinline__ double float_to_double_bits_lean(float f) {
+    const unsigned u = (unsigned)__float_as_int(f), ua = u & 0x7FFFFFFFu, s = u & 0x80000000u;
+    const bool nz = ua >= 0x00800000u;
+    const unsigned hi = ((ua >> 3) + (896u << 20)) | s;
+    return __hiloint2double((int)(nz ? hi : s), (int)(nz ? (u << 29) : 0u));
+}
+
+__device__ __forceinline__ double join_double_lean(dfl v) {
+    return float_to_double_bits_lean(v.h) + float_to_double_bits_lean(v.l);
+}
+__device__ __forceinline__ float4 df_load_lean(double2 a) {
+    const dfl r = split_double_lean(a.x), i = split_double_lean(a.y);
+    return make_float4(r.h, r.l, i.h, i.l);
+}
+__device__ __forceinline__ double2 df_store_lean(float4 v) {
+    return make_double2(join_double_lean({v.x, v.y}), join_double_lean({v.z, v.w}));
 }
 
 // Gate constants: 8 doubles (q11r, q11i, q12r, q12i, q21r, q21i, q22r, q22i),

@@ -98,10 +98,10 @@ __global__ void __launch_bounds__(kThreads) k_strided_df(double2* __restrict__ p
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             if (p0 + u * stride < n_items) {
-                float4 fa = CLS != GC_DIAG1 ? df_load(a[u]) : make_float4(0, 0, 0, 0), fb = df_load(b[u]);
+                float4 fa = CLS != GC_DIAG1 ? df_load_lean(a[u]) : make_float4(0, 0, 0, 0), fb = df_load_lean(b[u]);
                 df_pair_update<CLS>(cc, fa, fb);
-                if (CLS != GC_DIAG1) psi[i0[u]] = df_store(fa);
-                psi[i1[u]] = df_store(fb);
+                if (CLS != GC_DIAG1) psi[i0[u]] = df_store_lean(fa);
+                psi[i1[u]] = df_store_lean(fb);
             }
         }
     }
