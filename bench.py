@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 comparison step")
     ap.add_argument("--parts", default="gate1q,ctrl,iqft", help="sweeps: which of gate1q, ctrl, iqft to run")
+    ap.add_argument("--no-dense", action="store_true",
+                    help="complex64: plan with QS_PLAN_NO_DENSE (no tensor-core passes for runs on qubits 0..5)")
     ap.add_argument("--workload", default="qft30", choices=["qft30", "random33", "adjoint28", "sweeps", "batch512", "dense"],
                     help="qft30: the headline n=30 step; random33: n=33 complex128 / n=34 complex64 500-gate "
                          "circuits and the n=26 error table; adjoint28: n=28 complex64 adjoint vs parameter shift; "
@@ -456,7 +458,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     state = qs.State.create(n, dtype, stream=stream)
     t0 = time.perf_counter()
-    plan = state.plan(gates)
+    plan_flags = qs.PLAN_NO_DENSE if args.no_dense else qs.PLAN_DEFAULT
+    plan = state.plan(gates, flags=plan_flags)
     plan_ms = 1e3 * (time.perf_counter() - t0)
     passes = plan.passes()
     device_ops = plan.stats()["device_ops"]
@@ -497,6 +500,7 @@ def run_ours(args):
     value, ms_per_step = job_value(total_ms, step_bytes, args.steps, world, dist if world > 1 else None)
 
     tile_idx = [i for i, p in enumerate(passes) if p["kind"] == "tile"]
+    dense_idx = [i for i, p in enumerate(passes) if p["kind"] == "dense"]
     tile_ms = times[:, tile_idx].sum(axis=1).mean() if tile_idx else 0.0
     tile_launch_ms = times[:, tile_idx].mean() if tile_idx else float("nan")
     gates_ms = times.sum(axis=1).mean()
@@ -628,6 +632,8 @@ def run_ours(args):
                        if dtype == qs.QS_C128 else "complex64 state, FP32 arithmetic, FP64 reductions"},
             "effective_over_hbm_peak": value / hbm,
             "breakdown": {"plan_ms": plan_ms, "gates_ms": gates_ms, "tile_ms": tile_ms, "passes": len(passes),
+                          "dense_passes": len(dense_idx),
+                          "dense_ms": float(times[:, dense_idx].sum(axis=1).mean()) if dense_idx else 0.0,
                           "device_ops_after_fusion": device_ops,
                           "tile_passes": len(tile_idx), "gates_in_tile_passes": kinds.get("tile", 0),
                           "gates_in_single_passes": kinds.get("single", 0), "gate_bytes": gate_bytes,
@@ -881,7 +887,7 @@ def run_dense(args):
                 m, _ = _timed(lambda: st.apply_dense(U), stream, torch)
                 ms.append(m)
             tc_ms = statistics.median(ms)
-            p = st.plan(gates)
+            p = st.plan(gates, flags=qs.PLAN_NO_DENSE)
             for _ in range(3):
                 p.execute()
             sm = []
@@ -891,8 +897,8 @@ def run_dense(args):
             simt_ms = statistics.median(sm)
             stats = p.stats()
             p.close()
-            # the same run planned with QS_PLAN_DENSE: one tensor-core pass when it is long enough
-            pd = st.plan(gates, flags=qs.PLAN_DENSE)
+            # the same run planned as usual: one tensor-core pass when it is long enough
+            pd = st.plan(gates)
             for _ in range(3):
                 pd.execute()
             dm = []

@@ -172,13 +172,14 @@ enum {
                                r, s3, is applied as the bracket (two exact sums and no product
                                per component) with q11 left out.  The scalars left out of one
                                pass multiply to at least 2^-24. */
-    QS_PLAN_DENSE = 128     /* complex64 plans (QS_EDTYPE otherwise): a run of at least 10
-                               consecutive gates whose qubits all lie in 0..5 is multiplied into
-                               one 64 x 64 matrix on the host (FP64) and applied as one pass on
-                               the tensor cores (see qs_apply_dense); the rest of the circuit is
-                               planned as usual around it.  qs_plan_pass reports such a pass with
-                               kind 2.  qs_plan_destroy returns QS_ETIMEOUT if a bounded wait
-                               inside one of these passes gave up. */
+    QS_PLAN_NO_DENSE = 128  /* complex64 plans: no dense tensor-core passes.  Without it, a run of
+                               at least 10 consecutive gates whose qubits all lie in 0..5 is
+                               multiplied into one 64 x 64 matrix on the host (FP64) and applied
+                               as one pass on the tensor cores (see qs_apply_dense); the rest of
+                               the circuit is planned as usual around it.  qs_plan_pass reports
+                               such a pass with kind 2 and qs_plan_pass_dense returns its matrix;
+                               qs_plan_destroy returns QS_ETIMEOUT if a bounded wait inside one of
+                               these passes gave up.  complex128 plans have no dense passes. */
 };
 
 /* Build an execution plan for `gates` (copied in) on state s: gate classes,
@@ -237,7 +238,7 @@ QS_API qs_status qs_plan_pass_balanced(const qs_plan* p, int i, int* counts);
 QS_API qs_status qs_plan_pass_prp(const qs_plan* p, int i, int* counts);
 
 /* Per-pass description: for pass i, its kind (0 = single gate, 1 = tile,
- * 2 = dense block on qubits 0..5, see QS_PLAN_DENSE),
+ * 2 = dense block on qubits 0..5, see QS_PLAN_NO_DENSE),
  * first gate and gate count in plan order, and the tile's qubit mask. */
 QS_API qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* n_gates, uint64_t* tile_mask);
 
@@ -245,6 +246,11 @@ QS_API qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* n_gates, 
  * qs_plan_pass).  Within and across passes the planner only moves a gate ahead
  * of gates it commutes with (disjoint qubits, or both diagonal). */
 QS_API qs_status qs_plan_pass_gates(const qs_plan* p, int i, int* positions);
+
+/* The 64 x 64 matrix of dense pass i (kind 2): row-major, (re, im) doubles,
+ * 8192 doubles into U; the ordered product of the pass's gates on qubits 0..5,
+ * formed on the host in FP64.  QS_EINVAL for other passes. */
+QS_API qs_status qs_plan_pass_dense(const qs_plan* p, int i, double* U);
 
 /* Per-pass timing with CUDA events recorded on the state's stream around
  * every pass: keep `records` sets of events, used round robin by successive
@@ -256,7 +262,7 @@ QS_API qs_status qs_plan_set_timing(qs_plan* p, int records);
 QS_API qs_status qs_plan_pass_times(qs_plan* p, int record, float* ms);
 
 /* Free the plan; waits for the plan's launches on the state's stream first.
- * QS_ETIMEOUT if a bounded wait inside a dense pass gave up (QS_PLAN_DENSE). */
+ * QS_ETIMEOUT if a bounded wait inside a dense pass gave up (QS_PLAN_NO_DENSE). */
 QS_API qs_status qs_plan_destroy(qs_plan* p);
 
 /* ---- tile-shape tuning (the planner's fusion block size) ------------------- */

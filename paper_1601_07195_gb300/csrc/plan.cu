@@ -44,6 +44,7 @@ constexpr int kSearchRounds = 4; // local-search rounds over the tile set of a p
 struct PlanPass {
     int kind;        // 0 = single gate, 1 = tile pass, 2 = dense block on qubits 0..5 (tensor cores)
     int dense = -1;  // dense pass: index of its operand image in the plan's dense buffer
+    std::vector<double> U;  // dense pass: its 64 x 64 matrix (FP64, row-major (re, im))
     Op op;           // single gate
     TilePass tp;     // tile pass
     uint64_t mask;   // tile qubits (tile pass) or the gate's qubits
@@ -90,7 +91,7 @@ struct qs_plan {
     int records = 0;
     int next_record = 0;
     int device_ops = 0;  // gate updates the kernels apply per execution (after fusion)
-    // dense passes (QS_PLAN_DENSE): operand images, uploaded once, then an error flag
+    // dense passes (complex64): operand images, uploaded once, then an error flag
     std::vector<uint16_t> h_dense;
     void* d_dense = nullptr;
     int n_dense = 0;
@@ -540,7 +541,7 @@ size_t find_phase_run(const std::vector<Op>& ops, size_t i, const int* bit_of, q
     return best;
 }
 
-// ---- dense blocks on qubits 0..5 (QS_PLAN_DENSE, complex64) --------------------
+// ---- dense blocks on qubits 0..5 (complex64 plans, unless QS_PLAN_NO_DENSE) -----
 // A run of at least kDenseMinOps consecutive gates (circuit order) whose qubits
 // all lie in 0..5 is multiplied into one 64 x 64 matrix on the host (FP64) and
 // applied by the tensor-core block kernel (dense_tc.cu) as its own pass.  At
@@ -687,11 +688,10 @@ qs_status build(qs_plan* p, const std::vector<Op>& all_ops, int b, int b0, bool 
         pp.n_gates = (int)(dense[di].second - dense[di].first);
         for (size_t j = dense[di].first; j < dense[di].second; ++j) pp.members.push_back((int)j);
         pp.moves_only = false;
-        std::vector<double> U;
-        dense_product(all_ops, dense[di].first, dense[di].second, U);
+        dense_product(all_ops, dense[di].first, dense[di].second, pp.U);
         const size_t per = dense_tc_operand_bytes() / sizeof(uint16_t);
         p->h_dense.resize(p->h_dense.size() + per);
-        dense_tc_operand(U.data(), p->h_dense.data() + p->h_dense.size() - per);
+        dense_tc_operand(pp.U.data(), p->h_dense.data() + p->h_dense.size() - per);
         p->device_ops += 1;
         p->passes.push_back(pp);
         seg0 = dense[di].second;
@@ -926,13 +926,7 @@ qs_status qs_plan_create(qs_state* s, const qs_gate* gates, int n_gates, const d
     const bool fuse = !(flags & QS_PLAN_NO_FUSION);
     const bool upload = !(flags & QS_PLAN_DRY_RUN);
     std::vector<std::pair<size_t, size_t>> dense;
-    if (flags & QS_PLAN_DENSE) {
-        if (s->dt != QS_C64) {
-            delete p;
-            return fail(QS_EDTYPE, "QS_PLAN_DENSE: dense blocks are available for complex64 states only");
-        }
-        if (s->n >= kDenseQubits && fuse) dense = dense_runs(ops);
-    }
+    if (s->dt == QS_C64 && !(flags & QS_PLAN_NO_DENSE) && s->n >= kDenseQubits && fuse) dense = dense_runs(ops);
     qs_status st;
     if (s->dt == QS_C64) st = build<TileOp<float>>(p, ops, b, b0, fuse, upload, dense);
     else if (flags & QS_PLAN_ARITH_F64) st = build<TileOp<double>>(p, ops, b, b0, fuse, upload, dense);
@@ -1018,6 +1012,14 @@ qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* n_gates, uint64_
     if (kind) *kind = pp.kind;
     if (n_gates) *n_gates = pp.n_gates;
     if (tile_mask) *tile_mask = pp.mask;
+    return QS_OK;
+}
+
+qs_status qs_plan_pass_dense(const qs_plan* p, int i, double* U) {
+    if (!p || !U) return fail(QS_EINVAL, "NULL argument");
+    if (i < 0 || i >= (int)p->passes.size()) return fail(QS_EINVAL, "pass index out of range");
+    if (p->passes[i].kind != 2) return fail(QS_EINVAL, "pass is not a dense block");
+    std::memcpy(U, p->passes[i].U.data(), p->passes[i].U.size() * sizeof(double));
     return QS_OK;
 }
 

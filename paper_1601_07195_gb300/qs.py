@@ -20,7 +20,7 @@ QS_P_Z, QS_P_ZZ, QS_P_X = range(3)
 PLAN_DEFAULT, PLAN_NO_FUSION, PLAN_GRAPH, PLAN_ARITH_F64, PLAN_DRY_RUN, PLAN_NO_MERGE = 0, 1, 2, 4, 8, 16
 PLAN_NO_PHASE_RUNS = 32
 PLAN_NO_PRP = 64
-PLAN_DENSE = 128
+PLAN_NO_DENSE = 128
 
 # one tile-pass record (include/qs_records.h): double-float (complex128 plans),
 # float (complex64) and double (complex128 with PLAN_ARITH_F64) formats
@@ -70,6 +70,7 @@ _SIGS = {
     "qs_plan_pass": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                      ctypes.POINTER(ctypes.c_uint64)],
     "qs_plan_pass_gates": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "qs_plan_pass_dense": [_vp, ctypes.c_int, _dp],
     "qs_plan_device_ops": [_vp, ctypes.POINTER(ctypes.c_int)],
     "qs_plan_pass_op_counts": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "qs_plan_pass_balanced": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
@@ -308,6 +309,12 @@ class Plan:
             out.append({"kind": {0: "single", 1: "tile", 2: "dense"}[k.value], "n_gates": ng.value, "mask": mask.value,
                         "gates": list(pos[:ng.value])})
         return out
+
+    def dense_matrix(self, i):
+        """64 x 64 complex matrix of dense pass i (kind "dense")."""
+        out = np.zeros(2 * 64 * 64, dtype=np.float64)
+        _check(load().qs_plan_pass_dense(self._h, i, out.ctypes.data_as(_dp)))
+        return out.view(np.complex128).reshape(64, 64)
 
     def set_timing(self, records):
         _check(load().qs_plan_set_timing(self._h, records))

@@ -2,7 +2,8 @@
 
 Applies the records each tile pass hands its kernel (include/qs_records.h) to
 a whole state vector in complex128 numpy arithmetic, with each record double
-taken as hi + lo.  Single-gate passes apply their gate through the oracle.
+taken as hi + lo.  Single-gate passes apply their gate through the oracle; dense passes (complex64
+plans) apply the 64 x 64 matrix the planner formed for them.
 Comparing the result with the oracle applying the circuit checks the
 planner's rewrites on the CPU: the products of adjacent gates, the phase-run
 tables, the phase-shear-phase and scalar-free forms and the scalars moved
@@ -102,6 +103,8 @@ def run_plan(plan, psi, gates, theta=None):
     for i, ps in enumerate(plan.passes()):
         if ps["kind"] == "single":
             psi = O.run(psi, gates[ps["gates"][0]:ps["gates"][0] + 1], theta)
+        elif ps["kind"] == "dense":  # the pass's 64 x 64 matrix on qubits 0..5
+            psi = (psi.reshape(-1, 64) @ plan.dense_matrix(i).T).reshape(-1)
         else:
             recs, tq, fmt = plan.records(i)
             apply_records(psi, recs, tq, fmt)

@@ -145,9 +145,9 @@ def _low_run(length, seed):
 
 @pytest.mark.parametrize("graph", [False, True])
 def test_dense_plan_matches_oracle(qs, graph):
-    """QS_PLAN_DENSE: long runs on qubits 0..5 run as tensor-core passes between
-    ordinary tile passes; the state matches the oracle and the plan without dense
-    passes, eager and replayed as a CUDA graph (twice)."""
+    """complex64 plans: long runs on qubits 0..5 run as tensor-core passes between
+    ordinary tile passes; the state matches the oracle, eager and replayed as a
+    CUDA graph (twice)."""
     import torch
     n = 18
     r1, _ = G.random_circuit(n, 60, 21)
@@ -158,7 +158,7 @@ def test_dense_plan_matches_oracle(qs, graph):
     stream = torch.cuda.Stream()
     with qs.State.create(n, qs.QS_C64, stream=stream) as s:
         s.from_numpy(psi)
-        flags = qs.PLAN_DENSE | (qs.PLAN_GRAPH if graph else 0)
+        flags = qs.PLAN_GRAPH if graph else qs.PLAN_DEFAULT
         p = s.plan(gates, flags=flags)
         kinds = [ps["kind"] for ps in p.passes()]
         assert kinds.count("dense") == 2 and "tile" in kinds

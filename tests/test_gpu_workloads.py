@@ -61,15 +61,18 @@ def n30_reference():
     return n, x, G.concat([G.qft_circuit(n), r]), psi
 
 
-@pytest.mark.parametrize("dt", [1, 0])
-def test_benchmark_step_n30_every_amplitude(qs, n30_reference, dt):
+@pytest.mark.parametrize("dt,dense", [(1, False), (0, True), (0, False)])
+def test_benchmark_step_n30_every_amplitude(qs, n30_reference, dt, dense):
+    """complex64 plans run the QFT's last 21 gates (all on qubits 0..5) as one
+    tensor-core pass unless planned with QS_PLAN_NO_DENSE (dense = False)."""
     n, x, gates, want = n30_reference
     chunk = 1 << 24
     err = 0.0
     with qs.State.create(n, dt) as s:
         s.init_basis(x)
-        p = s.plan(gates)
-        assert p.stats()["tile_passes"] == p.stats()["passes"]
+        p = s.plan(gates, flags=qs.PLAN_DEFAULT if dense else qs.PLAN_NO_DENSE)
+        kinds = [ps["kind"] for ps in p.passes()]
+        assert kinds.count("dense") == (1 if dense else 0) and "single" not in kinds
         p.execute()
         for off in range(0, 1 << n, chunk):
             got = s.to_numpy(off, chunk)

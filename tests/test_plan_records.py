@@ -206,3 +206,20 @@ def test_random_plans_records_reproduce_oracle():
         check(n, gates, np.array([0.7, -1.3]), flags | arith, b | (min(b0, b) << 8), seed % 997, dt=dt, tol=tol)
 
     prop()
+
+
+def test_dense_passes_reproduce_oracle():
+    """complex64 plans with runs of >= 10 gates on qubits 0..5: the dense passes'
+    64 x 64 matrices (formed by the planner in FP64) together with the other
+    passes' records reproduce the oracle (dense products checked to rounding of
+    the float records around them)."""
+    from tests.test_planner import _low_run
+    for n, seed in ((8, 1), (11, 2), (14, 3)):
+        r1, _ = G.random_circuit(n, 40, seed)
+        r2, _ = G.random_circuit(n, 40, seed + 10)
+        gates = G.concat([_low_run(12, seed), r1, _low_run(30, seed + 1), r2, _low_run(10, seed + 2)])
+        st = fake_state(n, qs.QS_C64)
+        p = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN)
+        assert sum(ps["kind"] == "dense" for ps in p.passes()) >= 3
+        p.close()
+        check(n, gates, None, qs.PLAN_DEFAULT, 0, seed, dt=qs.QS_C64, tol=1e-5)

@@ -79,6 +79,10 @@ def test_plan_is_a_valid_reordering(case, dt, tile_bits):
             assert bin(ps["mask"]).count("1") == b
             for j in ps["gates"]:
                 assert all((ps["mask"] >> q) & 1 for q in mixing(gates[j]))
+        elif ps["kind"] == "dense":  # complex64: a run of consecutive gates on qubits 0..5
+            assert dt == qs.QS_C64 and ps["mask"] == 0x3F and ps["n_gates"] >= 10
+            assert ps["gates"] == list(range(ps["gates"][0], ps["gates"][0] + ps["n_gates"]))
+            assert all(int(gates[j]["t"]) < 6 and int(gates[j]["c"]) < 6 for j in ps["gates"])
         else:
             assert ps["n_gates"] == 1
     pos = {g: i for i, g in enumerate(order)}
@@ -392,16 +396,17 @@ def _low_run(length, seed):
 
 
 def test_dense_runs_become_dense_passes():
-    """QS_PLAN_DENSE (complex64): runs of >= 10 consecutive gates on qubits 0..5
-    become one dense pass each, in circuit order, with every other gate planned
-    around them; a 9-gate run stays in tile passes; every gate lands once."""
+    """complex64 plans: runs of >= 10 consecutive gates on qubits 0..5 become one
+    dense pass each, in circuit order, with every other gate planned around
+    them; a 9-gate run stays in tile passes; every gate lands once.  The pass's
+    matrix is the ordered product of its gates (numpy.kron operators)."""
     n = 14
     r1, _ = G.random_circuit(n, 40, 3)
     r2, _ = G.random_circuit(n, 30, 4)
     gates = G.concat([r1, _low_run(24, 1), r2, G.gate_u1(9, G.MAT_H), _low_run(9, 2), G.gate_u1(9, G.MAT_H),
                       _low_run(10, 5)])
     st = fake_state(n, qs.QS_C64)
-    p = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN | qs.PLAN_DENSE)
+    p = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN)
     passes = p.passes()
     dense = [ps for ps in passes if ps["kind"] == "dense"]
     low = [int(g["t"]) < 6 and int(g["c"]) < 6 for g in gates]  # maximal runs of gates on qubits 0..5
@@ -424,12 +429,44 @@ def test_dense_runs_become_dense_passes():
             continue
         lo, hi = ps["gates"][0], ps["gates"][-1]
         assert all(max(q["gates"]) < lo for q in passes[:i]) and all(min(q["gates"]) > hi for q in passes[i + 1:])
+    for i, ps in enumerate(passes):
+        if ps["kind"] == "dense":
+            U = np.eye(64, dtype=np.complex128)
+            for j in ps["gates"]:
+                U = _low_operator(gates[j]) @ U
+            assert np.max(np.abs(p.dense_matrix(i) - U)) < 1e-13
+        else:
+            with pytest.raises(qs.QSError):
+                p.dense_matrix(i)
     p.close()
-    # without the flag, or for complex128, no dense pass
-    p = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN)
+    # with QS_PLAN_NO_DENSE, or for complex128, no dense pass
+    p = qs.Plan(st, gates, flags=qs.PLAN_DRY_RUN | qs.PLAN_NO_DENSE)
     assert all(ps["kind"] != "dense" for ps in p.passes())
     p.close()
-    st128 = fake_state(n, qs.QS_C128)
-    with pytest.raises(qs.QSError) as e:
-        qs.Plan(st128, gates, flags=qs.PLAN_DRY_RUN | qs.PLAN_DENSE)
-    assert e.value.status == qs.QS_EDTYPE
+    p = qs.Plan(fake_state(n, qs.QS_C128), gates, flags=qs.PLAN_DRY_RUN)
+    assert all(ps["kind"] != "dense" for ps in p.passes())
+    p.close()
+
+
+def _low_operator(g):
+    """The 64 x 64 operator of one gate record on qubits 0..5 (qubit 5 leftmost)."""
+    m = g["m"]
+    Q = np.array([[m[0] + 1j * m[1], m[2] + 1j * m[3]], [m[4] + 1j * m[5], m[6] + 1j * m[7]]])
+    kind, t, c = int(g["kind"]), int(g["t"]), int(g["c"])
+    def kron(fs):
+        out = np.eye(1)
+        for f in fs:
+            out = np.kron(out, f)
+        return out
+    if kind == G.G_SWAP:
+        P = np.zeros((64, 64))
+        for i in range(64):
+            j = i
+            if ((i >> t) & 1) != ((i >> c) & 1):
+                j = i ^ (1 << t) ^ (1 << c)
+            P[j, i] = 1.0
+        return P
+    if kind == G.G_U1:
+        return kron([Q if k == t else np.eye(2) for k in reversed(range(6))])
+    return (kron([np.diag([1.0, 0.0]) if k == c else np.eye(2) for k in reversed(range(6))])
+            + kron([np.diag([0.0, 1.0]) if k == c else (Q if k == t else np.eye(2)) for k in reversed(range(6))]))
