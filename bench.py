@@ -543,33 +543,10 @@ def run_ours(args):
     }
     launches_per_step = 1 + len(passes) + 2 + 2  # init, passes, norm (2 kernels), marginals (2 kernels)
 
-    native = None
-    if dtype == qs.QS_C128 and not args.no_native:
-        # the same step with native FP64 instructions for the gate arithmetic (the paper's
-        # precision), under the same protocol; fewer steps, each takes about 4 s
-        pn = state.plan(gates, flags=qs.PLAN_ARITH_F64)
-        k_native, w_native = min(args.steps, 5), max(3, min(args.warmup, 3))
-        n_ms, n_times, n_clocks = timed_steps(pn, k_native, w_native)
-        n_value, n_ms_step = job_value(n_ms, step_bytes, k_native, world, dist if world > 1 else None)
-        n_tile = n_times[:, tile_idx].mean() if tile_idx else float("nan")
-        n_tile_ms = n_times[:, tile_idx].sum(axis=1).mean() if tile_idx else 0.0
-        f64_flops = sum(kernel_flops(pn.op_counts(i), n, _FLOPS) for i in tile_idx)
-        f64_tf = f64_flops / (n_tile_ms / 1e3) / 1e12 if n_tile_ms else 0.0
-        native = {"value": n_value, "unit": "GB/s", "ms_per_step": n_ms_step, "steps": k_native,
-                  "warmup": w_native, "dtype": "f64", "clocks": n_clocks,
-                  "note": "same step, plan flag QS_PLAN_ARITH_F64 (IEEE double arithmetic on the FP64 pipe)",
-                  "roofline": {"bound": "alu", "kernel": "k_tile_p<double, 12> (fused tile pass, FP64)",
-                               "achieved": f64_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                               "frac": f64_tf / FP64_PEAK_TFLOPS,
-                               "peak_source": "derived: 152 SMs x 2 DFMA (4 flop) per clock x 2.07 GHz",
-                               "what": "FP64 flops of the updates the kernel applies after fusion: 14 per "
-                                       "amplitude of a general update, 6 of a real / diagonal / anti-diagonal "
-                                       "one, 0 of a permutation",
-                               "avg_launch_ms": n_tile,
-                               "hbm_frac": pass_bytes / (n_tile / 1e3) / 1e9 / hbm if tile_idx else None}}
-        pn.close()
-
     e2e = None
+    # e2e runs before the native-FP64 arm: on the GB300 machines measured, host-to-device
+    # copies in a process that had run native-FP64 plans took 3-4x longer (270-370 ms
+    # instead of 82-91 ms for 17.2 GB), and stayed slow after those plans were freed
     if not args.no_e2e:
         # public API with host buffers: pinned host state -> device, qs_run (plans inside), marginals -> host
         host = torch.zeros(1 << n, dtype=torch.complex128 if dtype == qs.QS_C128 else torch.complex64,
@@ -603,6 +580,32 @@ def run_ours(args):
                                 "marginals_to_host": 1e3 * statistics.mean(parts[2])},
                "h2d_GBps": N * s_bytes / statistics.mean(parts[0]) / 1e9}
         del host
+
+    native = None
+    if dtype == qs.QS_C128 and not args.no_native:
+        # the same step with native FP64 instructions for the gate arithmetic (the paper's
+        # precision), under the same protocol; fewer steps, each takes about 4 s
+        pn = state.plan(gates, flags=qs.PLAN_ARITH_F64)
+        k_native, w_native = min(args.steps, 5), max(3, min(args.warmup, 3))
+        n_ms, n_times, n_clocks = timed_steps(pn, k_native, w_native)
+        n_value, n_ms_step = job_value(n_ms, step_bytes, k_native, world, dist if world > 1 else None)
+        n_tile = n_times[:, tile_idx].mean() if tile_idx else float("nan")
+        n_tile_ms = n_times[:, tile_idx].sum(axis=1).mean() if tile_idx else 0.0
+        f64_flops = sum(kernel_flops(pn.op_counts(i), n, _FLOPS) for i in tile_idx)
+        f64_tf = f64_flops / (n_tile_ms / 1e3) / 1e12 if n_tile_ms else 0.0
+        native = {"value": n_value, "unit": "GB/s", "ms_per_step": n_ms_step, "steps": k_native,
+                  "warmup": w_native, "dtype": "f64", "clocks": n_clocks,
+                  "note": "same step, plan flag QS_PLAN_ARITH_F64 (IEEE double arithmetic on the FP64 pipe)",
+                  "roofline": {"bound": "alu", "kernel": "k_tile_p<double, 12> (fused tile pass, FP64)",
+                               "achieved": f64_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": f64_tf / FP64_PEAK_TFLOPS,
+                               "peak_source": "derived: 152 SMs x 2 DFMA (4 flop) per clock x 2.07 GHz",
+                               "what": "FP64 flops of the updates the kernel applies after fusion: 14 per "
+                                       "amplitude of a general update, 6 of a real / diagonal / anti-diagonal "
+                                       "one, 0 of a permutation",
+                               "avg_launch_ms": n_tile,
+                               "hbm_frac": pass_bytes / (n_tile / 1e3) / 1e9 / hbm if tile_idx else None}}
+        pn.close()
 
     secondary = None
     if not args.no_secondary and rank == 0:
