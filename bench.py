@@ -544,22 +544,19 @@ def run_ours(args):
     launches_per_step = 1 + len(passes) + 2 + 2  # init, passes, norm (2 kernels), marginals (2 kernels)
 
     e2e = None
-    # e2e runs before the native-FP64 arm: on the GB300 machines measured, host-to-device
-    # copies in a process that had run native-FP64 plans took 3-4x longer (270-370 ms
-    # instead of 82-91 ms for 17.2 GB), and stayed slow after those plans were freed
     if not args.no_e2e:
-        # public API with host buffers: pinned host state -> device, qs_run (plans inside), marginals -> host
-        host = torch.zeros(1 << n, dtype=torch.complex128 if dtype == qs.QS_C128 else torch.complex64,
-                           pin_memory=True)
-        host[x] = 1.0
+        # public API with host buffers: the host state (qs_host_alloc: huge pages, page-locked)
+        # -> device, qs_run (plans inside), marginals -> host
+        hostbuf = qs.HostBuffer(1 << n, np.complex128 if dtype == qs.QS_C128 else np.complex64)
+        hostbuf.array[x] = 1.0
         e2e_steps = 5
-        state.copy_in_ptr(host.data_ptr(), 1 << n)
+        state.copy_in_ptr(hostbuf.ptr, 1 << n)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         parts = [[], [], []]  # each call below returns after its work is done
         for _ in range(e2e_steps):
             ta = time.perf_counter()
-            state.copy_in_ptr(host.data_ptr(), 1 << n)
+            state.copy_in_ptr(hostbuf.ptr, 1 << n)
             tb = time.perf_counter()
             state.run(gates)
             tc = time.perf_counter()
@@ -578,8 +575,9 @@ def run_ours(args):
                                 "h2d_state_each": [round(1e3 * v, 1) for v in parts[0]],
                                 "qs_run": 1e3 * statistics.mean(parts[1]),
                                 "marginals_to_host": 1e3 * statistics.mean(parts[2])},
-               "h2d_GBps": N * s_bytes / statistics.mean(parts[0]) / 1e9}
-        del host
+               "h2d_GBps": N * s_bytes / statistics.mean(parts[0]) / 1e9,
+               "host_buffer": "qs_host_alloc (transparent huge pages, page-locked)"}
+        hostbuf.close()
 
     native = None
     if dtype == qs.QS_C128 and not args.no_native:

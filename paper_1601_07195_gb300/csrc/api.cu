@@ -1,7 +1,10 @@
 // api.cu -- state lifetime, copies, single-gate entry points, error reporting,
 // and the host-side lowering of gate records (classification by gate class).
+#include <sys/mman.h>
+
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 
 #include "device.cuh"
@@ -261,6 +264,60 @@ qs_status qs_copy_in(qs_state* s, uint64_t off, uint64_t cnt, const void* host) 
     const size_t ab = amp_bytes(s->dt);
     QS_CUDA_TRY(cudaMemcpyAsync((char*)s->data + off * ab, host, cnt * ab, cudaMemcpyHostToDevice, s->stream));
     QS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    return QS_OK;
+}
+
+// ---- host buffers for transfers -------------------------------------------------
+// Page-locked host memory of base-size pages (what cudaHostAlloc returns) lost up
+// to 4x of its host-to-device rate on the GB300 nodes measured, for the first copy
+// after the GPU had been busy or idle for a few seconds, while an anonymous mapping
+// backed by transparent huge pages and then registered kept the full rate on every
+// copy.  The mapping's size is kept here so that qs_host_free needs only the pointer.
+namespace {
+std::mutex g_host_mu;
+std::map<void*, size_t> g_host_maps;
+}  // namespace
+
+qs_status qs_host_alloc(size_t bytes, void** out) {
+    if (!out) return fail(QS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (bytes == 0) return fail(QS_EINVAL, "size is zero");
+    const size_t align = (size_t)2 << 20;
+    const size_t len = (bytes + align - 1) / align * align;
+    void* p = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    if (p == MAP_FAILED) return fail(QS_ENOMEM, "mmap of the host buffer failed");
+#ifdef MADV_HUGEPAGE
+    madvise(p, len, MADV_HUGEPAGE);  // best effort: the buffer works with base pages too
+#endif
+    std::memset(p, 0, len);  // populate the pages (as huge pages where the kernel allows)
+    cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        munmap(p, len);
+        return fail(e == cudaErrorMemoryAllocation ? QS_ENOMEM : QS_ECUDA,
+                    std::string("cudaHostRegister of the host buffer failed: ") + cudaGetErrorString(e));
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_host_mu);
+        g_host_maps[p] = len;
+    }
+    *out = p;
+    return QS_OK;
+}
+
+qs_status qs_host_free(void* p) {
+    if (!p) return QS_OK;
+    size_t len = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_host_mu);
+        auto it = g_host_maps.find(p);
+        if (it == g_host_maps.end()) return fail(QS_EINVAL, "pointer was not returned by qs_host_alloc");
+        len = it->second;
+        g_host_maps.erase(it);
+    }
+    cudaError_t e = cudaHostUnregister(p);
+    munmap(p, len);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaHostUnregister");
     return QS_OK;
 }
 

@@ -60,6 +60,8 @@ _SIGS = {
     "qs_init_basis": [_vp, ctypes.c_uint64],
     "qs_copy_out": [_vp, ctypes.c_uint64, ctypes.c_uint64, _vp],
     "qs_copy_in": [_vp, ctypes.c_uint64, ctypes.c_uint64, _vp],
+    "qs_host_alloc": [ctypes.c_size_t, ctypes.POINTER(_vp)],
+    "qs_host_free": [_vp],
     "qs_apply_1q": [_vp, ctypes.c_int, _dp],
     "qs_apply_ctrl": [_vp, ctypes.c_int, ctypes.c_int, _dp],
     "qs_apply_swap": [_vp, ctypes.c_int, ctypes.c_int],
@@ -137,6 +139,35 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return int(getattr(stream, "cuda_stream", stream))
+
+
+class HostBuffer:
+    """Page-locked host memory from qs_host_alloc (huge pages, registered):
+    ``array`` is a numpy view of ``count`` elements of ``dtype``."""
+
+    def __init__(self, count, dtype=np.complex128):
+        dtype = np.dtype(dtype)
+        p = _vp()
+        _check(load().qs_host_alloc(count * dtype.itemsize, ctypes.byref(p)))
+        self._p = p
+        self.array = np.ctypeslib.as_array((ctypes.c_char * (count * dtype.itemsize)).from_address(p.value)
+                                           ).view(dtype)
+
+    @property
+    def ptr(self):
+        return self._p.value
+
+    def close(self):
+        if self._p is not None and self._p.value:
+            self.array = None
+            _check(load().qs_host_free(self._p))
+        self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class State:

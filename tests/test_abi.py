@@ -66,3 +66,12 @@ def test_wrapped_handle_validates_qubits_before_launch():
     bad = (ctypes.c_double * 8)(float("nan"), 0, 0, 0, 0, 0, 1, 0)
     assert lib.qs_apply_1q(h, 0, bad) == qs.QS_EINVAL
     assert lib.qs_destroy(h) == qs.QS_OK
+
+
+def test_host_buffer_arguments_without_gpu():
+    lib = qs.load()
+    p = ctypes.c_void_p()
+    assert lib.qs_host_alloc(0, ctypes.byref(p)) == qs.QS_EINVAL
+    assert lib.qs_host_alloc(64, None) == qs.QS_EINVAL
+    assert lib.qs_host_free(None) == qs.QS_OK
+    assert lib.qs_host_free(ctypes.c_void_p(1 << 20)) == qs.QS_EINVAL  # not from qs_host_alloc
