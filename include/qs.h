@@ -323,7 +323,9 @@ QS_API qs_status qs_apply_dense(qs_state* s, int q, const double* U);
 QS_API qs_status qs_norm(qs_state* s, double* out);
 
 /* Marginal P(qubit k = 1) = sum over i with bit k set of |alpha_i|^2.
- * k >= 0: one value into p1[0]; k = -1: all n marginals into p1[0..n-1]. */
+ * k >= 0: one value into p1[0]; k = -1: all n marginals into p1[0..n-1];
+ * k = -2: the n marginals and then the total sum_i |alpha_i|^2 (the squared
+ * norm) into p1[0..n], all from the same single read of the state. */
 QS_API qs_status qs_prob(qs_state* s, int k, double* p1);
 
 /* host_out[i] = |alpha_i|^2 for all 2^n amplitudes (host buffer of 2^n doubles). */

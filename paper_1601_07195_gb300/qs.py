@@ -296,6 +296,12 @@ class State:
         _check(load().qs_prob(self._h, -1, out.ctypes.data_as(_dp)))
         return out
 
+    def marginals_and_norm(self):
+        """(the n marginals, sum_i |alpha_i|^2) from one read of the state."""
+        out = np.zeros(self.n + 1, dtype=np.float64)
+        _check(load().qs_prob(self._h, -2, out.ctypes.data_as(_dp)))
+        return out[:self.n], float(out[self.n])
+
     def probs(self):
         out = np.empty(1 << self.n, dtype=np.float64)
         _check(load().qs_probs(self._h, out.ctypes.data_as(_dp)))

@@ -271,6 +271,8 @@ def test_reductions(qs, dt, n):
         for k in range(n):
             assert abs(s.prob(k) - O.marginals(ref)[k]) < 1e-13
         assert maxerr(s.expect(terms), O.expect(ref, terms)) < 1e-12
+        marg, total = s.marginals_and_norm()
+        assert maxerr(marg, O.marginals(ref)) < 1e-13 and maxerr(total, O.norm2(ref)) < 1e-13
         assert maxerr(s.probs(), O.probs(ref)) < 1e-15
 
 
