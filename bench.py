@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 comparison step")
+    ap.add_argument("--no-dense-leg", action="store_true", help="skip the tensor-core dense-block measurement")
     ap.add_argument("--parts", default="gate1q,ctrl,iqft", help="sweeps: which of gate1q, ctrl, iqft to run")
     ap.add_argument("--no-dense", action="store_true",
                     help="complex64: plan with QS_PLAN_NO_DENSE (no tensor-core passes for runs on qubits 0..5)")
@@ -146,6 +147,16 @@ def ncu_counters(kind):
     if not c or c["sha"] is None or c["sha"] != sources_sha(c["sources"]):
         return None
     return c
+
+
+def bf16_peak():
+    """(TFLOP/s, source) of the dense bf16 tensor peak: the measured cuBLAS burst, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
 
 
 def hbm_peak():
@@ -419,6 +430,40 @@ def secondary_gradients(qs, dtype, torch):
                                  "(lower bound on the arithmetic), per second of execution"}}
 
 
+def dense_leg(qs, torch, n, reps):
+    """The tensor-core dense block (k_dense6_tc) on an n-qubit complex64 state: a
+    complex64 plan of a 32-gate run on qubits 0..5 is one dense pass; CUDA events
+    around each execution on the state's stream, after 3 warm-up executions."""
+    hbm, hbm_src = hbm_peak()
+    gates, _ = _gate_run_low6(32, 72)
+    stream = torch.cuda.Stream()
+    with qs.State.create(n, qs.QS_C64, stream=stream) as st:
+        st.init_basis(0)
+        p = st.plan(gates)
+        kinds = [ps["kind"] for ps in p.passes()]
+        for _ in range(3):
+            p.execute()
+        ms = []
+        for _ in range(reps):
+            m, _ = _timed(p.execute, stream, torch)
+            ms.append(m)
+        p.close()
+    t = statistics.median(ms)
+    N = float(1 << n)
+    bytes_ = 2 * N * 8
+    flops = 6 * 2 * 128 * 128 * (N / 64)
+    cnt = ncu_counters("dense")
+    return {"kernel": "k_dense6_tc (tcgen05.mma kind::f16, TMEM accumulators)", "workload":
+            f"32-gate run on qubits 0..5 of an n={n} complex64 state, planned as {kinds.count('dense')} dense pass",
+            "ms": t, "reps": reps,
+            "roofline": {"bound": "hbm", "achieved": bytes_ / (t / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": bytes_ / (t / 1e3) / 1e9 / hbm, "peak_source": hbm_src,
+                         "traffic": cnt["dram_bytes"] * 2.0 ** (n - cnt["n"]) if cnt else None},
+            "tensor_tflops": flops / (t / 1e3) / 1e12,
+            "tensor_frac_of_bf16_peak": flops / (t / 1e3) / 1e12 / bf16_peak()[0],
+            "bf16_peak_source": bf16_peak()[1] + " bf16 GEMM burst (MEASURED_PEAKS.json bf16_tflops)"}
+
+
 def job_value(local_ms, step_bytes, steps, world, dist=None):
     """Whole-job throughput of `world` independent replicas (no collective on the
     data path): each rank did `steps` steps of `step_bytes`; the job took the
@@ -606,6 +651,10 @@ def run_ours(args):
                                "hbm_frac": pass_bytes / (n_tile / 1e3) / 1e9 / hbm if tile_idx else None}}
         pn.close()
 
+    dense_tc = None
+    if not args.no_dense_leg and rank == 0:
+        dense_tc = dense_leg(qs, torch, n, max(3, min(args.steps, 10)))
+
     secondary = None
     if not args.no_secondary and rank == 0:
         secondary = secondary_gradients(qs, dtype, torch)
@@ -647,6 +696,7 @@ def run_ours(args):
             "clocks": clocks,
             "secondary": secondary,
             "native_f64": native,
+            "dense_tc": dense_tc,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -922,7 +972,7 @@ def run_dense(args):
                              "traffic": (ncu_counters("dense")["dram_bytes"] * 2.0 ** (n - 25)
                                          if ncu_counters("dense") else None),
                              "tensor_tflops": flops / (tc_ms / 1e3) / 1e12,
-                             "tensor_frac_of_measured_bf16": flops / (tc_ms / 1e3) / 1e12 / 1960.8}})
+                             "tensor_frac_of_bf16_peak": flops / (tc_ms / 1e3) / 1e12 / bf16_peak()[0]}})
     print(json.dumps(out), flush=True)
 
 
