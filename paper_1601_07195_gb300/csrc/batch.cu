@@ -554,14 +554,31 @@ void dagger(const double m[8], double d[8]) {
 }
 
 // Lower an instance's gates; rotation classes are fixed by kind so that every
-// angle gives the same plan (RX general, RY real, RZ diagonal).
+// angle gives the same plan (RX general, RY real, RZ a phase gate).
+//
+// RZ(theta) = e^{-i theta/2} diag(1, e^{i theta}) is applied as diag(1, e^{i theta}),
+// which changes only the |1> amplitudes (half the arithmetic of a diagonal gate).
+// The dropped factor is a global phase: every forward state, and in the reverse
+// sweep phi and lambda alike, carries the same phase e^{i A} (A = half the sum of
+// the RZ angles applied so far), so E = <psi|H|psi> and the gradient terms
+// Im <lambda|Z|phi> are unchanged.  (With diag(1, e^{i theta}) as the gate, its
+// derivative is i diag(0, 1) U = (i/2)(I - Z) U, which adds -Im <lambda|phi> to
+// the term; <lambda|phi> = <H psi|psi> = E is real, so that addition is zero.)
+// Batches return energies and gradients only, never the state, so the phase
+// is unobservable; plans (qs_run) keep the exact RZ matrix.
 qs_status lower_instance(const qs_instance& in, std::vector<Op>& ops) {
     if (qs_status st = lower_gates(in.gates, in.n_gates, in.theta, in.n_params, in.n, ops)) return st;
     for (int j = 0; j < in.n_gates; ++j) {
         const int k = in.gates[j].kind;
         if (k == QS_G_RX) ops[j].cls = GC_GENERAL;
         else if (k == QS_G_RY) ops[j].cls = GC_REAL;
-        else if (k == QS_G_RZ) ops[j].cls = GC_DIAG;
+        else if (k == QS_G_RZ) {
+            const double th = in.theta[in.gates[j].param];
+            double* m = ops[j].m;
+            m[0] = 1.0; m[1] = 0.0; m[2] = m[3] = m[4] = m[5] = 0.0;
+            m[6] = std::cos(th); m[7] = std::sin(th);
+            ops[j].cls = GC_DIAG1;
+        }
     }
     return QS_OK;
 }
