@@ -12,7 +12,9 @@
  *
  * Not in the paper, built beside it: complex64 states, FP64 reductions
  * (norm, marginals, probabilities, Pauli-sum expectations), adjoint gradients
- * of rotation angles, and batched execution of many small circuits.
+ * of rotation angles, batched execution of many small circuits, dense blocks of
+ * gates on qubits 0..5 applied as one matrix on the tensor cores (complex64),
+ * and page-locked host buffers for state transfers.
  *
  * Conventions for every entry point:
  *   - Pointers are plain host or device pointers; sizes are element counts.
