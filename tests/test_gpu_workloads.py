@@ -136,3 +136,30 @@ def test_adjoint_n28_ising(qs):
         assert _log(abs(e[0] - e_ref)) < TOL[dt], dt
         assert _log(max(abs(gr[0][k] - v) for k, v in g_ref.items())) < TOL[dt], dt
     assert _log(float(np.max(np.abs(out[0][1][0] - out[1][1][0])))) < TOL[0]
+
+
+@pytest.mark.parametrize("n,dt", [(33, 1), (34, 0)])
+def test_largest_states_circuit_then_inverse(qs, n, dt):
+    """n = 33 complex128 and n = 34 complex64 (128 GiB each), the 500-gate circuit
+    family of the largest workload, planned and run, then its inverse: the state
+    returns to the basis state |x>.  Checked on 4099 sampled amplitudes (including
+    |x> itself and the ends) and the FP64 norm; no oracle state fits these sizes."""
+    import torch
+    free = torch.cuda.mem_get_info()[0]
+    if free < (8 << n) * (2 if dt == 1 else 1) + (4 << 30):
+        pytest.skip("not enough free device memory for this state")
+    r, _ = G.random_circuit(n, 500, G.SEEDS["random33"])
+    x = G.random_basis(n, 33)
+    rng = np.random.default_rng(n)
+    ys = np.unique(np.concatenate([rng.integers(0, 1 << n, 4096), [0, x, (1 << n) - 1]]))
+    with qs.State.create(n, dt) as s:
+        s.init_basis(x)
+        for gates in (r, G.inverse_circuit(r)):
+            p = s.plan(gates)
+            p.execute()
+            p.close()
+        vals = np.array([s.to_numpy(int(y), 1)[0] for y in ys])
+        nrm = s.norm()
+    want = (ys == x).astype(np.complex128)
+    assert _log(float(np.max(np.abs(vals - want)))) < TOL[dt]
+    assert _log(abs(nrm - 1.0)) < (1e-11 if dt == 1 else 1e-4)
