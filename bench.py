@@ -819,6 +819,26 @@ def run_adjoint28(args):
     print(json.dumps(res), flush=True)
 
 
+def _lanes_vs_pairs(st, m, amp_bytes, stream, torch):
+    """GB/s of a single-qubit gate, and of a gate controlled by the top qubit, on
+    targets 0..4 through each kernel form (the lane exchange and the pair kernel)."""
+    from paper_1601_07195_gb300 import qs
+    n = st.n
+    N = float(1 << n)
+    out = {}
+    for name, mode in (("lanes", qs.LANES_ON), ("pair_kernel", qs.LANES_OFF)):
+        st.set_lanes(mode)
+        g1, gc = [], []
+        for k in range(5):
+            ms, _ = _timed(lambda: [st.apply_1q(k, m) for _ in range(3)], stream, torch)
+            g1.append(2 * N * amp_bytes / (ms / 3 / 1e3) / 1e9)
+            ms, _ = _timed(lambda: [st.apply_ctrl(n - 1, k, m) for _ in range(3)], stream, torch)
+            gc.append(N * amp_bytes / (ms / 3 / 1e3) / 1e9)
+        out[name] = {"gate1q_GBps": g1, "ctrl_top_GBps": gc}
+    st.set_lanes(qs.LANES_AUTO)
+    return out
+
+
 def run_sweeps(args):
     """Per-target single-gate GB/s at n (default 30) complex128 (strided kernels),
     the controlled-gate (c, t) grid (the Fig. 6 analogue), and IQFT fused vs
@@ -845,6 +865,8 @@ def run_sweeps(args):
                 per_k.append(2 * N * 16 / (ms / 3 / 1e3) / 1e9)
             out[f"gate1q_GBps_by_target_{name}"] = per_k
             out[f"gate1q_frac_{name}"] = {"min": min(per_k) / hbm, "max": max(per_k) / hbm}
+            # targets 0..4: the two kernel forms (the line above uses the default choice)
+            out[f"targets0to4_{name}"] = _lanes_vs_pairs(st, haar, 16, stream, torch)
         st.set_arith(False)
         grid = [[None] * n for _ in range(n)]
         for c in (range(n) if "ctrl" in parts else ()):
@@ -854,6 +876,17 @@ def run_sweeps(args):
                 ms, _ = _timed(lambda: st.apply_ctrl(c, t, haar), stream, torch)
                 grid[c][t] = N * 16 / (ms / 1e3) / 1e9
         flat = [v for row in grid for v in row if v is not None]
+    if "gate1q" in parts:
+        with qs.State.create(n, qs.QS_C64, stream=stream) as st:
+            for _ in range(3):
+                st.apply_1q(0, haar)
+            per_k = []
+            for k in range(n):
+                ms, _ = _timed(lambda: [st.apply_1q(k, haar) for _ in range(3)], stream, torch)
+                per_k.append(2 * N * 8 / (ms / 3 / 1e3) / 1e9)
+            out["gate1q_GBps_by_target_c64"] = per_k
+            out["gate1q_frac_c64"] = {"min": min(per_k) / hbm, "max": max(per_k) / hbm}
+            out["targets0to4_c64"] = _lanes_vs_pairs(st, haar, 8, stream, torch)
     if flat:
         out["ctrl_GBps_grid"] = grid
         out["ctrl_GBps_summary"] = {"min": min(flat), "max": max(flat), "mean": statistics.mean(flat),

@@ -113,6 +113,21 @@ QS_API qs_status qs_set_stream(qs_state* s, void* cuda_stream);
  * the FP32 pipes, 1 uses native FP64 instructions (see QS_PLAN_ARITH_F64). */
 QS_API qs_status qs_set_arith(qs_state* s, int native_f64);
 
+/* Kernel form of the single-gate calls whose target t is 0..4 (the partner
+ * amplitude 2^t away lies in the same 32-amplitude group; Section 4.1's SIMD
+ * analogue).  The lane-exchange kernel has each warp read 32 consecutive
+ * amplitudes and exchange partners between lanes with warp shuffles; it
+ * covers non-diagonal single-qubit gates and controlled gates whose control
+ * is 5 or above.  The pair kernel is the one every other target uses.  Both
+ * compute Eq. 2 / Eq. 3 and agree to rounding (bit-exact for X).
+ *   QS_LANES_AUTO (default): the measured choice, lane exchange for native
+ *     FP64 and for complex64 single-qubit gates, the pair kernel for
+ *     double-float complex128 and complex64 controlled gates;
+ *   QS_LANES_OFF: the pair kernel;  QS_LANES_ON: the lane exchange.
+ * Any other mode, or a NULL state: QS_EINVAL. */
+typedef enum { QS_LANES_OFF = 0, QS_LANES_AUTO = 1, QS_LANES_ON = 2 } qs_lane_mode;
+QS_API qs_status qs_set_lanes(qs_state* s, int mode);
+
 /* Device address, qubit count and dtype of a state. */
 QS_API qs_status qs_info(const qs_state* s, void** dev_ptr, int* n, qs_dtype* dt);
 

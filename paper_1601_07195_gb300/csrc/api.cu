@@ -226,6 +226,14 @@ qs_status qs_set_arith(qs_state* s, int native_f64) {
     return QS_OK;
 }
 
+qs_status qs_set_lanes(qs_state* s, int mode) {
+    if (qs_status st = check_state(s)) return st;
+    if (mode != QS_LANES_OFF && mode != QS_LANES_AUTO && mode != QS_LANES_ON)
+        return fail(QS_EINVAL, "lane mode must be QS_LANES_OFF, QS_LANES_AUTO or QS_LANES_ON");
+    s->lane_mode = mode == QS_LANES_AUTO ? 0 : (mode == QS_LANES_ON ? 1 : -1);
+    return QS_OK;
+}
+
 qs_status qs_info(const qs_state* s, void** dev_ptr, int* n, qs_dtype* dt) {
     if (!s) return fail(QS_EINVAL, "state handle is NULL");
     if (dev_ptr) *dev_ptr = s->data;

@@ -158,6 +158,7 @@ struct qs_state {
     double* h_result;    // pinned host staging for reduction results
     size_t h_result_cap;
     bool arith_f64;      // complex128 single-gate kernels: native FP64 instead of double-float
+    int lane_mode;       // single gates on targets 0..4: 0 measured choice, -1 pair kernel, 1 lane exchange
     void* d_dense;       // dense tensor-core block: operand image (bf16 pieces) + error flag
     void* h_dense;       // pinned host staging of that operand image
 };

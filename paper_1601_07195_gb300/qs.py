@@ -21,6 +21,7 @@ PLAN_DEFAULT, PLAN_NO_FUSION, PLAN_GRAPH, PLAN_ARITH_F64, PLAN_DRY_RUN, PLAN_NO_
 PLAN_NO_PHASE_RUNS = 32
 PLAN_NO_PRP = 64
 PLAN_NO_DENSE = 128
+LANES_OFF, LANES_AUTO, LANES_ON = 0, 1, 2  # qs_set_lanes
 
 # one tile-pass record (include/qs_records.h): double-float (complex128 plans),
 # float (complex64) and double (complex128 with PLAN_ARITH_F64) formats
@@ -56,6 +57,7 @@ _SIGS = {
     "qs_destroy": [_vp],
     "qs_set_stream": [_vp, _vp],
     "qs_set_arith": [_vp, ctypes.c_int],
+    "qs_set_lanes": [_vp, ctypes.c_int],
     "qs_info": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "qs_init_basis": [_vp, ctypes.c_uint64],
     "qs_copy_out": [_vp, ctypes.c_uint64, ctypes.c_uint64, _vp],
@@ -251,6 +253,11 @@ class State:
     def set_arith(self, native_f64):
         """complex128 single-gate calls: native FP64 (True) or double-float (False, default)."""
         _check(load().qs_set_arith(self._h, 1 if native_f64 else 0))
+
+    def set_lanes(self, mode):
+        """Single-gate calls on targets 0..4: LANES_AUTO (default, the measured choice),
+        LANES_OFF (pair kernel) or LANES_ON (lane exchange by warp shuffles)."""
+        _check(load().qs_set_lanes(self._h, int(mode)))
 
     # ---- gates
     def apply_1q(self, k, m8):

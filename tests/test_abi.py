@@ -49,8 +49,15 @@ def test_invalid_arguments_rejected_without_gpu():
     m = (ctypes.c_double * 8)(*([0.0] * 8))
     assert lib.qs_apply_1q(None, 0, m) == qs.QS_EINVAL
     assert lib.qs_norm(None, None) == qs.QS_EINVAL
+    assert lib.qs_set_arith(None, 1) == qs.QS_EINVAL
+    assert lib.qs_set_lanes(None, 0) == qs.QS_EINVAL
     assert b"NULL" in lib.qs_last_error()
     assert lib.qs_destroy(None) == qs.QS_OK
+    h = ctypes.c_void_p()
+    assert lib.qs_wrap(ctypes.c_void_p(1 << 20), 6, qs.QS_C64, None, ctypes.byref(h)) == qs.QS_OK
+    assert lib.qs_set_lanes(h, 3) == qs.QS_EINVAL and lib.qs_set_lanes(h, -1) == qs.QS_EINVAL
+    assert all(lib.qs_set_lanes(h, m) == qs.QS_OK for m in (qs.LANES_OFF, qs.LANES_AUTO, qs.LANES_ON))
+    assert lib.qs_destroy(h) == qs.QS_OK
 
 
 def test_wrapped_handle_validates_qubits_before_launch():

@@ -96,6 +96,58 @@ def test_single_qubit_gate_every_qubit_every_class(qs, dt, native, n):
                 assert maxerr(got, want) < TOL[dt], (name, k)
 
 
+@pytest.mark.parametrize("dt,native", [(1, False), (1, True), (0, False)])
+@pytest.mark.parametrize("n", [5, 6, 11, 24])
+def test_lane_exchange_and_pair_kernels_targets_0_to_4(qs, dt, native, n):
+    """Targets 0..4 have two single-gate kernels: the lane exchange (one
+    amplitude per lane, the partner by warp shuffle) and the pair-indexed
+    kernel.  Each mode (forced on, off, and the measured default) is held to
+    the oracle for every class, single-qubit and controlled (controls above
+    the lanes take the lane kernel, controls among them the pair kernel).  n = 5 is one 32-amplitude group, n = 6 two, n = 24
+    enough groups for the grid-stride loop and a ragged last round."""
+    cases = [(name, t, c) for name in ("HAAR", "X", "ANTI", "H", "T") for t in range(5)
+             for c in [None] + [c for c in (0, 5, n - 1) if c < n and c != t]]
+
+    def oracle_apply(want, name, t, c):
+        if c is None:
+            O.apply_1q(want, t, MATS[name])
+        else:
+            O.apply_ctrl(want, c, t, MATS[name])
+
+    def gpu_apply(s, name, t, c):
+        if c is None:
+            s.apply_1q(t, MATS[name])
+        else:
+            s.apply_ctrl(c, t, MATS[name])
+
+    for lanes in (qs.LANES_ON, qs.LANES_OFF, qs.LANES_AUTO):
+        if n >= 24:  # one state through the whole sequence, compared at the end
+            psi = rand_state(n, 77 + n)
+            want = expected_input(psi, dt)
+            with upload(qs, n, dt, psi) as s:
+                s.set_arith(native)
+                s.set_lanes(lanes)
+                for case in cases:
+                    gpu_apply(s, *case)
+                    oracle_apply(want, *case)
+                got = s.to_numpy()
+            assert maxerr(got, want) < TOL[dt], lanes
+            continue
+        for name, t, c in cases:
+            psi = rand_state(n, 7 * t + (c or 0) + n)
+            with upload(qs, n, dt, psi) as s:
+                s.set_arith(native)
+                s.set_lanes(lanes)
+                gpu_apply(s, name, t, c)
+                got = s.to_numpy()
+            want = expected_input(psi, dt)
+            oracle_apply(want, name, t, c)
+            if name == "X":
+                assert np.array_equal(got, want.astype(got.dtype)), (lanes, t, c)
+            else:
+                assert maxerr(got, want) < TOL[dt], (lanes, name, t, c)
+
+
 @pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("n", [2, 7])
 def test_controlled_gate_every_pair(qs, dt, n):
