@@ -342,7 +342,13 @@ QS_API qs_status qs_norm(qs_state* s, double* out);
 /* Marginal P(qubit k = 1) = sum over i with bit k set of |alpha_i|^2.
  * k >= 0: one value into p1[0]; k = -1: all n marginals into p1[0..n-1];
  * k = -2: the n marginals and then the total sum_i |alpha_i|^2 (the squared
- * norm) into p1[0..n], all from the same single read of the state. */
+ * norm) into p1[0..n], all from the same single read of the state.
+ * For k = -1 / -2 on n >= 12 qubits, |alpha_i|^2 and the sums over each
+ * thread's 16 amplitudes of a 4096-amplitude chunk are formed in double-float
+ * arithmetic (about 47 significant bits) and the chunk sums accumulate in
+ * FP64; a chunk holding a component of magnitude 2^60 or more is summed in
+ * FP64 throughout.  Components below 2^-126 contribute nothing (an absolute
+ * error below 2^-96 for 2^30 amplitudes). */
 QS_API qs_status qs_prob(qs_state* s, int k, double* p1);
 
 /* host_out[i] = |alpha_i|^2 for all 2^n amplitudes (host buffer of 2^n doubles). */
@@ -364,7 +370,7 @@ QS_API qs_status qs_expect(qs_state* s, const qs_term* terms, int n_terms, doubl
  *              larger n returns QS_EINVAL because the static array is sized
  *              for at most 36 qubits).
  *   dev_out:   device buffer of n + 1 doubles: out[k] = P(qubit k = 1) for
- *              k < n, out[n] = sum_i |alpha_i|^2.
+ *              k < n, out[n] = sum_i |alpha_i|^2 (arithmetic as qs_prob, k = -2).
  * Asynchronous on cuda_stream; read dev_out after the stream has finished.
  * Each call whose stream is not capturing looks up the array's device
  * address (cudaGetSymbolAddress) with the current device; a captured call

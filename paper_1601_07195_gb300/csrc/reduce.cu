@@ -11,6 +11,7 @@
 #include <mutex>
 
 #include "device.cuh"
+#include "df.cuh"
 
 namespace qs {
 namespace {
@@ -18,7 +19,6 @@ namespace {
 constexpr int kRedThreads = 256;
 constexpr int kChunkBits = 12;                       // marginal chunk: 2^12 amplitudes per block step
 constexpr int kPerThread = 1 << (kChunkBits - 8);    // 16 amplitudes per thread per chunk
-constexpr int kMaxHigh = 40 - kChunkBits;            // chunk-index bits tracked per thread
 
 template <class T>
 __device__ __forceinline__ double prob(const T& a) {
@@ -74,37 +74,120 @@ __global__ void k_finalize(const double* __restrict__ partials, int n_blocks, in
 // the partial sums over r with bit m of r set, and per chunk-index bit the sum
 // of its chunk totals with that bit set; the block then folds the thread-id
 // bits.  Output per block: n + 1 partials (marginals, then the total).
+//
+// Within a chunk, |alpha|^2 and the 16-term tree are formed in double-float
+// arithmetic on the FP32 pipes (about 47 significant bits; df.cuh), and only
+// the five tree results per chunk are rounded to FP64 and accumulated there.
+// In FP64 throughout (two operations per amplitude for |alpha|^2 and 30
+// additions per 16) the FP64 pipe, not HBM, bounded the kernel: 11.3 ms for the
+// n = 30 complex128 state against 2.6 ms to read it.  A chunk that holds a
+// component of magnitude 2^60 or more (whose square would leave the FP32
+// range) takes the FP64 form; components below 2^-126 contribute nothing in
+// the double-float form (at most 2^-96 over a 2^30-amplitude state).
+//
+// With a power-of-two grid, chunk ch = blockIdx.x + j * gridDim.x keeps the low
+// log2(gridDim.x) bits of blockIdx.x, so those marginals come from the block's
+// total and only the bits of j are tracked per chunk.
+
+// |alpha|^2 as an unnormalised double-float pair
+__device__ __forceinline__ dfl prob_df(const double2& a) {
+    const dfl x = split_double_lean(a.x), y = split_double_lean(a.y);
+    const float px = x.h * x.h, py = y.h * y.h;
+    float e = fmaf(x.h, x.h, -px) + fmaf(y.h, y.h, -py);  // the squares' exact rounding errors
+    e = fmaf(2.0f * x.h, x.l, e);                         // cross terms (lo^2 is below 2^-48 of the square)
+    e = fmaf(2.0f * y.h, y.l, e);
+    const dfl s = two_sum(px, py);
+    return {s.h, s.l + e};
+}
+__device__ __forceinline__ dfl prob_df(const float2& a) {
+    const float px = a.x * a.x, py = a.y * a.y;
+    const float e = fmaf(a.x, a.x, -px) + fmaf(a.y, a.y, -py);
+    const dfl s = two_sum(px, py);
+    return {s.h, s.l + e};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    const dfl s = two_sum(a.h, b.h);
+    return {s.h, s.l + (a.l + b.l)};
+}
+__device__ __forceinline__ double df_to_double(dfl v) {
+    return float_to_double_bits_lean(v.h) + float_to_double_bits_lean(v.l);
+}
+// exponent field of the larger component, as an unsigned integer comparable across types
+__device__ __forceinline__ unsigned big_exp(const double2& a) {
+    return max((unsigned)__double2hiint(a.x) & 0x7FF00000u, (unsigned)__double2hiint(a.y) & 0x7FF00000u);
+}
+__device__ __forceinline__ unsigned big_exp(const float2& a) {
+    return max((unsigned)__float_as_int(a.x) & 0x7F800000u, (unsigned)__float_as_int(a.y) & 0x7F800000u);
+}
+template <class T> struct BigExp;
+template <> struct BigExp<double2> { static constexpr unsigned v = (1023u + 60u) << 20; };
+template <> struct BigExp<float2> { static constexpr unsigned v = (127u + 60u) << 23; };
+
+// The chunk tree: t[0..3] = sums over r with bit m of r set, t[4] = the total.
+template <class V, class Add>
+__device__ __forceinline__ void chunk_tree(const V* p, V* t, Add add) {
+    V q[8], o[4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) q[j] = add(p[2 * j], p[2 * j + 1]);
+    t[0] = add(add(add(p[1], p[3]), add(p[5], p[7])), add(add(p[9], p[11]), add(p[13], p[15])));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = add(q[2 * j], q[2 * j + 1]);
+    t[1] = add(add(q[1], q[3]), add(q[5], q[7]));
+    t[2] = add(o[1], o[3]);
+    t[3] = add(o[2], o[3]);
+    t[4] = add(add(o[0], o[1]), t[3]);
+}
+struct AddD {
+    __device__ __forceinline__ double operator()(double a, double b) const { return a + b; }
+};
+struct AddDF {
+    __device__ __forceinline__ dfl operator()(dfl a, dfl b) const { return df_add(a, b); }
+};
+
 template <class T>
 __global__ void __launch_bounds__(kRedThreads) k_marginals(const T* __restrict__ psi, int n, uint64_t n_chunks,
                                                            double* partials) {
     __shared__ double red[32];
-    double tot = 0.0, rbit[4] = {0, 0, 0, 0}, hbit[kMaxHigh];
-#pragma unroll
-    for (int k = 0; k < kMaxHigh; ++k) hbit[k] = 0.0;
+    // per thread, the sums of its chunk totals over chunks whose index bit g + k
+    // is set (k < nh - g), one row of kRedThreads doubles per bit
+    extern __shared__ double hsum[];
+    double tot = 0.0, rbit[4] = {0, 0, 0, 0};
     const int nh = n - kChunkBits;
+    // the grid has 2^g blocks (a power of two, at most the chunk count): chunk
+    // ch = blockIdx.x + j * 2^g has the block's bits below g and j's above
+    const int g = __ffs(gridDim.x) - 1;
+    const int nv = nh - g;
+    for (int k = 0; k < nv; ++k) hsum[k * kRedThreads + threadIdx.x] = 0.0;
     for (uint64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
         const uint64_t base = ch << kChunkBits;
-        double p[kPerThread];
+        T a[kPerThread];
+        unsigned big = 0;
 #pragma unroll
-        for (int r = 0; r < kPerThread; ++r) p[r] = prob(psi[base + ((uint64_t)r << 8) + threadIdx.x]);
-        // pairwise sums: the chunk total and the sums over r with bit m set come from
-        // one tree (30 FP64 additions per 16 amplitudes instead of 48; the FP64 pipe
-        // bounds this kernel on GB300)
-        double q[8], o[4];
+        for (int r = 0; r < kPerThread; ++r) {
+            a[r] = psi[base + ((uint64_t)r << 8) + threadIdx.x];
+            big = max(big, big_exp(a[r]));
+        }
+        double t[5];
+        if (__any_sync(0xffffffffu, big >= BigExp<T>::v)) {
+            double p[kPerThread];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) q[j] = p[2 * j] + p[2 * j + 1];
-        rbit[0] += ((p[1] + p[3]) + (p[5] + p[7])) + ((p[9] + p[11]) + (p[13] + p[15]));
+            for (int r = 0; r < kPerThread; ++r) p[r] = prob(a[r]);
+            chunk_tree<double>(p, t, AddD{});
+        } else {
+            dfl p[kPerThread], u[5];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) o[j] = q[2 * j] + q[2 * j + 1];
-        rbit[1] += (q[1] + q[3]) + (q[5] + q[7]);
-        rbit[2] += o[1] + o[3];
-        const double h1 = o[2] + o[3];
-        rbit[3] += h1;
-        const double s = (o[0] + o[1]) + h1;
+            for (int r = 0; r < kPerThread; ++r) p[r] = prob_df(a[r]);
+            chunk_tree<dfl>(p, u, AddDF{});
+#pragma unroll
+            for (int m = 0; m < 5; ++m) t[m] = df_to_double(u[m]);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) rbit[m] += t[m];
+        const double s = t[4];
         tot += s;
-#pragma unroll
-        for (int k = 0; k < kMaxHigh; ++k)
-            if (k < nh && ((ch >> k) & 1ull)) hbit[k] += s;
+        uint64_t j = ch >> g;
+        for (int k = 0; j != 0; ++k, j >>= 1)
+            if (j & 1ull) hsum[k * kRedThreads + threadIdx.x] += s;
     }
     double* out = partials + (size_t)blockIdx.x * (n + 1);
     for (int k = 0; k < 8; ++k) {
@@ -115,12 +198,11 @@ __global__ void __launch_bounds__(kRedThreads) k_marginals(const T* __restrict__
         const double v = block_sum(rbit[m], red);
         if (threadIdx.x == 0) out[8 + m] = v;
     }
-#pragma unroll
-    for (int k = 0; k < kMaxHigh; ++k) {
-        if (k < nh) {
-            const double v = block_sum(hbit[k], red);
-            if (threadIdx.x == 0) out[kChunkBits + k] = v;
-        }
+    for (int k = 0; k < nh; ++k) {
+        // bits below g are the block's own: its total or nothing
+        const double h = k < g ? (((blockIdx.x >> k) & 1u) ? tot : 0.0) : hsum[(k - g) * kRedThreads + threadIdx.x];
+        const double v = block_sum(h, red);
+        if (threadIdx.x == 0) out[kChunkBits + k] = v;
     }
     const double v = block_sum(tot, red);
     if (threadIdx.x == 0) out[n] = v;
@@ -226,6 +308,21 @@ qs_status norm_impl(qs_state* s, double* out) {
     return sync_result(s, s->d_partials + blocks, 1, out);
 }
 
+// Grid of the marginal kernel: a power of two (its chunk-index bit bookkeeping
+// needs one), at most 512 blocks, the chunk count and `fit`.
+int marginal_blocks(uint64_t chunks, uint64_t fit) {
+    uint64_t b = 512;
+    while (b > chunks || b > fit) b >>= 1;
+    return (int)(b ? b : 1);
+}
+// its dynamic shared memory: one row of per-thread sums per chunk-index bit above log2(blocks)
+size_t marginal_smem(int n, int blocks) {
+    int g = 0;
+    while ((1 << (g + 1)) <= blocks) ++g;
+    const int nv = n - kChunkBits - g;
+    return nv > 0 ? (size_t)nv * kRedThreads * sizeof(double) : 0;
+}
+
 template <class T>
 qs_status marginals_impl(qs_state* s, double* out_all) {
     const int n = s->n;
@@ -236,12 +333,11 @@ qs_status marginals_impl(qs_state* s, double* out_all) {
         return sync_result(s, s->d_partials, n + 1, out_all);
     }
     const uint64_t chunks = 1ull << (n - kChunkBits);
-    uint64_t b = (uint64_t)sm_count() * 4;
-    if (b > chunks) b = chunks;
-    const int blocks = (int)b;
+    const int blocks = marginal_blocks(chunks, ~0ull);
     if (qs_status st = ensure_scratch(s, (size_t)blocks * (n + 1) + (n + 1), n + 1)) return st;
     double* fin = s->d_partials + (size_t)blocks * (n + 1);
-    k_marginals<T><<<blocks, kRedThreads, 0, s->stream>>>((const T*)s->data, n, chunks, s->d_partials);
+    k_marginals<T><<<blocks, kRedThreads, marginal_smem(n, blocks), s->stream>>>((const T*)s->data, n, chunks,
+                                                                                  s->d_partials);
     k_finalize<<<1, 64, 0, s->stream>>>(s->d_partials, blocks, n + 1, n + 1, fin);
     QS_CUDA_TRY(cudaGetLastError());
     return sync_result(s, fin, n + 1, out_all);
@@ -432,14 +528,10 @@ qs_status marginals_noalloc_impl(const void* psi, int n, cudaStream_t st, double
     double* scratch = nullptr;
     if (qs_status s = static_scratch(st, &scratch)) return s;
     const uint64_t chunks = 1ull << (n - kChunkBits);
-    uint64_t b = (uint64_t)sm_count() * 4;
-    const uint64_t fit = (uint64_t)kStaticPartials / (uint64_t)(n + 1);
-    if (b > fit) b = fit;
-    if (b > chunks) b = chunks;
-    const int blocks = (int)b;
+    const int blocks = marginal_blocks(chunks, (uint64_t)kStaticPartials / (uint64_t)(n + 1));
     // every partial the finalize kernel reads is written first by k_marginals, so
     // nothing left over from an earlier call is ever read
-    k_marginals<T><<<blocks, kRedThreads, 0, st>>>((const T*)psi, n, chunks, scratch);
+    k_marginals<T><<<blocks, kRedThreads, marginal_smem(n, blocks), st>>>((const T*)psi, n, chunks, scratch);
     k_finalize<<<1, 64, 0, st>>>(scratch, blocks, n + 1, n + 1, dev_out);
     QS_CUDA_TRY(cudaGetLastError());
     return QS_OK;

@@ -310,7 +310,7 @@ def test_qft_closed_form_n18(qs, dt):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
-@pytest.mark.parametrize("n", [3, 11, 12, 13, 17])
+@pytest.mark.parametrize("n", [3, 11, 12, 13, 17, 24])
 def test_reductions(qs, dt, n):
     psi = rand_state(n, 40 + n)
     ref = expected_input(psi, dt)
@@ -326,6 +326,33 @@ def test_reductions(qs, dt, n):
         marg, total = s.marginals_and_norm()
         assert maxerr(marg, O.marginals(ref)) < 1e-13 and maxerr(total, O.norm2(ref)) < 1e-13
         assert maxerr(s.probs(), O.probs(ref)) < 1e-15
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_marginals_of_states_outside_the_unit_range(qs, dt):
+    """The marginal kernel forms |alpha|^2 and its per-chunk sums in double-float
+    form and takes FP64 for a 2^12-amplitude chunk holding a component of
+    magnitude 2^60 or more.  Unnormalised states: one with a few huge chunks
+    among ordinary ones (both forms in one reduction), one scaled by 2^70
+    throughout, and one scaled by 2^-80, whose squares leave the float range
+    (absolute error bound 2^-96)."""
+    n = 16
+    base = rand_state(n, 91)
+    mixed = base.copy()
+    mixed[(1 << 13):(1 << 13) + (1 << 12)] *= 2.0 ** 70  # one chunk of components near 2^62
+    mixed[5 << 12] = 2.0 ** 61                           # and a single such component in another
+    for psi, rel in ((mixed, True), (base * 2.0 ** 70, True), (base * 2.0 ** -80, False)):
+        if dt == 0 and not np.all(np.isfinite(psi.astype(np.complex64))):
+            continue
+        ref = expected_input(psi, dt)
+        want, total = O.marginals(ref), O.norm2(ref)
+        with upload(qs, n, dt, psi) as s:
+            marg, got_total = s.marginals_and_norm()
+        scale = total if rel else 1.0
+        assert np.max(np.abs(marg - want)) / scale < 1e-13
+        assert abs(got_total - total) / scale < 1e-13
+        if not rel:
+            assert np.max(np.abs(marg - want)) < 2.0 ** -96
 
 
 def test_reductions_are_deterministic(qs):
