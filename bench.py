@@ -622,7 +622,8 @@ def run_ours(args):
                                 "qs_run": 1e3 * statistics.mean(parts[1]),
                                 "marginals_to_host": 1e3 * statistics.mean(parts[2])},
                "h2d_GBps": N * s_bytes / statistics.mean(parts[0]) / 1e9,
-               "host_buffer": "qs_host_alloc (transparent huge pages, page-locked)"}
+               "host_buffer": "qs_host_alloc (transparent huge pages, page-locked)",
+               "host_huge_page_fraction": hostbuf.huge_page_fraction()}
         hostbuf.close()
 
     native = None

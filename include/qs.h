@@ -139,11 +139,15 @@ QS_API qs_status qs_copy_out(qs_state* s, uint64_t off, uint64_t cnt, void* host
 QS_API qs_status qs_copy_in(qs_state* s, uint64_t off, uint64_t cnt, const void* host);
 
 /* Page-locked host memory for qs_copy_in / qs_copy_out, at least `bytes`
- * long, zeroed: an anonymous mapping advised as transparent huge pages, then
- * registered with the CUDA runtime.  On the GB300 nodes measured, copies of a
- * 17 GB state from it ran at full link rate (about 210 GB/s) every time, while
- * page-locked memory of base-size pages (cudaHostAlloc) took up to 4x longer
- * for the first copy after the GPU had been busy or idle for some seconds.
+ * long, zeroed: an anonymous mapping aligned to the transparent huge page size
+ * and advised (and, where the fault path found none free, collapsed) into huge
+ * pages, then registered with the CUDA runtime.  On the GB300 nodes measured
+ * (64 KiB base pages, 512 MiB huge pages), copies of a 17 GB state from a
+ * fully huge-page-backed buffer ran at about 210 GB/s every time, while
+ * cudaHostAlloc memory slowed to 330-690 ms per copy when each copy followed
+ * 0.75 s of kernels on a host whose memory earlier jobs had fragmented.
+ * Huge pages are best effort: on fragmented memory part of the buffer may stay
+ * on base pages, and copies from that part are slower.
  * Free it with qs_host_free.  QS_ENOMEM or QS_ECUDA if it cannot be had. */
 QS_API qs_status qs_host_alloc(size_t bytes, void** out);
 

@@ -159,6 +159,24 @@ class HostBuffer:
     def ptr(self):
         return self._p.value
 
+    def huge_page_fraction(self):
+        """Share of the buffer backed by transparent huge pages (Linux /proc/self/smaps;
+        None where that is not readable)."""
+        lo, size = self._p.value, self.array.nbytes
+        try:
+            with open("/proc/self/smaps") as fh:
+                inside, total = False, 0
+                for line in fh:
+                    head = line.split()[0]
+                    if "-" in head and not head.endswith(":"):
+                        a, b = (int(v, 16) for v in head.split("-"))
+                        inside = a < lo + size and b > lo
+                    elif inside and head == "AnonHugePages:":
+                        total += int(line.split()[1]) * 1024
+            return min(1.0, total / size)
+        except (OSError, ValueError):
+            return None
+
     def close(self):
         if self._p is not None and self._p.value:
             self.array = None
