@@ -86,6 +86,46 @@ __device__ __forceinline__ void gacc_dfprod(GAcc& a, float xh, float xl, float y
 }
 __device__ __forceinline__ double gacc_value(const GAcc& a) { return (double)a.h + (double)a.l; }
 
+// a + b for two accumulators, renormalised (TwoSum of the high parts, then
+// Fast2Sum of the result), so that later sums keep the pair's ~47 bits
+__device__ __forceinline__ GAcc gacc_plus(GAcc a, GAcc b) {
+    const dfl s = two_sum(a.h, b.h);
+    const float t = s.l + (a.l + b.l);
+    const float h = s.h + t;
+    return {h, t - (h - s.h)};
+}
+// Sum over the warp in float pairs (valid in every lane).  A rotation's
+// gradient partial is reduced per gate; in FP64 (a conversion and five
+// additions per thread at 1/64 of the FP32 rate) that reduction cost as much
+// as the gate's double-float arithmetic on both tiles.
+__device__ __forceinline__ GAcc gacc_warp_sum(GAcc a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        GAcc b;
+        b.h = __shfl_xor_sync(0xffffffffu, a.h, o);
+        b.l = __shfl_xor_sync(0xffffffffu, a.l, o);
+        a = gacc_plus(a, b);
+    }
+    return a;
+}
+// Sum over the block, as a double valid in thread 0: warps in float pairs, then
+// the per-warp pairs (in `red`, 32 float2) summed by warp 0 and converted once.
+// Barriers on entry and exit keep `red` reusable.
+__device__ __forceinline__ double gacc_block_sum(GAcc a, float2* red) {
+    a = gacc_warp_sum(a);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = make_float2(a.h, a.l);
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        GAcc w;
+        if (lane < (int)(blockDim.x >> 5)) { w.h = red[lane].x; w.l = red[lane].y; }
+        r = gacc_value(gacc_warp_sum(w));
+    }
+    return r;
+}
+
 // ---- arithmetic traits: complex64 (FP32) and complex128 (double-float) ----------
 struct TrF {
     using E = float2;               // tile element
@@ -222,11 +262,6 @@ __device__ __forceinline__ void adj_pairs_any(typename Tr::E* f, typename Tr::E*
     else adj_pairs<Tr, CLS, THREADS>(f, l, N, cb, tb, op, gen, acc);
 }
 
-__device__ __forceinline__ double warp_sum_only(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // One reversed op on the (phi, lambda) tiles.  A rotation's gradient partial is
 // written to out[op.pad1]: reduced over the CTA (WARP_SLOTS = false), or only
@@ -282,10 +317,12 @@ __device__ __forceinline__ void adj_apply(typename Tr::E* f, typename Tr::E* l, 
     }
     if (gen) {  // uniform over the CTA: every thread takes part in the reduction
         if constexpr (WARP_SLOTS) {
-            const double w = warp_sum_only(active ? gacc_value(acc) : 0.0);
-            if ((threadIdx.x & 31) == 0) out[op.pad1 * (THREADS / 32) + (threadIdx.x >> 5)] = w;
+            // per-warp float pairs; the pass sums them in FP64 once at its end
+            const GAcc w = gacc_warp_sum(active ? acc : GAcc{});
+            if ((threadIdx.x & 31) == 0)
+                reinterpret_cast<float2*>(out)[op.pad1 * (THREADS / 32) + (threadIdx.x >> 5)] = make_float2(w.h, w.l);
         } else {
-            const double s = block_sum_b(active ? gacc_value(acc) : 0.0, red);
+            const double s = gacc_block_sum(active ? acc : GAcc{}, reinterpret_cast<float2*>(red));
             if (threadIdx.x == 0) out[op.pad1] = s;
         }
     }
@@ -307,7 +344,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_tile_adj(typename Tr::G* __rest
     const uint32_t N = 1u << b;
     E* f = reinterpret_cast<E*>(smem_raw);
     E* l = f + N;
-    double* wslots = reinterpret_cast<double*>(l + N);        // n_slots x warps
+    double* wslots = reinterpret_cast<double*>(l + N);        // n_slots x warps, each a float pair
     uint64_t* hioff = reinterpret_cast<uint64_t*>(wslots + (size_t)n_slots * kWarps);
     phi += (uint64_t)blockIdx.y * P.inst_stride;
     lam += (uint64_t)blockIdx.y * P.inst_stride;
@@ -384,9 +421,13 @@ __global__ void __launch_bounds__(kAdjThreads) k_tile_adj(typename Tr::G* __rest
         }
     }
     // rotation partials: the warps' sums in fixed order (slots this pass does not use are never read)
+    const float2* wpairs = reinterpret_cast<const float2*>(wslots);
     for (int sl = threadIdx.x; sl < n_slots; sl += kAdjThreads) {
         double acc = 0.0;
-        for (int w = 0; w < kWarps; ++w) acc += wslots[sl * kWarps + w];
+        for (int w = 0; w < kWarps; ++w) {
+            const float2 v = wpairs[sl * kWarps + w];
+            acc += (double)v.x + (double)v.y;
+        }
         out[sl] = acc;
     }
 }
@@ -532,7 +573,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_batch_small(const SmallDesc* 
         __syncthreads();
         GAcc acc;
         for (uint32_t e = threadIdx.x; e < N; e += kSmallThreads) Tr::re(acc, psi[e], lam[e], 1.0f);
-        const double en = block_sum_b(gacc_value(acc), red);
+        const double en = gacc_block_sum(acc, reinterpret_cast<float2*>(red));
         if (threadIdx.x == 0) energies[d.e_out] = en;
         for (int g = 0; g < d.n_ops; ++g) {  // rev[] is already in reverse circuit order
             const typename Tr::Op op = rev[d.op_off + g];
