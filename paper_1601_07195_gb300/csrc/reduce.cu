@@ -309,11 +309,28 @@ qs_status norm_impl(qs_state* s, double* out) {
 }
 
 // Grid of the marginal kernel: a power of two (its chunk-index bit bookkeeping
-// needs one), at most 512 blocks, the chunk count and `fit`.
+// needs one); at least one resident wave, and up to 1024 blocks while each
+// still gets 64 chunks or more; at most the chunk count and `fit`.  Measured
+// (marginals and norm): n = 30 complex128 3.37 ms with 1024 blocks, 3.76 with
+// 512, 3.81 with 256; n = 26 0.30 ms with 256 blocks, 0.44 with 1024.
+template <class T>
 int marginal_blocks(uint64_t chunks, uint64_t fit) {
-    uint64_t b = 512;
-    while (b > chunks || b > fit) b >>= 1;
-    return (int)(b ? b : 1);
+    static int per_sm = 0;  // resident blocks per SM (registers bound it); the same on every device here
+    if (per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_marginals<T>, kRedThreads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            v = 0;
+        }
+        per_sm = v > 0 ? v : 1;
+    }
+    const uint64_t wave = (uint64_t)per_sm * (uint64_t)sm_count();
+    uint64_t want = 1;
+    while (want * 2 <= wave) want *= 2;                          // the largest power of two in one wave
+    while (want * 2 <= 1024 && want * 2 * 64 <= chunks) want *= 2;  // more blocks while each keeps 64 chunks
+    uint64_t b = 1;
+    while (b * 2 <= chunks && b * 2 <= fit && b * 2 <= want) b *= 2;
+    return (int)b;
 }
 // its dynamic shared memory: one row of per-thread sums per chunk-index bit above log2(blocks)
 size_t marginal_smem(int n, int blocks) {
@@ -333,7 +350,7 @@ qs_status marginals_impl(qs_state* s, double* out_all) {
         return sync_result(s, s->d_partials, n + 1, out_all);
     }
     const uint64_t chunks = 1ull << (n - kChunkBits);
-    const int blocks = marginal_blocks(chunks, ~0ull);
+    const int blocks = marginal_blocks<T>(chunks, ~0ull);
     if (qs_status st = ensure_scratch(s, (size_t)blocks * (n + 1) + (n + 1), n + 1)) return st;
     double* fin = s->d_partials + (size_t)blocks * (n + 1);
     k_marginals<T><<<blocks, kRedThreads, marginal_smem(n, blocks), s->stream>>>((const T*)s->data, n, chunks,
@@ -528,7 +545,7 @@ qs_status marginals_noalloc_impl(const void* psi, int n, cudaStream_t st, double
     double* scratch = nullptr;
     if (qs_status s = static_scratch(st, &scratch)) return s;
     const uint64_t chunks = 1ull << (n - kChunkBits);
-    const int blocks = marginal_blocks(chunks, (uint64_t)kStaticPartials / (uint64_t)(n + 1));
+    const int blocks = marginal_blocks<T>(chunks, (uint64_t)kStaticPartials / (uint64_t)(n + 1));
     // every partial the finalize kernel reads is written first by k_marginals, so
     // nothing left over from an earlier call is ever read
     k_marginals<T><<<blocks, kRedThreads, marginal_smem(n, blocks), st>>>((const T*)psi, n, chunks, scratch);
