@@ -359,10 +359,53 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def secondary_gradients(qs, dtype, torch):
+def partition_instances(costs, world):
+    """Instances to ranks for the batched path: longest first, each to the rank
+    with the least cost so far (cost = 2^n x gates, the work of one instance).
+    Returns one ascending list of instance indices per rank."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    loads, parts = [0.0] * world, [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (loads[q], q))
+        parts[r].append(i)
+        loads[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def gather_results(local, world, dist=None):
+    """The final gather of the batched path: every rank's {instance: (energy,
+    gradients)} merged on all ranks (the only collective besides timing)."""
+    if world == 1 or dist is None:
+        return dict(local)
+    objs = [None] * world
+    dist.all_gather_object(objs, local)
+    merged = {}
+    for o in objs:
+        merged.update(o)
+    return merged
+
+
+def shard_value(count, local_s, world, dist=None):
+    """Instances per second of a batch split over `world` ranks: all `count`
+    instances over the slowest rank's time.  Returns (value, max seconds)."""
+    s = local_s
+    if world > 1 and dist is not None:
+        import torch
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([local_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        s = float(t.item())
+    return count / s, s
+
+
+def secondary_gradients(qs, dtype, torch, world=1, rank=0, dist=None):
     """Batched adjoint gradients of the 512-instance variational workload vs
-    per-circuit central finite differences on the same GPU (sampled)."""
-    insts = G.batch_instances(G.SEEDS["batch512"], count=512)
+    per-circuit central finite differences on the same GPU (sampled).  With
+    `world` ranks the instances are split by cost and each rank runs its share
+    as one batch (no collective until the final gather of the results)."""
+    all_insts = G.batch_instances(G.SEEDS["batch512"], count=512)
+    mine = partition_instances([float(1 << x["n"]) * len(x["gates"]) for x in all_insts], world)[rank]
+    insts = [all_insts[i] for i in mine]
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     batch = qs.Batch(insts, dtype)   # plans, buffers
@@ -370,17 +413,24 @@ def secondary_gradients(qs, dtype, torch):
     t_setup = time.perf_counter() - t0
     reps = 3
     # the new angle sets are drawn before the timed region (input generation is not the method)
-    new_thetas = [[G.angles(len(x["theta"]), 7000 + 1000 * r + k) for k, x in enumerate(insts)] for r in range(reps)]
+    new_thetas = [[G.angles(len(all_insts[i]["theta"]), 7000 + 1000 * r + i) for i in mine] for r in range(reps)]
+    if world > 1:
+        dist.barrier()
     t0 = time.perf_counter()
     for r in range(reps):            # new angles each time: matrices re-staged, graph replayed
-        batch.execute(new_thetas[r])
-    t_adj = (time.perf_counter() - t0) / reps
+        energies, grads = batch.execute(new_thetas[r])
+    t_local = (time.perf_counter() - t0) / reps
+    results = gather_results({i: (float(energies[k]), grads[k]) for k, i in enumerate(mine)}, world, dist)
+    value, t_adj = shard_value(len(all_insts), t_local, world, dist)
+    if len(results) != len(all_insts):
+        raise RuntimeError("batched path: the gather lost instances")
     t0 = time.perf_counter()
     for r in range(reps):            # same angles: graph replay only (no host-side matrix staging)
         batch.execute()
     t_replay = (time.perf_counter() - t0) / reps
     bstats = batch.stats()
     batch.close()
+    insts = all_insts
     # finite-difference comparator: 2P+1 planned energy evaluations per instance (complex128
     # central differences, h = 1e-6), one instance of every qubit count in the batch, weighted
     # by how many instances of that count the batch holds
@@ -388,7 +438,7 @@ def secondary_gradients(qs, dtype, torch):
     for inst in insts:
         by_n.setdefault(inst["n"], []).append(inst)
     fd_s = {}
-    for n, group in sorted(by_n.items()):
+    for n, group in (sorted(by_n.items()) if rank == 0 else ()):  # the comparator runs on rank 0 only
         inst = group[0]
         th = inst["theta"]
         with qs.State.create(n, dtype, stream=stream) as st:
@@ -406,7 +456,7 @@ def secondary_gradients(qs, dtype, torch):
                 energy(tp)
                 energy(tm)
             fd_s[n] = time.perf_counter() - t0
-    fd_total = sum(fd_s[n] * len(g) for n, g in by_n.items())
+    fd_total = sum(fd_s[n] * len(g) for n, g in by_n.items()) if fd_s else float("nan")
     # arithmetic the batch applies, for its bound: forward on psi, then the reverse sweep on
     # phi and lambda, every gate once per state; RY (real) and RZ (diagonal) updates at
     # 44 FP32 flops per amplitude in double-float (complex128) or 6 in FP32 (complex64),
@@ -414,8 +464,9 @@ def secondary_gradients(qs, dtype, torch):
     per_amp = 44.0 if dtype == 1 else 6.0
     flops = sum(3 * 2 * inst["n"] * 8 * per_amp * float(1 << inst["n"]) for inst in insts)  # L = 8 layers
     tf = flops / t_adj / 1e12
-    return {"metric": "batched adjoint-gradient circuits/sec", "value": len(insts) / t_adj, "unit": "circuits/s",
+    return {"metric": "batched adjoint-gradient circuits/sec", "value": value, "unit": "circuits/s",
             "instances": len(insts), "dtype": "c128" if dtype == 1 else "c64", "setup_s": t_setup,
+            "ranks": world, "scaling": "strong" if world > 1 else None,
             "s_per_execution_new_angles": t_adj, "s_per_execution_same_angles": t_replay,
             "persistent_small_instances": bstats["small"], "structure_groups": bstats["groups"],
             "launches_per_execution": bstats["launches"],
@@ -660,8 +711,8 @@ def run_ours(args):
         dense_tc = dense_leg(qs, torch, n, max(3, min(args.steps, 10)))
 
     secondary = None
-    if not args.no_secondary and rank == 0:
-        secondary = secondary_gradients(qs, dtype, torch)
+    if not args.no_secondary:  # every rank runs its share of the instances
+        secondary = secondary_gradients(qs, dtype, torch, world, rank, dist if world > 1 else None)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
