@@ -873,11 +873,15 @@ qs_status record(qs_batch* bt) {
         QS_CUDA_TRY(cudaGetLastError());
         // reverse sweep
         op0 = 0;
-        const size_t smem = ((size_t)2 * sizeof(T) << g.b_adj) + ((size_t)8 << g.b_adj) +
-                            (size_t)g.n_slots * (kAdjThreads / 32) * sizeof(double);
         for (size_t pi = 0; pi < g.rev.size(); ++pi) {
             const PassDesc& d = g.rev[pi];
             TilePass tp = d.tp;
+            // phi and lambda tiles, the per-warp rotation slots, and the 2^(b - b0)
+            // run offsets of this pass (sized per pass: 16 KiB for all 2^b would
+            // leave room for only two CTAs per SM instead of three)
+            const size_t smem = ((size_t)2 * sizeof(T) << tp.b) +
+                                (size_t)g.n_slots * (kAdjThreads / 32) * sizeof(double) +
+                                ((size_t)8 << (tp.b - tp.b0));
             tp.op0 = (int)op0;
             tp.nops = (int)d.members.size();
             tp.inst_stride = N;
