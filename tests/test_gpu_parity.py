@@ -451,6 +451,37 @@ def test_invalid_arguments_on_live_state(qs):
         assert abs(s.norm() - 1.0) < 1e-14
 
 
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n", [1, 2, 5, 12])
+def test_degenerate_circuits_and_states(qs, dt, n):
+    """The method's degenerate cases, on live states: an empty circuit (a plan of
+    no passes, the state untouched bit for bit), a circuit of identities (dropped
+    by the planner), X on every qubit from the all-ones basis state back to |0..0>
+    (bit-exact), and the reductions of a basis state against their exact values."""
+    x = (1 << n) - 1
+    with qs.State.create(n, dt) as s:
+        s.init_basis(x)
+        before = s.to_numpy()
+        p = s.plan(G.concat([]))
+        assert p.stats()["passes"] == 0
+        p.execute()
+        p.close()
+        s.run(G.concat([]))
+        ident = G.concat([G.gate_u1(k, (1, 0, 0, 1)) for k in range(n)])
+        s.run(ident)
+        assert np.array_equal(s.to_numpy(), before)
+        marg, total = s.marginals_and_norm()
+        assert np.array_equal(marg, np.ones(n)) and total == 1.0
+        assert np.array_equal(s.probs(), (np.arange(1 << n) == x).astype(np.float64))
+        z = s.expect(G.terms([(G.P_Z, k, -1, 1.0) for k in range(n)]))
+        assert z == -float(n)
+        s.run(G.concat([G.gate_u1(k, G.MAT_X) for k in range(n)]))
+        got = s.to_numpy()
+    want = np.zeros(1 << n, dtype=got.dtype)
+    want[0] = 1.0
+    assert np.array_equal(got, want)
+
+
 @pytest.mark.parametrize("arith", ["df", "f64"])
 @pytest.mark.parametrize("tile_bits", [0, 7])
 def test_c128_arithmetic_modes_deep_circuit(qs, arith, tile_bits):
