@@ -119,12 +119,12 @@ HBM_FALLBACK_GBS = 6800.0  # used only when no measured copy bandwidth is availa
 # counters are reported as null.
 CSRC = os.path.join(ROOT, "paper_1601_07195_gb300", "csrc")
 NCU_COUNTERS = {
-    "df": {"kernel": "k_tile_df_p<12>", "sources": ["tile_df.cu", "tile_df_ops.cuh", "df.cuh"],
-           "sha": "aa7025dea6ab442a", "n": 26, "dram_bytes": 1.073920e9 + 1.012985e9, "warp_inst": 2.532212736e9,
-           "ms": 2.72144},
-    "c64": {"kernel": "k_tile_p<float, 12>", "sources": ["tile.cu", "tile_ops.cuh"],
-            "sha": "bc1fbe4910456e8f", "n": 27, "dram_bytes": 1.074498e9 + 1.012733e9, "warp_inst": 2.035941376e9,
-            "ms": 1.8864},
+    "df": {"kernel": "k_tile_df_p<12>", "sources": ["tile_df.cu", "tile_df_ops.cuh", "df.cuh", "device.cuh"],
+           "sha": "d6cab46b77aa5766", "n": 26, "dram_bytes": 1.074481e9 + 1.012876e9, "warp_inst": 2.48020992e9,
+           "ms": 2.66112},
+    "c64": {"kernel": "k_tile_p<float, 12>", "sources": ["tile.cu", "tile_ops.cuh", "device.cuh"],
+            "sha": "93359d643c6021a1", "n": 27, "dram_bytes": 1.074398e9 + 1.013030e9, "warp_inst": 1.895563264e9,
+            "ms": 1.859744},
     "dense": {"kernel": "k_dense6_tc", "sources": ["dense_tc.cu"],
               "sha": "9a74760c8df754dc", "n": 25, "dram_bytes": 268.584960e6 + 206.582528e6, "warp_inst": 37525171.0,
               "ms": 0.091456},

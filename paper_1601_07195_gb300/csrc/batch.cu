@@ -219,11 +219,11 @@ __device__ __forceinline__ void adj_pairs_fixed(typename Tr::E* f, typename Tr::
     using E = typename Tr::E;
     if (cb < 0) {
         constexpr int PAIRS = (1 << (B - 1)) / THREADS;
-        const uint32_t i0 = insert_zero32(threadIdx.x, tb), h = 1u << tb;
+        const uint32_t i0 = insert_zero32(threadIdx.x, tb), h = 1u << tb, hm = ~0u << tb;
 #pragma unroll
         for (int m = 0; m < PAIRS; m += 2) {
-            const uint32_t a = i0 + insert_zero32((uint32_t)(m * THREADS), tb);
-            const uint32_t b = i0 + insert_zero32((uint32_t)((m + 1) * THREADS), tb);
+            const uint32_t a = i0 + insert_zero32_hm((uint32_t)(m * THREADS), hm);
+            const uint32_t b = i0 + insert_zero32_hm((uint32_t)((m + 1) * THREADS), hm);
             E f0 = f[a], f1 = f[a + h], l0 = l[a], l1 = l[a + h];
             E g0 = f[b], g1 = f[b + h], k0 = l[b], k1 = l[b + h];
             if (gen) { gen_acc<Tr>(acc, gen, f0, f1, l0, l1); gen_acc<Tr>(acc, gen, g0, g1, k0, k1); }
@@ -238,10 +238,11 @@ __device__ __forceinline__ void adj_pairs_fixed(typename Tr::E* f, typename Tr::
         constexpr int ITEMS = (1 << (B - 2)) / THREADS;
         const int lo = min(cb, tb), hi = max(cb, tb);
         const uint32_t i0 = insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb), h = 1u << tb;
+        const uint32_t hlo = ~0u << lo, hhi = ~0u << hi;
 #pragma unroll
         for (int m = 0; m < ITEMS; m += 2) {
-            const uint32_t a = i0 + insert_two_zeros32((uint32_t)(m * THREADS), lo, hi);
-            const uint32_t b = i0 + insert_two_zeros32((uint32_t)((m + 1) * THREADS), lo, hi);
+            const uint32_t a = i0 + insert_zero32_hm(insert_zero32_hm((uint32_t)(m * THREADS), hlo), hhi);
+            const uint32_t b = i0 + insert_zero32_hm(insert_zero32_hm((uint32_t)((m + 1) * THREADS), hlo), hhi);
             E f0 = f[a], f1 = f[a + h], l0 = l[a], l1 = l[a + h];
             E g0 = f[b], g1 = f[b + h], k0 = l[b], k1 = l[b + h];
             if (gen) { gen_acc<Tr>(acc, gen, f0, f1, l0, l1); gen_acc<Tr>(acc, gen, g0, g1, k0, k1); }

@@ -37,6 +37,10 @@ __device__ __forceinline__ uint32_t insert_zero32(uint32_t p, int k) {
 __device__ __forceinline__ uint32_t insert_two_zeros32(uint32_t p, int lo, int hi) {
     return insert_zero32(insert_zero32(p, lo), hi);
 }
+// The same with the mask of the bits at and above k precomputed (hm = ~0u << k):
+// moving those bits up by one is adding them once more, p + (p & hm).  Two
+// integer instructions per index where p is a compile-time offset.
+__device__ __forceinline__ uint32_t insert_zero32_hm(uint32_t p, uint32_t hm) { return p + (p & hm); }
 
 // Deposit the low bits of v into the set bits of mask (software pdep).
 __device__ __forceinline__ uint64_t deposit_bits(uint64_t v, uint64_t mask) {

@@ -99,7 +99,7 @@ __device__ __forceinline__ void df_tile_1q_fixed(float4* sm, int tb, const float
     static_assert(PAIRS >= 2 && PAIRS % 2 == 0, "tile too small for the fixed path");
     static_assert(THREADS % 32 == 0, "step offsets must leave bits 0..4 alone");
     constexpr int STEP = (PAIRS % kDfIlp == 0) ? kDfIlp : 2;
-    const uint32_t e0 = insert_zero32(threadIdx.x, tb);
+    const uint32_t e0 = insert_zero32(threadIdx.x, tb), hm = ~0u << tb;
     float4* s0 = sm + L::at(e0);
     float4* s1 = sm + L::at(e0 | (1u << tb));
 QS_UNROLL(QS_DF_STEP_UNROLL)
@@ -108,7 +108,7 @@ QS_UNROLL(QS_DF_STEP_UNROLL)
         float4 a[STEP], b[STEP];
 #pragma unroll
         for (int u = 0; u < STEP; ++u) {
-            d[u] = insert_zero32((uint32_t)((m + u) * THREADS), tb);
+            d[u] = insert_zero32_hm((uint32_t)((m + u) * THREADS), hm);
             if (CLS != GC_DIAG1) a[u] = s0[d[u]];
             b[u] = s1[d[u]];
         }
@@ -130,6 +130,7 @@ __device__ __forceinline__ void df_tile_cu_fixed(float4* sm, int cb, int tb, con
     constexpr int STEP = (ITEMS % kDfIlp == 0) ? kDfIlp : 2;
     const int lo = min(cb, tb), hi = max(cb, tb);
     const uint32_t e0 = insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb);
+    const uint32_t hlo = ~0u << lo, hhi = ~0u << hi;
     float4* s0 = sm + L::at(e0);
     float4* s1 = sm + L::at(e0 | (1u << tb));
 QS_UNROLL(QS_DF_STEP_UNROLL)
@@ -138,7 +139,7 @@ QS_UNROLL(QS_DF_STEP_UNROLL)
         float4 a[STEP], b[STEP];
 #pragma unroll
         for (int u = 0; u < STEP; ++u) {
-            d[u] = insert_two_zeros32((uint32_t)((m + u) * THREADS), lo, hi);
+            d[u] = insert_zero32_hm(insert_zero32_hm((uint32_t)((m + u) * THREADS), hlo), hhi);
             if (CLS != GC_DIAG1) a[u] = s0[d[u]];
             b[u] = s1[d[u]];
         }

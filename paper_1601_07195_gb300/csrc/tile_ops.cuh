@@ -83,7 +83,7 @@ __device__ __forceinline__ void tile_1q_fixed(typename Amp<R>::T* sm, int tb, co
     static_assert(THREADS % 32 == 0, "step offsets must leave bits 0..4 alone");
     constexpr int PAIRS = (1 << (B - 1)) / THREADS;
     constexpr int STEP = (PAIRS % kTileIlp == 0) ? kTileIlp : 2;
-    const uint32_t e0 = insert_zero32(threadIdx.x, tb);
+    const uint32_t e0 = insert_zero32(threadIdx.x, tb), hm = ~0u << tb;
     T* s0 = sm + L::at(e0);
     T* s1 = sm + L::at(e0 | (1u << tb));
 QS_UNROLL(QS_TILE_STEP_UNROLL)
@@ -92,7 +92,7 @@ QS_UNROLL(QS_TILE_STEP_UNROLL)
         T a[STEP], b[STEP];
 #pragma unroll
         for (int u = 0; u < STEP; ++u) {
-            d[u] = insert_zero32((uint32_t)((k + u) * THREADS), tb);
+            d[u] = insert_zero32_hm((uint32_t)((k + u) * THREADS), hm);
             if (CLS != GC_DIAG1) a[u] = s0[d[u]];
             b[u] = s1[d[u]];
         }
@@ -114,6 +114,7 @@ __device__ __forceinline__ void tile_cu_fixed(typename Amp<R>::T* sm, int cb, in
     constexpr int STEP = (ITEMS % kTileIlp == 0) ? kTileIlp : 2;
     const int lo = min(cb, tb), hi = max(cb, tb);
     const uint32_t e0 = insert_two_zeros32(threadIdx.x, lo, hi) | (1u << cb);
+    const uint32_t hlo = ~0u << lo, hhi = ~0u << hi;
     T* s0 = sm + L::at(e0);
     T* s1 = sm + L::at(e0 | (1u << tb));
 QS_UNROLL(QS_TILE_STEP_UNROLL)
@@ -122,7 +123,7 @@ QS_UNROLL(QS_TILE_STEP_UNROLL)
         T a[STEP], b[STEP];
 #pragma unroll
         for (int u = 0; u < STEP; ++u) {
-            d[u] = insert_two_zeros32((uint32_t)((k + u) * THREADS), lo, hi);
+            d[u] = insert_zero32_hm(insert_zero32_hm((uint32_t)((k + u) * THREADS), hlo), hhi);
             if (CLS != GC_DIAG1) a[u] = s0[d[u]];
             b[u] = s1[d[u]];
         }
