@@ -41,6 +41,7 @@ __device__ __forceinline__ uint32_t insert_two_zeros32(uint32_t p, int lo, int h
 // moving those bits up by one is adding them once more, p + (p & hm).  Two
 // integer instructions per index where p is a compile-time offset.
 __device__ __forceinline__ uint32_t insert_zero32_hm(uint32_t p, uint32_t hm) { return p + (p & hm); }
+__device__ __forceinline__ uint64_t insert_zero_hm(uint64_t p, uint64_t hm) { return p + (p & hm); }
 
 // Deposit the low bits of v into the set bits of mask (software pdep).
 __device__ __forceinline__ uint64_t deposit_bits(uint64_t v, uint64_t mask) {

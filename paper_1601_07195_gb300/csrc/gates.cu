@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(kThreads) k_strided(typename Amp<R>::T* __rest
     using T = typename Amp<R>::T;
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
     const int lo = min(t, c), hi = max(t, c);
+    const uint64_t hm_lo = ~0ull << lo, hm_hi = ~0ull << hi;  // zero-bit insertion as p + (p & hm)
     for (uint64_t p0 = (uint64_t)blockIdx.x * kThreads + threadIdx.x; p0 < n_items; p0 += stride * kUnroll) {
         uint64_t i0[kUnroll], i1[kUnroll];
         T a[kUnroll], b[kUnroll];
@@ -36,13 +37,13 @@ __global__ void __launch_bounds__(kThreads) k_strided(typename Amp<R>::T* __rest
         for (int u = 0; u < kUnroll; ++u) {
             const uint64_t p = p0 + u * stride;
             if (MODE == 0) {
-                i0[u] = insert_zero(p, t);
+                i0[u] = insert_zero_hm(p, hm_lo);  // lo = t here
                 i1[u] = i0[u] | (1ull << t);
             } else if (MODE == 1) {
-                i0[u] = insert_two_zeros(p, lo, hi) | (1ull << c);
+                i0[u] = insert_zero_hm(insert_zero_hm(p, hm_lo), hm_hi) | (1ull << c);
                 i1[u] = i0[u] | (1ull << t);
             } else {
-                const uint64_t i = insert_two_zeros(p, lo, hi);
+                const uint64_t i = insert_zero_hm(insert_zero_hm(p, hm_lo), hm_hi);
                 i0[u] = i | (1ull << t);
                 i1[u] = i | (1ull << c);
             }
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(kThreads) k_strided_df(double2* __restrict__ p
     for (int j = 0; j < 8; ++j) { cc[2 * j] = hi.v[j]; cc[2 * j + 1] = lo.v[j]; }
     const uint64_t stride = (uint64_t)gridDim.x * kThreads;
     const int lo_q = min(t, c), hi_q = max(t, c);
+    const uint64_t hm_lo = ~0ull << lo_q, hm_hi = ~0ull << hi_q;  // zero-bit insertion as p + (p & hm)
     for (uint64_t p0 = (uint64_t)blockIdx.x * kThreads + threadIdx.x; p0 < n_items; p0 += stride * kUnroll) {
         uint64_t i0[kUnroll], i1[kUnroll];
         double2 a[kUnroll], b[kUnroll];
@@ -82,10 +84,10 @@ __global__ void __launch_bounds__(kThreads) k_strided_df(double2* __restrict__ p
         for (int u = 0; u < kUnroll; ++u) {
             const uint64_t p = p0 + u * stride;
             if (MODE == 0) {
-                i0[u] = insert_zero(p, t);
+                i0[u] = insert_zero_hm(p, hm_lo);  // lo_q = t here
                 i1[u] = i0[u] | (1ull << t);
             } else {
-                i0[u] = insert_two_zeros(p, lo_q, hi_q) | (1ull << c);
+                i0[u] = insert_zero_hm(insert_zero_hm(p, hm_lo), hm_hi) | (1ull << c);
                 i1[u] = i0[u] | (1ull << t);
             }
         }
