@@ -318,11 +318,11 @@ cudaError_t dispatch(qs_state* s, const Op& op) {
 
 // Whether a gate takes the lane-exchange kernel.  The measured choice
 // (lane_mode 0; n = 30, GB/s for targets 0..4, lanes vs pair kernel):
-//   native FP64:  single-qubit 2,335 vs 2,102-2,108, controlled 2,345-2,349 vs 2,100-2,106: lanes
-//   complex64:    single-qubit 6,618-6,621 vs 6,601-6,634 (a tie): lanes;
-//                 controlled 6,103-6,169 vs 6,425-6,545: pair kernel
-//   double-float: single-qubit 5,855-5,877 vs 6,207-6,288, controlled 5,312-5,352 vs
-//                 6,088-6,182: pair kernel (its four extra shuffles per amplitude cost
+//   native FP64:  single-qubit 2,333 vs 2,099-2,106, controlled 2,343-2,347 vs 2,096-2,103: lanes
+//   complex64:    single-qubit 6,607-6,612 vs 6,543-6,645 (a tie): lanes;
+//                 controlled 6,077-6,137 vs 6,507-6,613: pair kernel
+//   double-float: single-qubit 5,849-5,862 vs 6,284-6,397, controlled 5,291-5,330 vs
+//                 6,129-6,248: pair kernel (its four extra shuffles per amplitude cost
 //                 issue slots in a kernel bound by the integer pipe)
 bool lane_op(const qs_state* s, const Op& op, bool arith_f64) {
     if (s->lane_mode < 0 || s->n < 5 || op.t >= 5) return false;
