@@ -330,10 +330,10 @@ __device__ __forceinline__ void df_phase_run(float4* sm, float4* tab, uint32_t N
     const uint32_t lmask = nlo - 1u;
     if constexpr (B > 0 && (1 << (B - 1)) / THREADS >= 1) {
         constexpr int ITEMS = (1 << (B - 1)) / THREADS;
-        const uint32_t e0 = insert_zero32(t, jb) | (1u << jb), s0 = L::at(e0);
+        const uint32_t e0 = insert_zero32(t, jb) | (1u << jb), s0 = L::at(e0), hm = ~0u << jb;
 #pragma unroll
         for (int m = 0; m < ITEMS; ++m) {
-            const uint32_t d = insert_zero32((uint32_t)(m * THREADS), jb);
+            const uint32_t d = insert_zero32_hm((uint32_t)(m * THREADS), hm);
             const uint32_t e = e0 + d;  // tables by tile index, the amplitude by its SMEM place
             sm[s0 + d] = df_cmul_v(df_cmul_v(tlo[e & lmask], thi[e >> lob]), sm[s0 + d]);
         }
