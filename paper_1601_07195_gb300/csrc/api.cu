@@ -278,8 +278,9 @@ qs_status qs_copy_in(qs_state* s, uint64_t off, uint64_t cnt, const void* host) 
 
 // ---- host buffers for transfers -------------------------------------------------
 // Page-locked host memory of base-size pages (what cudaHostAlloc returns) lost up
-// to 4x of its host-to-device rate on the GB300 nodes measured, for the first copy
-// after the GPU had been busy or idle for a few seconds, while an anonymous mapping
+// to 8x of its host-to-device rate on the GB300 nodes measured (64 KiB base pages):
+// for the first copy after the GPU had been busy or idle for a few seconds, and
+// for every copy once other jobs had fragmented host memory.  An anonymous mapping
 // backed by transparent huge pages and then registered kept the full rate on every
 // copy.  The mapping's size is kept here so that qs_host_free needs only the pointer.
 namespace {
