@@ -206,6 +206,17 @@ enum {
                                r, s3, is applied as the bracket (two exact sums and no product
                                per component) with q11 left out.  The scalars left out of one
                                pass multiply to at least 2^-24. */
+    QS_PLAN_NO_DIAG_RUNS = 256, /* apply runs of phase gates that no phase run covers one by
+                               one.  Without it, a run of at least four consecutive gates
+                               inside a tile pass that are diagonal with q11 = 1 and whose
+                               combined phase separates over the low and the high half of the
+                               tile bits (phases on one qubit; controlled phases between a tile
+                               qubit and a qubit outside the tile, between two outside qubits,
+                               or between two tile qubits of the same half) is applied as one
+                               update: per tile, the factor of each tile bit under the tile's
+                               outside bits, tables over the two halves, and two complex
+                               products per amplitude.  Such runs are the inverse QFT's
+                               controlled phases whose target lies outside the tile. */
     QS_PLAN_NO_DENSE = 128  /* complex64 plans: no dense tensor-core passes.  Without it, a run of
                                at least 10 consecutive gates whose qubits all lie in 0..5 is
                                multiplied into one 64 x 64 matrix on the host (FP64) and applied

@@ -8,7 +8,7 @@
  *
  * Record layout (96 bytes, native byte order):
  *   int32 kind    0 single-qubit, 1 controlled, 2 swap, 3 phase-run header,
- *                 4 phase-run payload
+ *                 4 phase-run or diagonal-run payload, 5 diagonal-run header
  *   int32 cls     gate class, see below
  *   int32 tb, tq  target tile bit (-1: outside the tile) and target qubit;
  *                 swap: first qubit
@@ -44,6 +44,16 @@
  * of the qubit in field tb, tq, cb or cq (f = 0..3).  Every amplitude whose
  * bit j is 1 is multiplied by C0 times psi of each of its set tile bits times
  * the factor of each outside qubit it has set.
+ *
+ * Diagonal runs (kind 5 and 4): a header (cls = number of payload records,
+ * tb = number of terms T, cq = lob, the low-half bit count); then ceil(T / 4)
+ * payload records whose slot f holds the factor of term 4r + f and whose int
+ * field tb, tq, cb or cq (f = 0..3) holds type << 16 | x << 8 | y:
+ *   type 0: tile bit x, times outside qubit y (255: unconditional);
+ *   type 1: tile bits x and y (both in one half: both < lob or both >= lob);
+ *   type 2: outside qubit x, times outside qubit y (255: none).
+ * Every amplitude is multiplied by the factor of each term whose bits are all
+ * set in its index.
  */
 #ifndef QS_RECORDS_H
 #define QS_RECORDS_H

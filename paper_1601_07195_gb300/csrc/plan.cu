@@ -519,6 +519,88 @@ void emit_phase_run(const std::vector<Op>& ops, size_t i0, size_t i1, int j, con
     }
 }
 
+// ---- diagonal runs (record layout in qs_internal.h) --------------------------------
+// A phase gate that can join a diagonal run of a pass with tile bits bit_of:
+// its phase separates over the two halves of the tile index unless it couples
+// a tile bit of the low half (< lob) with one of the high half.
+bool drun_gate(const Op& o, const int* bit_of, int lob) {
+    if (!phase_gate(o)) return false;
+    if (o.kind == OP_1Q) return true;
+    const int bt = bit_of[o.t], bc = bit_of[o.c];
+    return !(bt >= 0 && bc >= 0 && ((bt < lob) != (bc < lob)));
+}
+// two complex products on every amplitude (twice a phase gate's half-tile
+// product) and the per-tile tables
+int diag_run_cost(qs_dtype dt) { return 4 * class_cost(GC_DIAG1, dt) + 8 * 12; }
+
+// Length of the diagonal run starting at ops[i] (0: none worth fusing).
+size_t find_diag_run(const std::vector<Op>& ops, size_t i, const int* bit_of, int b, qs_dtype dt) {
+    const int lob = prun_lo_bits(b);
+    size_t k = i;
+    int cost = 0;
+    while (k < ops.size() && drun_gate(ops[k], bit_of, lob)) {
+        cost += phase_gate_cost(ops[k], dt);
+        ++k;
+    }
+    return (k - i >= 4 && cost > diag_run_cost(dt)) ? k - i : 0;
+}
+
+// Records of the diagonal run ops[i0, i1): its gates as bit, pair and scalar
+// terms, equal terms multiplied together.
+template <class OpT>
+void emit_diag_run(const std::vector<Op>& ops, size_t i0, size_t i1, const int* bit_of, int b,
+                   std::vector<OpT>& out) {
+    std::map<int, std::pair<double, double>> terms;  // type << 16 | x << 8 | y -> factor
+    auto add = [&](int type, int x, int y, double fr, double fi) {
+        auto it = terms.emplace(type << 16 | x << 8 | y, std::make_pair(1.0, 0.0)).first;
+        double acc[2] = {it->second.first, it->second.second};
+        cmul_acc(acc, fr, fi);
+        it->second = {acc[0], acc[1]};
+    };
+    for (size_t i = i0; i < i1; ++i) {
+        const Op& o = ops[i];
+        const double fr = o.m[6], fi = o.m[7];  // q22: the phase where every qubit of the gate is 1
+        if (o.kind == OP_1Q) {
+            if (bit_of[o.t] >= 0) add(kDrunBit, bit_of[o.t], kDrunNone, fr, fi);
+            else add(kDrunScalar, o.t, kDrunNone, fr, fi);
+            continue;
+        }
+        const int bt = bit_of[o.t], bc = bit_of[o.c];
+        if (bt >= 0 && bc >= 0) add(kDrunPair, std::min(bt, bc), std::max(bt, bc), fr, fi);
+        else if (bt >= 0) add(kDrunBit, bt, o.c, fr, fi);
+        else if (bc >= 0) add(kDrunBit, bc, o.t, fr, fi);
+        else add(kDrunScalar, std::min(o.t, o.c), std::max(o.t, o.c), fr, fi);
+    }
+    const int n_terms = (int)terms.size(), n_rec = (n_terms + 3) / 4;
+    const double one[2] = {1.0, 0.0};
+    OpT h{};
+    h.kind = OP_DRUN;
+    h.cls = n_rec;
+    h.tb = n_terms;
+    h.tq = -1;
+    h.cb = -1;
+    h.cq = prun_lo_bits(b);
+    set_slot(h, 0, one);
+    out.push_back(h);
+    auto it = terms.begin();
+    for (int r = 0; r < n_rec; ++r) {
+        OpT dr{};
+        dr.kind = OP_PDATA;
+        for (int f = 0; f < 4; ++f) {
+            if (it != terms.end()) {
+                const double v[2] = {it->second.first, it->second.second};
+                set_slot(dr, f, v);
+                set_slot_qubit(dr, f, it->first);
+                ++it;
+            } else {
+                set_slot(dr, f, one);
+                set_slot_qubit(dr, f, kDrunScalar << 16 | kDrunNone << 8 | kDrunNone);  // not read
+            }
+        }
+        out.push_back(dr);
+    }
+}
+
 // Length of the longest run starting at ops[i] and its pivot (-1: none worth fusing).
 size_t find_phase_run(const std::vector<Op>& ops, size_t i, const int* bit_of, qs_dtype dt, int& pivot) {
     pivot = -1;
@@ -635,6 +717,7 @@ qs_status build(qs_plan* p, const std::vector<Op>& all_ops, int b, int b0, bool 
         std::vector<Op> fused = fuse_single_qubit(ops, d.members, p->s->dt, !(p->flags & QS_PLAN_NO_MERGE));
         pp.moves_only = true;
         const bool runs = !(p->flags & QS_PLAN_NO_PHASE_RUNS);
+        const bool druns = !(p->flags & QS_PLAN_NO_DIAG_RUNS);
         std::vector<PrpForm> forms;
         std::vector<char> form;
         double Kpass[2] = {1.0, 0.0};
@@ -644,6 +727,19 @@ qs_status build(qs_plan* p, const std::vector<Op>& all_ops, int b, int b0, bool 
         for (size_t i = 0; i < fused.size();) {
             int pivot = -1;
             const size_t len = runs ? find_phase_run(fused, i, d.bit_of, p->s->dt, pivot) : 0;
+            const size_t dlen = druns ? find_diag_run(fused, i, d.bit_of, d.tp.b, p->s->dt) : 0;
+            if (dlen > len) {
+                const size_t before = tops.size();
+                emit_diag_run(fused, i, i + dlen, d.bit_of, d.tp.b, tops);
+                if (df) t64.resize(t64.size() + (tops.size() - before), TileOp<double>{});
+                // two complex products on every amplitude: the arithmetic of two diagonal gates
+                pp.op_counts[OP_1Q][GC_DIAG] += 2;
+                pp.tp.io |= kIoDiagRuns;
+                pp.moves_only = false;
+                p->device_ops += 1;
+                i += dlen;
+                continue;
+            }
             if (len > 0) {
                 const size_t before = tops.size();
                 emit_phase_run(fused, i, i + len, pivot, d.bit_of, d.tp.b, tops);
@@ -722,7 +818,7 @@ qs_status build(qs_plan* p, const std::vector<Op>& all_ops, int b, int b0, bool 
                 int io = 0;
                 if (k > 0) io |= kIoPairsIn;
                 if (k + 1 < dfp.size()) io |= kIoPairsOut;
-                p->passes[dfp[k]].tp.io = io;
+                p->passes[dfp[k]].tp.io = (p->passes[dfp[k]].tp.io & kIoDiagRuns) | io;
             }
             i = j;
         }

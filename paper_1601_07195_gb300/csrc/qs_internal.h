@@ -46,7 +46,7 @@ enum GateClass : int {
 // Operation kinds after lowering the gate records.  OP_PRUN and OP_PDATA occur
 // only in tile-pass records: a fused run of phase gates around one qubit (a
 // header record followed by cls payload records of kind OP_PDATA).
-enum OpKind : int { OP_1Q = 0, OP_CU = 1, OP_SWAP = 2, OP_PRUN = 3, OP_PDATA = 4 };
+enum OpKind : int { OP_1Q = 0, OP_CU = 1, OP_SWAP = 2, OP_PRUN = 3, OP_PDATA = 4, OP_DRUN = 5 };
 
 // A lowered gate (host side, FP64 matrix).
 struct Op {
@@ -101,11 +101,31 @@ constexpr int kMaxTileBits = 14;
 //           int fields tb, tq, cb, cq (factor slots 0..3)
 // A factor slot f of a record holds one complex number: m[2f], m[2f+1]
 // (native records) or c[4f..4f+3] = re.hi, re.lo, im.hi, im.lo (double-float).
+//
+// Diagonal runs (kind OP_DRUN): a sequence of gates diagonal with q11 = 1 whose
+// combined phase separates over the low and the high half of the tile index
+// (phases on one qubit; controlled phases between a tile bit and an outside
+// qubit, between two outside qubits, or between two tile bits of one half).
+// The run multiplies every amplitude by  T_lo[e & (2^lob - 1)] * T_hi[e >> lob]
+// where, for the tile with base index `base`,
+//   psi_k   = product of the "bit" terms (k, y) with y none or bit y of base set,
+//   C       = product of the "scalar" terms whose outside qubits are all set in base,
+//   T_lo[i] = C * product of psi_k over the set bits k of i, times the "pair"
+//             terms (x, y) of the low half with both bits set in i;
+//   T_hi[u] = the same over the high half.
+// Records:
+//   header  kind OP_DRUN, cls = payload records, tb = number of terms, cq = lob
+//   payload ceil(terms / 4) records; term f of a record: its int field
+//           (tb, tq, cb, cq for f = 0..3) = type << 16 | x << 8 | y, factor slot f
+//           type 0 bit: x = tile bit, y = outside qubit of the condition or 255
+//           type 1 pair: x, y = tile bits of one half
+//           type 2 scalar: x = outside qubit, y = second outside qubit or 255
 inline int prun_lo_bits(int b) { return b / 2; }
-// shared-memory entries (16 bytes each) for T_lo, T_hi and C
+// shared-memory entries (16 bytes each) for T_lo, T_hi, C and the per-bit factors
 inline size_t prun_table_entries(int b) {
-    return ((size_t)1 << prun_lo_bits(b)) + ((size_t)1 << (b - prun_lo_bits(b))) + 1;
+    return ((size_t)1 << prun_lo_bits(b)) + ((size_t)1 << (b - prun_lo_bits(b))) + 1 + (size_t)b;
 }
+constexpr int kDrunBit = 0, kDrunPair = 1, kDrunScalar = 2, kDrunNone = 255;
 
 // Kernel argument describing one tile pass (by value).
 struct TilePass {
@@ -127,6 +147,7 @@ struct TilePass {
 constexpr int kIoPairsIn = 1;   // the pass reads float pairs (no split)
 constexpr int kIoPairsOut = 2;  // the pass writes float pairs (no join)
 constexpr int kIoDiscard = 4;   // reverse adjoint passes: the states are not read again, no store
+constexpr int kIoDiagRuns = 8;  // the pass holds diagonal runs: launched with the kernel variant that applies them
 
 // One pass of a plan, before its ops are converted to device records.
 struct PassDesc {

@@ -29,7 +29,9 @@ constexpr int kTileThreads = QS_TILE_THREADS;
 #endif
 constexpr int kLoadBatch = QS_LOAD_BATCH;
 
-template <class R, int B = 0, class OpAt>
+// DR: the pass holds diagonal runs; passes without them use the variant
+// without that code path (as in tile_df.cu).
+template <class R, int B = 0, bool DR = false, class OpAt>
 __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, const TilePass& P, OpAt op_at) {
     using T = typename Amp<R>::T;
     // complex64 tiles use the bank-spreading layout (tile_ops.cuh)
@@ -40,7 +42,7 @@ __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, 
     const uint32_t N = 1u << b;
     // tile, then the phase-run tables (16 bytes per entry, qs_internal.h), then the run offsets
     unsigned char* tab = smem_raw + (sizeof(T) << b);
-    uint64_t* hioff = reinterpret_cast<uint64_t*>(tab + 16u * ((1u << (b / 2)) + (1u << (b - b / 2)) + 1u));
+    uint64_t* hioff = reinterpret_cast<uint64_t*>(tab + 16u * ((1u << (b / 2)) + (1u << (b - b / 2)) + 1u + (uint32_t)b));
     const uint64_t base = deposit_bits((uint64_t)blockIdx.x, P.nontile_mask);
     for (uint32_t h = threadIdx.x; h < (1u << nh); h += kTileThreads) {
         uint64_t off = 0;
@@ -75,6 +77,10 @@ __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, 
             phase_run<R, kTileThreads, B, L>(sm, tab, N, b, op, op_at, g, base);
             g += op.cls;  // the run's payload records
             __syncthreads();
+        } else if (DR && op.kind == OP_DRUN) {
+            if constexpr (DR) diag_run<R, kTileThreads, B, L>(sm, tab, N, b, op, op_at, g, base);
+            g += op.cls;
+            __syncthreads();
         } else if (tile_apply<R, kTileThreads, B, L>(sm, N, op, base)) {
             __syncthreads();
         }
@@ -83,12 +89,12 @@ __device__ __forceinline__ void tile_body(typename Amp<R>::T* __restrict__ psi, 
 }
 
 // ops in device memory (batched launches: one op array per instance)
-template <class R>
+template <class R, bool DR>
 __global__ void __launch_bounds__(kTileThreads) k_tile(typename Amp<R>::T* __restrict__ psi,
                                                        const TileOp<R>* __restrict__ ops, TilePass P) {
     psi += (uint64_t)blockIdx.y * P.inst_stride;
     ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride + P.op0;
-    tile_body<R>(psi, P, [&](int g) -> const TileOp<R>& { return ops[g]; });
+    tile_body<R, 0, DR>(psi, P, [&](int g) -> const TileOp<R>& { return ops[g]; });
 }
 
 // ops in the kernel's parameter block (constant cache, no global load per op)
@@ -98,38 +104,41 @@ template <class R> struct TileParams {
     TileOp<R> ops[kOps];
 };
 
-template <class R, int B>
+template <class R, int B, bool DR>
 __global__ void __launch_bounds__(kTileThreads) k_tile_p(typename Amp<R>::T* __restrict__ psi,
                                                          const __grid_constant__ TileParams<R> L) {
-    tile_body<R, B>(psi, L.P, [&](int g) -> const TileOp<R>& { return L.ops[g]; });
+    tile_body<R, B, DR>(psi, L.P, [&](int g) -> const TileOp<R>& { return L.ops[g]; });
 }
 
-template <class R, int B>
+template <class R, int B, bool DR = false>
 cudaError_t launch_p(qs_state* s, const TileParams<R>& L, size_t smem) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_p<R, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
+        cudaError_t e = cudaFuncSetAttribute(k_tile_p<R, B, DR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
         if (e != cudaSuccess) return e;
         configured = true;
     }
     const dim3 grid((unsigned)(1ull << (s->n - L.P.b)), 1);
-    k_tile_p<R, B><<<grid, kTileThreads, smem, s->stream>>>(reinterpret_cast<typename Amp<R>::T*>(s->data), L);
+    k_tile_p<R, B, DR><<<grid, kTileThreads, smem, s->stream>>>(reinterpret_cast<typename Amp<R>::T*>(s->data), L);
     return cudaGetLastError();
 }
 
 template <class R>
 cudaError_t launch_tile(qs_state* s, const void* d_ops, const TilePass& P, unsigned count) {
     const size_t smem = tile_pass_smem(s->dt, P.b, P.b0);
-    static bool configured[2] = {false, false};
-    const int which = sizeof(R) == 8 ? 1 : 0;
-    if (!configured[which]) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
+    static bool configured[2][2] = {{false, false}, {false, false}};
+    const int which = sizeof(R) == 8 ? 1 : 0, dr = (P.io & kIoDiagRuns) ? 1 : 0;
+    if (!configured[which][dr]) {
+        cudaError_t e = dr ? cudaFuncSetAttribute(k_tile<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin())
+                           : cudaFuncSetAttribute(k_tile<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
         if (e != cudaSuccess) return e;
-        configured[which] = true;
+        configured[which][dr] = true;
     }
     const dim3 grid((unsigned)(1ull << (s->n - P.b)), count);
-    k_tile<R><<<grid, kTileThreads, smem, s->stream>>>(reinterpret_cast<typename Amp<R>::T*>(s->data),
-                                                       reinterpret_cast<const TileOp<R>*>(d_ops), P);
+    auto* psi = reinterpret_cast<typename Amp<R>::T*>(s->data);
+    auto* ops = reinterpret_cast<const TileOp<R>*>(d_ops);
+    if (dr) k_tile<R, true><<<grid, kTileThreads, smem, s->stream>>>(psi, ops, P);
+    else k_tile<R, false><<<grid, kTileThreads, smem, s->stream>>>(psi, ops, P);
     return cudaGetLastError();
 }
 
@@ -141,6 +150,13 @@ cudaError_t launch_tile_p(qs_state* s, const void* h_ops, const TilePass& P) {
     L.P = P;
     L.P.op0 = 0;
     std::memcpy(L.ops, reinterpret_cast<const TileOp<R>*>(h_ops) + P.op0, sizeof(TileOp<R>) * (size_t)P.nops);
+    if (P.io & kIoDiagRuns) {
+        switch (P.b) {
+        case 12: return launch_p<R, 12, true>(s, L, smem);
+        case 13: return launch_p<R, 13, true>(s, L, smem);
+        default: return launch_p<R, 0, true>(s, L, smem);
+        }
+    }
     switch (P.b) {
     case 11: return launch_p<R, 11>(s, L, smem);
     case 12: return launch_p<R, 12>(s, L, smem);

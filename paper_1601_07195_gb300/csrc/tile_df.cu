@@ -34,8 +34,11 @@ constexpr int kLoadBatch = QS_LOAD_BATCH;
 using kDfLayout = std::conditional<QS_DF_SWIZZLE != 0, Swizzled16Layout, FlatLayout>::type;
 
 // The pass body; OpAt(g) yields op g of the pass.  B > 0: the tile has
-// exactly 2^B amplitudes and the fixed-size gate paths are used.
-template <int B = 0, class OpAt>
+// exactly 2^B amplitudes and the fixed-size gate paths are used.  DR: the pass
+// holds diagonal runs.  Passes without them use the variant without that code:
+// compiled in, it raised the kernel's registers from 40 to 61 and slowed
+// passes without any run by 10%.
+template <int B = 0, bool DR = false, class OpAt>
 __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const TilePass& P, OpAt op_at) {
     using L = kDfLayout;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -44,7 +47,7 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
     const uint32_t N = 1u << b;
     // tile, then the phase-run tables (qs_internal.h), then the run offsets
     float4* tab = sm + N;
-    uint64_t* hioff = reinterpret_cast<uint64_t*>(tab + (1u << (b / 2)) + (1u << (b - b / 2)) + 1u);
+    uint64_t* hioff = reinterpret_cast<uint64_t*>(tab + (1u << (b / 2)) + (1u << (b - b / 2)) + 1u + (uint32_t)b);
     const uint64_t base = deposit_bits((uint64_t)blockIdx.x, P.nontile_mask);
     for (uint32_t h = threadIdx.x; h < (1u << nh); h += kThreads) {
         uint64_t off = 0;
@@ -94,6 +97,10 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
             df_phase_run<kThreads, B, L>(sm, tab, N, b, op, op_at, g, base);
             g += op.cls;  // the run's payload records
             __syncthreads();
+        } else if (DR && op.kind == OP_DRUN) {
+            if constexpr (DR) df_diag_run<kThreads, B, L>(sm, tab, N, b, op, op_at, g, base);
+            g += op.cls;
+            __syncthreads();
         } else if (df_tile_apply<kThreads, B, L>(sm, N, op, base)) {
             __syncthreads();
         }
@@ -114,25 +121,25 @@ __device__ __forceinline__ void tile_df_body(double2* __restrict__ psi, const Ti
 }
 
 // ops in device memory (batched launches: one op array per instance)
-template <int B>
+template <int B, bool DR>
 __global__ void __launch_bounds__(kThreads) k_tile_df(double2* __restrict__ psi, const TileOpDF* __restrict__ ops,
                                                       TilePass P) {
     psi += (uint64_t)blockIdx.y * P.inst_stride;
     ops += (uint64_t)blockIdx.y * (uint64_t)P.ops_stride + P.op0;
-    tile_df_body<B>(psi, P, [&](int g) -> const TileOpDF& { return ops[g]; });
+    tile_df_body<B, DR>(psi, P, [&](int g) -> const TileOpDF& { return ops[g]; });
 }
 
-template <int B>
+template <int B, bool DR>
 cudaError_t launch_df_ptr(qs_state* s, const void* d_ops, const TilePass& P, unsigned count, size_t smem) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_df<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
+        cudaError_t e = cudaFuncSetAttribute(k_tile_df<B, DR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
         if (e != cudaSuccess) return e;
         configured = true;
     }
     const dim3 grid((unsigned)(1ull << (s->n - P.b)), count);
-    k_tile_df<B><<<grid, kThreads, smem, s->stream>>>(reinterpret_cast<double2*>(s->data),
-                                                      reinterpret_cast<const TileOpDF*>(d_ops), P);
+    k_tile_df<B, DR><<<grid, kThreads, smem, s->stream>>>(reinterpret_cast<double2*>(s->data),
+                                                          reinterpret_cast<const TileOpDF*>(d_ops), P);
     return cudaGetLastError();
 }
 
@@ -145,22 +152,22 @@ struct TileParamsDF {
 };
 static_assert(sizeof(TileParamsDF) <= 32000, "kernel parameter block too large");
 
-template <int B>
+template <int B, bool DR>
 __global__ void __launch_bounds__(kThreads) k_tile_df_p(double2* __restrict__ psi,
                                                         const __grid_constant__ TileParamsDF L) {
-    tile_df_body<B>(psi, L.P, [&](int g) -> const TileOpDF& { return L.ops[g]; });
+    tile_df_body<B, DR>(psi, L.P, [&](int g) -> const TileOpDF& { return L.ops[g]; });
 }
 
-template <int B>
+template <int B, bool DR>
 cudaError_t launch_df_p(qs_state* s, const TileParamsDF& L, size_t smem) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_df_p<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
+        cudaError_t e = cudaFuncSetAttribute(k_tile_df_p<B, DR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
         if (e != cudaSuccess) return e;
         configured = true;
     }
     const dim3 grid((unsigned)(1ull << (s->n - L.P.b)), 1);
-    k_tile_df_p<B><<<grid, kThreads, smem, s->stream>>>(reinterpret_cast<double2*>(s->data), L);
+    k_tile_df_p<B, DR><<<grid, kThreads, smem, s->stream>>>(reinterpret_cast<double2*>(s->data), L);
     return cudaGetLastError();
 }
 
@@ -179,12 +186,19 @@ cudaError_t launch_tile_df_params(qs_state* s, const TileOpDF* h_ops, const Tile
     L.P.op0 = 0;
     std::memcpy(L.ops, h_ops + P.op0, sizeof(TileOpDF) * (size_t)P.nops);
     // fixed-size instantiations for the tile sizes the planner and autotuner use
+    if (P.io & kIoDiagRuns) {
+        switch (P.b) {
+        case 12: return launch_df_p<12, true>(s, L, smem);
+        case 13: return launch_df_p<13, true>(s, L, smem);
+        default: return launch_df_p<0, true>(s, L, smem);
+        }
+    }
     switch (P.b) {
-    case 10: return launch_df_p<10>(s, L, smem);
-    case 11: return launch_df_p<11>(s, L, smem);
-    case 12: return launch_df_p<12>(s, L, smem);
-    case 13: return launch_df_p<13>(s, L, smem);
-    default: return launch_df_p<0>(s, L, smem);
+    case 10: return launch_df_p<10, false>(s, L, smem);
+    case 11: return launch_df_p<11, false>(s, L, smem);
+    case 12: return launch_df_p<12, false>(s, L, smem);
+    case 13: return launch_df_p<13, false>(s, L, smem);
+    default: return launch_df_p<0, false>(s, L, smem);
     }
 }
 
@@ -192,10 +206,14 @@ int tile_df_param_ops() { return kParamOps; }
 
 cudaError_t launch_tile_df(qs_state* s, const void* d_ops, const TilePass& P, unsigned count) {
     const size_t smem = tile_pass_smem(s->dt, P.b, P.b0);
+    if (P.io & kIoDiagRuns) {
+        if (P.b == 12) return launch_df_ptr<12, true>(s, d_ops, P, count, smem);
+        return launch_df_ptr<0, true>(s, d_ops, P, count, smem);
+    }
     switch (P.b) {
-    case 12: return launch_df_ptr<12>(s, d_ops, P, count, smem);
-    case 13: return launch_df_ptr<13>(s, d_ops, P, count, smem);
-    default: return launch_df_ptr<0>(s, d_ops, P, count, smem);
+    case 12: return launch_df_ptr<12, false>(s, d_ops, P, count, smem);
+    case 13: return launch_df_ptr<13, false>(s, d_ops, P, count, smem);
+    default: return launch_df_ptr<0, false>(s, d_ops, P, count, smem);
     }
 }
 

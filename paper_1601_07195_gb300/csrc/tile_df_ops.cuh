@@ -345,6 +345,89 @@ __device__ __forceinline__ void df_phase_run(float4* sm, float4* tab, uint32_t N
     }
 }
 
+// Term i of the diagonal run whose header is record g: its factor, and its
+// type and indices from the int field of its slot (qs_internal.h).
+template <class OpAt>
+__device__ __forceinline__ float4 df_drun_term(OpAt op_at, int g, int i, int& type, int& x, int& y) {
+    const TileOpDF& r = op_at(g + 1 + (i >> 2));
+    const int f = i & 3;
+    const int code = slot_qubit(r, f);
+    type = code >> 16;
+    x = (code >> 8) & 255;
+    y = code & 255;
+    return df_slot(r, f);
+}
+
+// Applies the diagonal run whose header is record g.  Three steps, each ended
+// by a barrier (the caller's barrier ends the last):
+//   1. thread k < b forms psi_k from the bit terms of tile bit k whose outside
+//      condition holds for this tile; the last thread forms C from the scalar terms;
+//   2. threads [0, 2^lob) form T_lo (times C), the next 2^hib threads T_hi, each
+//      with the pair terms of its half;
+//   3. every amplitude is multiplied by T_lo[e & (2^lob - 1)] * T_hi[e >> lob].
+template <int THREADS, int B, class L, class OpAt>
+__device__ __forceinline__ void df_diag_run(float4* sm, float4* tab, uint32_t N, int b, const TileOpDF& h,
+                                            OpAt op_at, int g, uint64_t base) {
+    const int n_terms = h.tb, lob = h.cq, hib = b - lob;
+    const uint32_t nlo = 1u << lob, nhi = 1u << hib;
+    float4* tlo = tab;
+    float4* thi = tab + nlo;
+    float4* tc = tab + nlo + nhi;
+    float4* psi = tc + 1;
+    const uint32_t t = threadIdx.x;
+    const float4 one = make_float4(1.f, 0.f, 0.f, 0.f);
+    auto holds = [&](int q) { return q == kDrunNone || ((base >> q) & 1ull) != 0; };
+    if ((int)t < b) {
+        float4 v = one;
+        for (int i = 0; i < n_terms; ++i) {
+            int type, x, y;
+            const float4 f = df_drun_term(op_at, g, i, type, x, y);
+            if (type == kDrunBit && x == (int)t && holds(y)) v = df_cmul_v(f, v);
+        }
+        psi[t] = v;
+    } else if (t == THREADS - 1) {
+        float4 v = one;
+        for (int i = 0; i < n_terms; ++i) {
+            int type, x, y;
+            const float4 f = df_drun_term(op_at, g, i, type, x, y);
+            if (type == kDrunScalar && holds(x) && holds(y)) v = df_cmul_v(f, v);
+        }
+        *tc = v;
+    }
+    __syncthreads();
+    if (t < nlo + nhi) {
+        const bool low = t < nlo;
+        const uint32_t u = low ? t : t - nlo;
+        const int k0 = low ? 0 : lob, nb = low ? lob : hib;
+        float4 v = low ? *tc : one;
+        for (int k = 0; k < nb; ++k)
+            if ((u >> k) & 1u) v = df_cmul_v(psi[k0 + k], v);
+        for (int i = 0; i < n_terms; ++i) {
+            int type, x, y;
+            const float4 f = df_drun_term(op_at, g, i, type, x, y);
+            if (type == kDrunPair && x >= k0 && x < k0 + nb && ((u >> (x - k0)) & 1u) && ((u >> (y - k0)) & 1u))
+                v = df_cmul_v(f, v);
+        }
+        if (low) tlo[u] = v;
+        else thi[u] = v;
+    }
+    __syncthreads();
+    const uint32_t lmask = nlo - 1u;
+    if constexpr (B > 0 && (1 << B) >= THREADS) {
+        constexpr int PER = (1 << B) / THREADS;
+#pragma unroll 4
+        for (int m = 0; m < PER; ++m) {
+            const uint32_t e = t + (uint32_t)(m * THREADS), se = L::at(e);
+            sm[se] = df_cmul_v(df_cmul_v(tlo[e & lmask], thi[e >> lob]), sm[se]);
+        }
+    } else {
+        for (uint32_t e = t; e < N; e += THREADS) {
+            const uint32_t se = L::at(e);
+            sm[se] = df_cmul_v(df_cmul_v(tlo[e & lmask], thi[e >> lob]), sm[se]);
+        }
+    }
+}
+
 template <int THREADS, int B = 0, class L = FlatLayout>
 __device__ __forceinline__ bool df_tile_apply(float4* sm, uint32_t N, const TileOpDF& op, uint64_t base) {
     if (op.kind == OP_SWAP) {

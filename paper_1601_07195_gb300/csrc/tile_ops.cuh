@@ -285,6 +285,85 @@ __device__ __forceinline__ void phase_run(typename Amp<R>::T* sm, void* tab_raw,
     }
 }
 
+// Applies the diagonal run whose header is record g; steps and barriers as in
+// df_diag_run (tile_df_ops.cuh): per-bit factors psi_k and the per-tile C, then
+// T_lo (times C) and T_hi with the pair terms of each half, then every
+// amplitude times T_lo * T_hi.  The tables live in `tab`, 16 bytes per entry.
+template <class R, int THREADS, int B, class L, class OpAt>
+__device__ __forceinline__ void diag_run(typename Amp<R>::T* sm, void* tab_raw, uint32_t N, int b,
+                                         const TileOp<R>& h, OpAt op_at, int g, uint64_t base) {
+    using T = typename Amp<R>::T;
+    const int n_terms = h.tb, lob = h.cq, hib = b - lob;
+    const uint32_t nlo = 1u << lob, nhi = 1u << hib;
+    T* tlo = reinterpret_cast<T*>(tab_raw);
+    T* thi = tlo + nlo;
+    T* tc = tlo + nlo + nhi;
+    T* psi = tc + 1;
+    const uint32_t t = threadIdx.x;
+    T one;
+    one.x = (R)1;
+    one.y = (R)0;
+    auto term = [&](int i, int& type, int& x, int& y) -> T {
+        const TileOp<R>& r = op_at(g + 1 + (i >> 2));
+        const int f = i & 3;
+        const int code = slot_qubit(r, f);
+        type = code >> 16;
+        x = (code >> 8) & 255;
+        y = code & 255;
+        return slot_value<T>(r, f);
+    };
+    auto holds = [&](int q) { return q == kDrunNone || ((base >> q) & 1ull) != 0; };
+    if ((int)t < b) {
+        T v = one;
+        for (int i = 0; i < n_terms; ++i) {
+            int type, x, y;
+            const T f = term(i, type, x, y);
+            if (type == kDrunBit && x == (int)t && holds(y)) v = cmul_v(f, v);
+        }
+        psi[t] = v;
+    } else if (t == THREADS - 1) {
+        T v = one;
+        for (int i = 0; i < n_terms; ++i) {
+            int type, x, y;
+            const T f = term(i, type, x, y);
+            if (type == kDrunScalar && holds(x) && holds(y)) v = cmul_v(f, v);
+        }
+        *tc = v;
+    }
+    __syncthreads();
+    if (t < nlo + nhi) {
+        const bool low = t < nlo;
+        const uint32_t u = low ? t : t - nlo;
+        const int k0 = low ? 0 : lob, nb = low ? lob : hib;
+        T v = low ? *tc : one;
+        for (int k = 0; k < nb; ++k)
+            if ((u >> k) & 1u) v = cmul_v(psi[k0 + k], v);
+        for (int i = 0; i < n_terms; ++i) {
+            int type, x, y;
+            const T f = term(i, type, x, y);
+            if (type == kDrunPair && x >= k0 && x < k0 + nb && ((u >> (x - k0)) & 1u) && ((u >> (y - k0)) & 1u))
+                v = cmul_v(f, v);
+        }
+        if (low) tlo[u] = v;
+        else thi[u] = v;
+    }
+    __syncthreads();
+    const uint32_t lmask = nlo - 1u;
+    if constexpr (B > 0 && (1 << B) >= THREADS) {
+        constexpr int PER = (1 << B) / THREADS;
+#pragma unroll 4
+        for (int m = 0; m < PER; ++m) {
+            const uint32_t e = t + (uint32_t)(m * THREADS), se = L::at(e);
+            sm[se] = cmul_v(cmul_v(tlo[e & lmask], thi[e >> lob]), sm[se]);
+        }
+    } else {
+        for (uint32_t e = t; e < N; e += THREADS) {
+            const uint32_t se = L::at(e);
+            sm[se] = cmul_v(cmul_v(tlo[e & lmask], thi[e >> lob]), sm[se]);
+        }
+    }
+}
+
 template <class R, int THREADS, int B = 0, class L = FlatLayout>
 __device__ __forceinline__ bool tile_apply(typename Amp<R>::T* sm, uint32_t N, const TileOp<R>& op, uint64_t base) {
     if (op.kind == OP_SWAP) {

@@ -21,6 +21,7 @@ PLAN_DEFAULT, PLAN_NO_FUSION, PLAN_GRAPH, PLAN_ARITH_F64, PLAN_DRY_RUN, PLAN_NO_
 PLAN_NO_PHASE_RUNS = 32
 PLAN_NO_PRP = 64
 PLAN_NO_DENSE = 128
+PLAN_NO_DIAG_RUNS = 256
 LANES_OFF, LANES_AUTO, LANES_ON = 0, 1, 2  # qs_set_lanes
 
 # one tile-pass record (include/qs_records.h): double-float (complex128 plans),

@@ -2,7 +2,7 @@
 
 Applies the records each tile pass hands its kernel (include/qs_records.h) to
 a whole state vector in complex128 numpy arithmetic, with each record double
-taken as hi + lo.  Single-gate passes apply their gate through the oracle; dense passes (complex64
+taken as hi + lo (phase runs and diagonal runs included).  Single-gate passes apply their gate through the oracle; dense passes (complex64
 plans) apply the 64 x 64 matrix the planner formed for them.
 Comparing the result with the oracle applying the circuit checks the
 planner's rewrites on the CPU: the products of adjacent gates, the phase-run
@@ -77,6 +77,28 @@ def apply_records(psi, recs, tile_qubits, fmt=1):
                 fac = np.where((idx >> q) & 1, fac * _Rec(pr, fmt).cpx(2 * f), fac)
             sel = ((idx >> j) & 1) == 1
             psi[sel] *= fac[sel]
+            g += 1 + cls
+            continue
+        if kind == 5:  # diagonal run: header, then bit / pair / scalar terms, four per record
+            n_terms = int(r["tb"])
+            fac = np.ones(psi.size, dtype=np.complex128)
+            for i in range(n_terms):
+                pr = recs[g + 1 + i // 4]
+                f = i % 4
+                code = int((pr["tb"], pr["tq"], pr["cb"], pr["cq"])[f])
+                typ, x, y = code >> 16, (code >> 8) & 255, code & 255
+                if typ == 0:    # tile bit x, outside condition y (255: none)
+                    on = (idx >> tile_qubits[x]) & 1
+                    if y != 255:
+                        on = on & ((idx >> y) & 1)
+                elif typ == 1:  # tile bits x and y
+                    on = ((idx >> tile_qubits[x]) & 1) & ((idx >> tile_qubits[y]) & 1)
+                else:           # outside qubits x and y (255: none)
+                    on = (idx >> x) & 1
+                    if y != 255:
+                        on = on & ((idx >> y) & 1)
+                fac = np.where(on == 1, fac * _Rec(pr, fmt).cpx(2 * f), fac)
+            psi *= fac
             g += 1 + cls
             continue
         if kind == 2:

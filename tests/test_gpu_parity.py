@@ -452,6 +452,27 @@ def test_invalid_arguments_on_live_state(qs):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("n,tile_bits", [(14, 8 | (3 << 8)), (20, 0), (22, 12 | (4 << 8))])
+def test_diagonal_runs_match_oracle(qs, dt, n, tile_bits):
+    """Diagonal runs (one record set per run of phase gates that separates over
+    the two halves of the tile bits) on the GPU: runs of every term kind, and the
+    inverse QFT of a random state, against the oracle; the same circuits with
+    QS_PLAN_NO_DIAG_RUNS give the same states."""
+    from tests.test_plan_records import diag_circuit
+    for gates in (diag_circuit(n, 12, 700 + n, outside_from=4), G.inverse_circuit(G.qft_circuit(n))):
+        psi = rand_state(n, 31 + n)
+        want = expected_input(psi, dt)
+        want = O.run(want, gates)
+        for flags in (qs.PLAN_DEFAULT, qs.PLAN_NO_DIAG_RUNS):
+            with upload(qs, n, dt, psi) as s:
+                p = s.plan(gates, flags=flags, tile_bits=tile_bits)
+                p.execute()
+                p.close()
+                got = s.to_numpy()
+            assert maxerr(got, want) < TOL[dt], (flags, n)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("n", [1, 2, 5, 12])
 def test_degenerate_circuits_and_states(qs, dt, n):
     """The method's degenerate cases, on live states: an empty circuit (a plan of

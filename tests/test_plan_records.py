@@ -107,6 +107,87 @@ def test_records_reproduce_oracle(n, tile_bits, flags):
         assert not np.any(forms)
 
 
+def _drun_count(p):
+    count = 0
+    for i in range(p.stats()["passes"]):
+        recs, _, _ = p.records(i)
+        count += int(np.sum(recs["kind"] == 5)) if len(recs) else 0
+    return count
+
+
+def diag_circuit(n, count, seed, outside_from):
+    """Runs of phase gates of every kind a diagonal run takes: phases on one qubit,
+    controlled phases between tile qubits of one half (low qubits 0..1, or
+    2..3), and between qubits below `outside_from` and qubits at or above it
+    (which the tile shapes below leave outside); between runs, a Haar gate, so
+    that passes hold several runs."""
+    rng = G.SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        for _ in range(4 + rng.randint(9)):
+            k = rng.randint(5)
+            phi = rng.uniform_range(0.0, 6.0)
+            lo, hi = rng.randint(outside_from), outside_from + rng.randint(n - outside_from)
+            if k == 0:
+                out.append(G.gate_u1((lo, hi)[rng.randint(2)], G.mat_cphase(phi)))  # a phase on one qubit
+            elif k == 1:
+                out.append(G.gate_cu(lo, hi, G.mat_cphase(phi)))
+            elif k == 2:
+                out.append(G.gate_cu(hi, lo, G.mat_cphase(phi)))
+            elif k == 3:
+                a = rng.randint(2)
+                out.append(G.gate_cu(a, 1 - a, G.mat_cphase(phi)))
+            else:
+                h2 = (outside_from + rng.randint(n - outside_from), outside_from + rng.randint(n - outside_from))
+                if h2[0] != h2[1]:
+                    out.append(G.gate_cu(h2[0], h2[1], G.mat_cphase(phi)))
+        out.append(G.gate_u1(rng.randint(n), G.haar_2x2(rng)))
+    return G.concat(out)
+
+
+@pytest.mark.parametrize("dt,tol", [(qs.QS_C128, TOL), (qs.QS_C64, 1e-5)])
+@pytest.mark.parametrize("n,tile_bits", [(9, 4 | (2 << 8)), (12, 6 | (2 << 8)), (14, 8 | (3 << 8))])
+def test_diagonal_runs_reproduce_oracle(n, tile_bits, dt, tol):
+    """Runs of phase gates whose phase separates over the two halves of the tile
+    bits become one diagonal-run record set (kind 5): bit terms with and without
+    an outside condition, pair terms inside one half, scalar terms of outside
+    qubits.  Applied on the host they give the oracle's state; without them
+    (QS_PLAN_NO_DIAG_RUNS) there are none and the state is the same."""
+    gates = diag_circuit(n, 12, 900 + n, outside_from=4)
+    psi = rand_state(n, 3 + n)
+    want = O.run(psi.copy(), gates)
+    for flags, expect_runs in ((qs.PLAN_DEFAULT, True), (qs.PLAN_NO_DIAG_RUNS, False)):
+        p = qs.Plan(fake_state(n, dt), gates, flags=qs.PLAN_DRY_RUN | flags, tile_bits=tile_bits)
+        try:
+            assert (_drun_count(p) > 0) == expect_runs
+            got = run_plan(p, psi, gates)
+        finally:
+            p.close()
+        assert np.max(np.abs(got - want)) < tol, (flags, np.max(np.abs(got - want)))
+
+
+@pytest.mark.parametrize("n,tile_bits", [(12, 6 | (2 << 8)), (16, 8 | (4 << 8))])
+def test_inverse_qft_diagonal_runs(n, tile_bits):
+    """The inverse QFT's controlled phases whose target lies outside the tile
+    form diagonal runs; the records reproduce the oracle's inverse QFT of a
+    random state, and the plan holds fewer records than without the runs."""
+    gates = G.inverse_circuit(G.qft_circuit(n))
+    psi = rand_state(n, 17 + n)
+    want = O.run(psi.copy(), gates)
+    ops = {}
+    for flags in (qs.PLAN_DEFAULT, qs.PLAN_NO_DIAG_RUNS):
+        p = qs.Plan(fake_state(n), gates, flags=qs.PLAN_DRY_RUN | flags, tile_bits=tile_bits)
+        try:
+            if flags == qs.PLAN_DEFAULT:
+                assert _drun_count(p) > 0
+            ops[flags] = p.stats()["device_ops"]
+            got = run_plan(p, psi, gates)
+        finally:
+            p.close()
+        assert np.max(np.abs(got - want)) < TOL, flags
+    assert ops[qs.PLAN_DEFAULT] < ops[qs.PLAN_NO_DIAG_RUNS]
+
+
 @pytest.mark.parametrize("n", [10, 14])
 def test_records_qft_and_random_workload_shape(n):
     """The benchmark's circuit shape (QFT of a basis state, then random gates),
