@@ -120,11 +120,11 @@ HBM_FALLBACK_GBS = 6800.0  # used only when no measured copy bandwidth is availa
 CSRC = os.path.join(ROOT, "paper_1601_07195_gb300", "csrc")
 NCU_COUNTERS = {
     "df": {"kernel": "k_tile_df_p<12>", "sources": ["tile_df.cu", "tile_df_ops.cuh", "df.cuh", "device.cuh"],
-           "sha": "dd0ca578abe0f1ec", "n": 26, "dram_bytes": 1.074071e9 + 1.012979e9, "warp_inst": 2.48020992e9,
-           "ms": 2.662304},
+           "sha": "02ec315fe702a534", "n": 26, "dram_bytes": 1.075091e9 + 1.013137e9, "warp_inst": 2.48020992e9,
+           "ms": 2.662048},
     "c64": {"kernel": "k_tile_p<float, 12>", "sources": ["tile.cu", "tile_ops.cuh", "device.cuh"],
-            "sha": "9a8ba8f2e2723b5e", "n": 27, "dram_bytes": 1.073805e9 + 1.012977e9, "warp_inst": 1.890975744e9,
-            "ms": 1.854784},
+            "sha": "7aeefc8007452f30", "n": 27, "dram_bytes": 1.073797e9 + 1.012957e9, "warp_inst": 1.891237888e9,
+            "ms": 1.8576},
     "dense": {"kernel": "k_dense6_tc", "sources": ["dense_tc.cu"],
               "sha": "9a74760c8df754dc", "n": 25, "dram_bytes": 268.584960e6 + 206.582528e6, "warp_inst": 37525171.0,
               "ms": 0.091456},
