@@ -308,7 +308,10 @@ qs_status qs_host_alloc(size_t bytes, void** out) {
     // the buffer can be a huge page: the device then reads it through far fewer
     // translations (a 16 GiB copy: 84-97 ms on huge pages; 310-680 ms with 12 of
     // its 32 pages left at 64 KiB)
-    const size_t align = thp_size();
+    // (buffers smaller than one huge page are aligned to 2 MiB only: rounding
+    // them up to 512 MiB would waste memory and the time to populate it)
+    const size_t thp = thp_size();
+    const size_t align = bytes >= thp ? thp : ((size_t)2 << 20);
     const size_t len = (bytes + align - 1) / align * align;
     void* raw = mmap(nullptr, len + align, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
     if (raw == MAP_FAILED) return fail(QS_ENOMEM, "mmap of the host buffer failed");
