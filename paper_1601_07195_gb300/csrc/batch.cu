@@ -693,6 +693,12 @@ struct Group {
     std::vector<int> rev_nslot_used;
     int n_slots = 0, n_rot = 0;
     size_t fwd_per = 0, rev_per = 0;  // op records per instance
+    // forward passes: per member, the length of the diagonal run that starts
+    // there (0: a record of its own, or inside a run), the pass's record count,
+    // and whether it holds runs
+    std::vector<std::vector<int>> fwd_runs;
+    std::vector<int> fwd_nrec;
+    std::vector<char> fwd_dr;
     Region st_fwd, st_rev;            // in the staging / device op buffer
     std::vector<int> slot_rot;        // rev.size() * n_slots
     int* d_slot_rot = nullptr;
@@ -792,8 +798,26 @@ qs_status stage_ops(qs_batch* bt, const double* theta_all) {
             reverse_ops(ops, rops);
             OpT* f = reinterpret_cast<OpT*>(bt->h_stage + g.st_fwd.off) + k * g.fwd_per;
             size_t w = 0;
-            for (const PassDesc& d : g.fwd)
-                for (int j : d.members) f[w++] = make_rec<OpT>(ops[j], d.bit_of, 0, -1);
+            std::vector<Op> pass_ops;
+            std::vector<OpT> run_recs;
+            for (size_t pi = 0; pi < g.fwd.size(); ++pi) {
+                const PassDesc& d = g.fwd[pi];
+                pass_ops.clear();
+                for (int j : d.members) pass_ops.push_back(ops[j]);
+                for (size_t i = 0; i < pass_ops.size();) {
+                    const int len = g.fwd_runs[pi][i];
+                    if (len > 0) {  // a diagonal run: the same records for every member, other factors
+                        run_recs.clear();
+                        diag_run_records(pass_ops, i, i + (size_t)len, d.bit_of, d.tp.b, run_recs);
+                        for (const OpT& r : run_recs) f[w++] = r;
+                        i += (size_t)len;
+                    } else {
+                        f[w++] = make_rec<OpT>(pass_ops[i], d.bit_of, 0, -1);
+                        ++i;
+                    }
+                }
+            }
+            if (w != g.fwd_per) return fail(QS_EINVAL, "batch: forward records differ between members of a group");
             // reverse: a rotation's gradient goes to its slot within the pass
             OpT* r = reinterpret_cast<OpT*>(bt->h_stage + g.st_rev.off) + k * g.rev_per;
             w = 0;
@@ -855,14 +879,15 @@ qs_status record(qs_batch* bt) {
             const PassDesc& d = g.fwd[fi];
             TilePass tp = d.tp;
             tp.op0 = (int)op0;
-            tp.nops = (int)d.members.size();
+            tp.nops = g.fwd_nrec[fi];
             tp.inst_stride = N;
             tp.ops_stride = (int)g.fwd_per;
             // double-float forward passes hand the state over as float pairs;
             // the last one leaves doubles for lambda = H psi and the reverse sweep
             tp.io = df ? ((fi > 0 ? kIoPairsIn : 0) | (fi + 1 < g.fwd.size() ? kIoPairsOut : 0)) : 0;
+            if (g.fwd_dr[fi]) tp.io |= kIoDiagRuns;
             if (qs_status s = launch_tile_pass(&sv, bt->d_stage + g.st_fwd.off, tp, false, count)) return s;
-            op0 += d.members.size();
+            op0 += (size_t)g.fwd_nrec[fi];
         }
         // lambda = H psi, energy
         dim3 hg((unsigned)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count() * 4), count);
@@ -1002,7 +1027,37 @@ qs_status build_batch(qs_batch* bt) {
         if (qs_status st = plan_passes(g.n, rops, g.b_adj, b0, true, 1, g.rev)) return st;
         for (const PassDesc& d : g.fwd)
             if (!d.tile) return fail(QS_EINVAL, "batch: a gate does not fit a tile");
-        g.fwd_per = ops.size();
+        // diagonal runs of the forward passes (the RZ layers: phases on
+        // consecutive qubits), found on the group's shared structure
+        g.fwd_per = 0;
+        g.fwd_runs.assign(g.fwd.size(), {});
+        g.fwd_nrec.assign(g.fwd.size(), 0);
+        g.fwd_dr.assign(g.fwd.size(), 0);
+        {
+            std::vector<Op> pass_ops;
+            std::vector<TileOpDF> recs;
+            for (size_t pi = 0; pi < g.fwd.size(); ++pi) {
+                const PassDesc& d = g.fwd[pi];
+                pass_ops.clear();
+                for (int j : d.members) pass_ops.push_back(ops[j]);
+                g.fwd_runs[pi].assign(pass_ops.size(), 0);
+                for (size_t i = 0; i < pass_ops.size();) {
+                    const size_t len = diag_run_length(pass_ops, i, d.bit_of, d.tp.b, bt->dt);
+                    if (len > 0) {
+                        recs.clear();
+                        diag_run_records(pass_ops, i, i + len, d.bit_of, d.tp.b, recs);
+                        g.fwd_runs[pi][i] = (int)len;
+                        g.fwd_nrec[pi] += (int)recs.size();
+                        g.fwd_dr[pi] = 1;
+                        i += len;
+                    } else {
+                        g.fwd_nrec[pi] += 1;
+                        ++i;
+                    }
+                }
+                g.fwd_per += (size_t)g.fwd_nrec[pi];
+            }
+        }
         g.rev_per = rops.size();
         // rotation slots per reverse pass
         std::vector<int> rank(ops.size(), -1);

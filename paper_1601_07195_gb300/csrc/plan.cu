@@ -874,6 +874,18 @@ qs_status launch_all(qs_plan* p, cudaEvent_t* ev) {
 
 }  // namespace
 
+size_t diag_run_length(const std::vector<Op>& ops, size_t i, const int* bit_of, int b, qs_dtype dt) {
+    return find_diag_run(ops, i, bit_of, b, dt);
+}
+void diag_run_records(const std::vector<Op>& ops, size_t i0, size_t i1, const int* bit_of, int b,
+                      std::vector<TileOpDF>& out) {
+    emit_diag_run(ops, i0, i1, bit_of, b, out);
+}
+void diag_run_records(const std::vector<Op>& ops, size_t i0, size_t i1, const int* bit_of, int b,
+                      std::vector<TileOp<float>>& out) {
+    emit_diag_run(ops, i0, i1, bit_of, b, out);
+}
+
 qs_status plan_passes(int n, const std::vector<Op>& ops, int b, int b0, bool fuse, int min_tile_members,
                       std::vector<PassDesc>& out) {
     b = std::min(b, n);

@@ -164,6 +164,14 @@ struct PassDesc {
 qs_status plan_passes(int n, const std::vector<Op>& ops, int b, int b0, bool fuse, int min_tile_members,
                       std::vector<PassDesc>& out);
 
+// Diagonal runs (plan.cu) for other record builders: the length of the run
+// worth fusing that starts at ops[i] of a pass (0: none), and its records.
+size_t diag_run_length(const std::vector<Op>& ops, size_t i, const int* bit_of, int b, qs_dtype dt);
+void diag_run_records(const std::vector<Op>& ops, size_t i0, size_t i1, const int* bit_of, int b,
+                      std::vector<TileOpDF>& out);
+void diag_run_records(const std::vector<Op>& ops, size_t i0, size_t i1, const int* bit_of, int b,
+                      std::vector<TileOp<float>>& out);
+
 }  // namespace qs
 
 // Internal state handle.
