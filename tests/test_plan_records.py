@@ -289,6 +289,28 @@ def test_random_plans_records_reproduce_oracle():
     prop()
 
 
+def test_random_plans_with_diagonal_runs_reproduce_oracle():
+    """Property test over circuits that interleave runs of phase gates (every
+    diagonal-run term kind) with other gates, random tile shapes, flags and
+    record formats: the records, diagonal runs included, reproduce the oracle."""
+    hyp = pytest.importorskip("hypothesis")
+    st_ = hyp.strategies
+    flag_sets = [qs.PLAN_DEFAULT, qs.PLAN_NO_PHASE_RUNS, qs.PLAN_NO_DIAG_RUNS, qs.PLAN_NO_MERGE]
+    modes = [(qs.QS_C128, 0, TOL), (qs.QS_C128, qs.PLAN_ARITH_F64, TOL), (qs.QS_C64, 0, 1e-5)]
+
+    @hyp.settings(max_examples=80, deadline=None, derandomize=True)
+    @hyp.given(n=st_.integers(4, 11), runs=st_.integers(1, 8), seed=st_.integers(0, 10 ** 6),
+               b=st_.integers(2, 10), b0=st_.integers(0, 4), flags=st_.sampled_from(flag_sets),
+               mode=st_.sampled_from(modes))
+    def prop(n, runs, seed, b, b0, flags, mode):
+        dt, arith, tol = mode
+        gates = G.concat([mixed_circuit(n, 20, seed), diag_circuit(n, runs, seed + 1, outside_from=n // 2),
+                          mixed_circuit(n, 10, seed + 2)])
+        check(n, gates, np.array([0.7, -1.3]), flags | arith, b | (min(b0, b) << 8), seed % 991, dt=dt, tol=tol)
+
+    prop()
+
+
 def test_dense_passes_reproduce_oracle():
     """complex64 plans with runs of >= 10 gates on qubits 0..5: the dense passes'
     64 x 64 matrices (formed by the planner in FP64) together with the other
