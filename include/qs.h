@@ -253,15 +253,16 @@ QS_API qs_status qs_plan_stats(const qs_plan* p, int* n_passes, int* n_tile_pass
 /* Gate updates one execution applies after fusing adjacent single-qubit gates
  * on the same qubit within a tile pass (into their product, where that is
  * cheaper to apply; exact identities are dropped) and runs of phase gates
- * (one update per run, see QS_PLAN_NO_PHASE_RUNS). */
+ * (one update per run, see QS_PLAN_NO_PHASE_RUNS and QS_PLAN_NO_DIAG_RUNS). */
 QS_API qs_status qs_plan_device_ops(const qs_plan* p, int* n_ops);
 
 /* Gate updates of pass i as the kernels apply them (after fusion): counts[3][6]
  * by operation (0 = single-qubit, 1 = controlled, 2 = swap) and class
  * (0 general, 1 real, 2 diagonal, 3 diagonal with q11 = 1, 4 anti-diagonal,
- * 5 permutation).  A fused run of phase gates counts as one single-qubit
- * diagonal update: two complex products on half the amplitudes, the same
- * arithmetic. */
+ * 5 permutation).  A fused run of phase gates around one qubit counts as one
+ * single-qubit diagonal update (two complex products on half the amplitudes,
+ * the same arithmetic); a diagonal run (QS_PLAN_NO_DIAG_RUNS) counts as two
+ * (two complex products on every amplitude). */
 QS_API qs_status qs_plan_pass_op_counts(const qs_plan* p, int i, int* counts);
 
 /* Of pass i's real gate updates (class 1 above), how many the complex128

@@ -390,7 +390,7 @@ class Plan:
 
     def op_counts(self, i):
         """3x6 array: ops of pass i by (single-qubit, controlled, swap) x gate class; a fused run of
-        phase gates counts as one single-qubit diagonal op."""
+        phase gates around one qubit counts as one single-qubit diagonal op, a diagonal run as two."""
         buf = (ctypes.c_int * 18)()
         _check(load().qs_plan_pass_op_counts(self._h, i, buf))
         return np.array(buf[:], dtype=np.int64).reshape(3, 6)

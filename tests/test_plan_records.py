@@ -188,6 +188,26 @@ def test_inverse_qft_diagonal_runs(n, tile_bits):
     assert ops[qs.PLAN_DEFAULT] < ops[qs.PLAN_NO_DIAG_RUNS]
 
 
+def test_diagonal_run_op_counts():
+    """A pass whose only records are one diagonal run reports it as two
+    single-qubit diagonal updates (two complex products on every amplitude),
+    and as one device op; without the runs the same gates count one by one."""
+    n = 10
+    gates = G.concat([G.gate_u1(q, G.mat_cphase(0.1 * q + 0.3)) for q in range(6)])  # phases, no shared qubit
+    p = qs.Plan(fake_state(n), gates, flags=qs.PLAN_DRY_RUN, tile_bits=8 | (4 << 8))
+    try:
+        assert _drun_count(p) == 1
+        counts = sum(p.op_counts(i) for i in range(p.stats()["passes"]))
+        assert counts[0][2] == 2 and counts.sum() == 2 and p.stats()["device_ops"] == 1
+    finally:
+        p.close()
+    p = qs.Plan(fake_state(n), gates, flags=qs.PLAN_DRY_RUN | qs.PLAN_NO_DIAG_RUNS, tile_bits=8 | (4 << 8))
+    try:
+        assert _drun_count(p) == 0 and p.stats()["device_ops"] == 6
+    finally:
+        p.close()
+
+
 @pytest.mark.parametrize("n", [10, 14])
 def test_records_qft_and_random_workload_shape(n):
     """The benchmark's circuit shape (QFT of a basis state, then random gates),
